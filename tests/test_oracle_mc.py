@@ -1,0 +1,208 @@
+"""Statistical pins of the oracle's Monte Carlo step (CPU only).
+
+C-2  Non-interacting cells (A0 = D0 = K = 0, no demag, B = 0): the length chain
+     of each cell must leave invariant the stationary law of the exact
+     length-move kernel of Sec. II (multiplicative factor uniform in
+     [1-sigma, 1+sigma], acceptance Eq. 5 with the m^4 factor), which this test
+     computes by linear algebra, independently of the oracle's code.  That law
+     agrees with the paper's Eq. 7 within its O(sigma) bias; mutants of the
+     oracle with powers 1 or 2 in Eq. 5 fail.
+C-3  Non-interacting cells in a field B along x: <m_x> equals the quadrature of
+     m^2 exp(-F_l/kT) sinh(a)/a L(a) over m, a = V Ms0 B m / kT (Eq. 1 with the
+     Zeeman term), which tests the cone move's symmetry.
+C-7  Fitting Eq. 7 to the sampled lengths recovers m_e and chi (Fig. 2 idea).
+     Plus sublattice independence of the red-black pass.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import optimize, stats
+
+import oracle as O
+import workloads as W
+
+KB = O.KB
+
+
+def free_spec(n, T, Tc=870.0, B=(0.0, 0.0, 0.0), h=5e-9, Ms0=8.6e5):
+    return W._base((n, n, 1), (h, h, h), A0=0.0, Ms0=Ms0, Tc=Tc, T=T, B=B)
+
+
+def length_law(T, Tc, V, Ms0, power=4, ng=900):
+    """Stationary law of the single-cell length chain on a log-m grid."""
+    sig = O.sigma(T, Tc, V, Ms0)
+    Fl = np.vectorize(lambda m: O.long_energy(m, T, Tc, V, Ms0) / (KB * T))
+    mm = np.geomspace(1e-5, 1.2, 20000)
+    p = mm ** 3 * np.exp(-(Fl(mm) - Fl(mm).min()))
+    c = np.cumsum(p)
+    c /= c[-1]
+    lo = mm[np.searchsorted(c, 1e-9)] * 0.8
+    hi = mm[np.searchsorted(c, 1 - 1e-9)] * 1.2
+    y = np.linspace(math.log(lo), math.log(hi), ng + 1)
+    dy = y[1] - y[0]
+    mid = np.exp(0.5 * (y[1:] + y[:-1]))
+    F = Fl(mid)
+    K = np.zeros((ng, ng))
+    for i in range(ng):
+        a = math.log(mid[i] * (1 - sig))
+        b = math.log(mid[i] * (1 + sig))
+        j = np.arange(max(0, int((a - y[0]) / dy)), min(ng - 1, int((b - y[0]) / dy)) + 1)
+        ya = np.maximum(a, y[j])
+        yb = np.minimum(b, y[j + 1])
+        ok = yb > ya
+        j, ya, yb = j[ok], ya[ok], yb[ok]
+        prob = (np.exp(yb) - np.exp(ya)) / (2 * sig * mid[i])
+        acc = np.minimum(1.0, (mid[j] / mid[i]) ** power * np.exp(-(F[j] - F[i])))
+        K[i, j] = prob * acc
+        K[i, i] += 1 - K[i].sum()
+    w, v = np.linalg.eig(K.T)
+    pi = np.real(v[:, np.argmin(abs(w - 1))])
+    pi /= pi.sum()
+    p7 = mid ** 3 * np.exp(-(F - F.min()))          # Eq. 7 density times dm/dy = m
+    p7 /= p7.sum()
+    return y, mid, pi, p7
+
+
+def draw_from(y, pi, n, seed):
+    rng = np.random.default_rng(seed)
+    c = np.concatenate([[0.0], np.cumsum(pi)])
+    u = rng.uniform(0, 1, n)
+    k = np.clip(np.searchsorted(c, u) - 1, 0, len(pi) - 1)
+    frac = (u - c[k]) / np.maximum(pi[k], 1e-300)
+    return np.exp(y[k] + frac * (y[k + 1] - y[k]))
+
+
+def chi2_p(samples, y, pi, nbins=30):
+    """chi^2 p-value of samples against a binned law (equiprobable bins)."""
+    cdf = np.concatenate([[0.0], np.cumsum(pi)])
+    edges_q = np.linspace(0, 1, nbins + 1)[1:-1]
+    idx = np.searchsorted(cdf, edges_q)
+    edges = np.exp(y[np.clip(idx, 0, len(y) - 1)])
+    counts = np.bincount(np.searchsorted(edges, samples), minlength=nbins)
+    expct = np.diff(np.concatenate([[0.0], cdf[np.clip(idx, 0, len(cdf) - 1)], [1.0]])) * len(samples)
+    keep = expct > 5
+    chi2 = ((counts[keep] - expct[keep]) ** 2 / expct[keep]).sum()
+    return stats.chi2.sf(chi2, keep.sum() - 1)
+
+
+def run_lengths(T, power, n=128, sweeps=300, seed=3, start=None):
+    spec = free_spec(n, T)
+    o = O.Oracle(spec, len_power=power)
+    ncell = n * n
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal((ncell, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    m = d * start[:, None]
+    st = O.new_state(seed=seed, theta_deg=30.0, adapt=True, demag_mode=0)
+    m, _, _ = o.run(m, sweeps, st)
+    return np.linalg.norm(m, axis=1)
+
+
+@pytest.mark.parametrize("T,sweeps", [(300.0, 200), (800.0, 300), (900.0, 300)])
+def test_length_law_invariant(T, sweeps):
+    V = 125e-27
+    y, mid, pi, p7 = length_law(T, 870.0, V, 8.6e5, power=4)
+    start = draw_from(y, pi, 128 * 128, seed=11)
+    L = run_lengths(T, 4, sweeps=sweeps, start=start)
+    assert chi2_p(L, y, pi) > 1e-3
+
+
+@pytest.mark.parametrize("T", [300.0, 800.0])
+def test_length_law_matches_eq7_below_tc(T):
+    V = 125e-27
+    y, mid, pi, p7 = length_law(T, 870.0, V, 8.6e5, power=4, ng=1200)
+    # the exact law of the paper's rule and Eq. 7: CDF gap from the O(sigma) bias
+    # (about 1e-3 here) plus the grid's own error
+    assert np.abs(np.cumsum(pi) - np.cumsum(p7)).max() < 3e-3
+    start = draw_from(y, p7, 128 * 128, seed=12)        # start from Eq. 7 itself
+    L = run_lengths(T, 4, sweeps=300, start=start, seed=4)
+    assert chi2_p(L, y, p7) > 1e-3
+    mean7 = (mid * p7).sum()
+    assert L.mean() == pytest.approx(mean7, abs=4 * L.std() / math.sqrt(L.size))
+
+
+@pytest.mark.parametrize("power", [1, 2])
+def test_wrong_length_factor_is_rejected(power):
+    # planted mistake in Eq. 5 (oracle run with another power): the paper's law drifts
+    T = 900.0
+    V = 125e-27
+    y, mid, pi, p7 = length_law(T, 870.0, V, 8.6e5, power=4)
+    start = draw_from(y, pi, 128 * 128, seed=13)
+    L = run_lengths(T, power, sweeps=300, start=start)
+    assert chi2_p(L, y, pi) < 1e-6
+
+
+def test_convergence_from_uniform_start():
+    T = 300.0
+    V = 125e-27
+    y, mid, pi, p7 = length_law(T, 870.0, V, 8.6e5, power=4)
+    L = run_lengths(T, 4, sweeps=400, start=np.full(128 * 128, 0.8))
+    assert chi2_p(L, y, pi) > 1e-3
+
+
+def test_fit_of_eq7_recovers_me_and_chi():
+    T, Tc, V, Ms0 = 800.0, 870.0, 125e-27, 8.6e5
+    y, mid, pi, p7 = length_law(T, Tc, V, Ms0, power=4)
+    start = draw_from(y, pi, 128 * 128, seed=14)
+    L = run_lengths(T, 4, sweeps=300, start=start)
+
+    def nll(par):
+        me, lchi = par
+        chi = math.exp(lchi)
+        a = V * Ms0 / (8 * chi * me * me * KB * T)
+        grid = np.linspace(1e-4, 1.0, 4000)
+        logp = 2 * np.log(grid) - a * (grid ** 2 - me ** 2) ** 2
+        logZ = np.log(np.trapezoid(np.exp(logp - logp.max()), grid)) + logp.max()
+        return -(2 * np.log(L) - a * (L ** 2 - me ** 2) ** 2 - logZ).sum()
+
+    me0, chi0 = O.me(T, Tc), O.chi(T, Tc)
+    res = optimize.minimize(nll, [me0 * 1.1, math.log(chi0) + 0.2], method="Nelder-Mead",
+                            options={"xatol": 1e-6, "fatol": 1e-6, "maxiter": 2000})
+    me_fit, chi_fit = res.x[0], math.exp(res.x[1])
+    assert me_fit == pytest.approx(me0, rel=0.02)
+    assert chi_fit == pytest.approx(chi0, rel=0.06)
+
+
+def test_cone_and_zeeman_langevin_average():
+    T, Tc, V, Ms0, B = 300.0, 870.0, 125e-27, 8.6e5, 0.1
+    spec = free_spec(64, T, B=(B, 0.0, 0.0))
+    o = O.Oracle(spec)
+    n = o.n
+    me = O.me(T, Tc)
+    m = W.random_state(n, 5, me, me)[:, :3].astype(np.float64)
+    st = O.new_state(seed=7, theta_deg=30.0, adapt=True, demag_mode=0)
+    m, _, _ = o.run(m, 400, st)
+    st.adapt = 0
+    m, _, obs = o.run(m, 1500, st, obs_every=10)
+    mx = obs["mean_m"][0]
+    # quadrature of Eq. 1 with Zeeman
+    grid = np.linspace(me - 0.02, me + 0.02, 20001)
+    Fl = np.array([O.long_energy(x, T, Tc, V, Ms0) for x in grid]) / (KB * T)
+    a = V * Ms0 * B * grid / (KB * T)
+    w = grid ** 2 * np.exp(-(Fl - Fl.min())) * np.sinh(a) / a
+    lang = 1 / np.tanh(a) - 1 / a
+    ref = np.trapezoid(w * grid * lang, grid) / np.trapezoid(w, grid)
+    # SE from 150 snapshots of 4096 cells, snapshots correlated over a few sweeps
+    assert mx == pytest.approx(ref, abs=3e-3)
+    assert abs(obs["mean_m"][1]) < 3e-3 and abs(obs["mean_m"][2]) < 3e-3
+
+
+def test_pass_touches_only_its_sublattice_and_ignores_same_colour_cells():
+    spec = W._base((8, 6, 2), (3e-9, 3e-9, 3e-9), A0=1e-11, D0=1e-3, K1=2e5, T=400.0,
+                   B=(0.01, 0.0, 0.02))
+    o = O.Oracle(spec)
+    m = W.random_state(o.n, 8, 0.7, 0.9)[:, :3].astype(np.float64)
+    m1, acc, dec, _ = o.sweep_pass(m, None, 0, 5, 0, 99, 40.0)
+    ijk = np.array([(q % 8, (q // 8) % 6, q // 48) for q in range(o.n)])
+    black = (ijk.sum(1) % 2) == 1
+    assert np.array_equal(m1[black], m[black])
+    assert np.all(acc[black] == -1) and np.all(acc[~black] >= 0)
+    # perturbing another red cell changes no other red cell's decision value
+    m2 = m.copy()
+    r = np.flatnonzero(~black)[3]
+    m2[r] *= 0.9
+    _, _, dec2, _ = o.sweep_pass(m2, None, 0, 5, 0, 99, 40.0)
+    others = ~black
+    others[r] = False
+    assert np.array_equal(dec[others], dec2[others])
