@@ -1,0 +1,355 @@
+"""Benchmark of the MMC hot path on GB300: cell-updates per second.
+
+One step = 100 MMC iterations (the cone-adaptation window, Sec. II) of the
+whole batch: per iteration the FFT demag field (Eq. 14), the red and the black
+sublattice pass; the window/adaptation kernel after the 100th.  The default
+workload is the chiral-film temperature scan: 16 chains of 512x512x1 cells
+(2x2x1 nm), DMI, perpendicular anisotropy, demag, T = 50 + 40 c K, random
+initial state, all chains in one CUDA graph per step.
+
+Printed (one JSON line): value = cell-updates/s with inputs resident in HBM
+(device-timed with CUDA events on the library's stream); e2e = the same metric
+through the public API with the state copied from pinned host memory and the
+observables read back every step; roofline of the dominant kernel (per-kernel
+CUDA-event durations from mmc_phase_times); cpu_baseline = the FP64 oracle on
+the host cores on a bounded sample; clocks sampled with nvidia-smi during the
+timed region.
+
+--impl reference times the FP64 oracle itself (the reference arm of this
+benchmark) on the same workload: each step is one iteration of one chain.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "MMC cell-updates/s incl. demag"
+UNIT = "cell-updates/s"
+SWEEPS_PER_STEP = 100
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chiral512",
+                    choices=["chiral512", "film256", "permalloy32", "granular", "probe8192"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-demag", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    if name == "chiral512":
+        return W.chiral512_batch(16, 512), True, "16 chains 512x512x1, 2x2x1 nm, DMI+Ku+demag, T=50..650 K"
+    if name == "film256":
+        return [W.film256(256)], True, "256x256x1, 4 nm, demag, B=100 mT"
+    if name == "permalloy32":
+        return [W.permalloy32()], False, "32x32x1 periodic, 5 nm, no demag"
+    if name == "granular":
+        sizes = W.granular_sizes(32, 7)
+        return W.granular_batch(32, 7, sizes), True, "32 granular chains, sides %d..%d, hotspot, demag" % (
+            min(sizes), max(sizes))
+    if name == "probe8192":
+        return [W.probe(8192)], False, "8192x8192x1, 5 nm, no demag"
+    raise ValueError(name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_sweep.cu", "k_demag.cu", "fft.cuh", "philox.cuh", "mmc_internal.h"):
+        with open(os.path.join(ROOT, "paper_2106_05593_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload_name, src_hash):
+    """DRAM bytes per launch from a committed ncu summary, if taken on this source."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic_per_launch.txt")
+    if not os.path.exists(p):
+        return None
+    for ln in open(p):
+        t = ln.split()
+        if len(t) >= 4 and not ln.startswith("#") and t[0] == kernel and t[1] == workload_name and t[2] == src_hash:
+            return float(t[3])
+    return None
+
+
+# algorithmic bytes per cell per launch (documented in the design doc)
+def algorithmic_bytes(kind, demag, percell):
+    if kind == "sweep_pass":     # per pass: half the cells updated; 48 B/cell-update (+48 per-cell table)
+        return 0.5 * (48.0 if demag else 32.0) + (0.5 * 48.0 if percell else 0.0)
+    if kind == "demag_rows_fwd":  # m read 16 B, three half-spectrum rows written 24 B
+        return 40.0
+    if kind == "demag_cols":      # spectrum read and written, 2 x 24 B
+        return 48.0
+    if kind == "demag_rows_inv":  # spectrum read 24 B, h_eff written 16 B
+        return 40.0
+    return 0.0
+
+
+def cpu_baseline(specs, demag, nsweeps=3):
+    """FP64 oracle, one thread, one chain of the workload for a few iterations."""
+    import oracle as O
+    spec = specs[0]
+    o = O.Oracle(spec)
+    n = o.n
+    m = o.init_state(random=True, length=0.5, chain=0, seed=1)
+    st = O.new_state(seed=1, theta_deg=30.0, adapt=True, demag_mode=1 if demag else 0)
+    o.run(m, 1, st)
+    t0 = time.perf_counter()
+    o.run(m, nsweeps, st)
+    dt = time.perf_counter() - t0
+    return {"value": n * nsweeps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"chain 0 of the workload ({spec['mesh'][0]}x{spec['mesh'][1]}x{spec['mesh'][2]}), "
+                      f"{nsweeps} iterations after 1 warm-up, demag {'FFT FP64' if demag else 'off'}"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    specs, demag, desc = workload(args.workload)
+    spec = specs[0]
+    o = O.Oracle(spec)
+    m = o.init_state(random=True, length=0.5, chain=0, seed=1)
+    st = O.new_state(seed=1, theta_deg=30.0, adapt=True, demag_mode=1 if demag else 0)
+    per = 1
+    for _ in range(args.warmup):
+        m, _, _ = o.run(m, per, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        m, _, _ = o.run(m, per, st)
+    dt = time.perf_counter() - t0
+    value = o.n * per * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc,
+                       "sample": "chain 0, one MMC iteration per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"chain 0 of {args.workload}, {per} iteration per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2106_05593_gb300 import MMC, build
+    build.build()
+    specs, demag, desc = workload(args.workload)
+    percell = args.workload == "granular"
+    stream = torch.cuda.Stream()
+    g = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), stream=stream)
+    seed = 1 + rank
+    g.init_random(seed)
+    ncell = sum(g.ncell)
+    cells_per_step = ncell * SWEEPS_PER_STEP
+    for _ in range(args.warmup):
+        g.sweep(SWEEPS_PER_STEP, seed)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = g.launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.sweep(SWEEPS_PER_STEP, seed)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = g.launches - l0
+    clk = clocks.stop()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = cells_per_step * args.steps * world / (ms_max * 1e-3)
+
+    # per-kernel durations (CUDA events on the library's stream), one more window
+    phases = g.phase_times(SWEEPS_PER_STEP, seed)
+    peak, peak_kind = measured_peaks()
+    best = None
+    for kind, (tms, cnt) in phases.items():
+        if cnt and (best is None or tms > phases[best][0]):
+            best = kind
+    tms, cnt = phases[best]
+    avg_s = tms / cnt * 1e-3
+    bytes_per_launch = algorithmic_bytes(best, demag, percell) * ncell
+    achieved = bytes_per_launch / avg_s / 1e9
+    src = kernel_source_hash()
+    roofline = {"bound": "hbm", "kernel": best, "achieved": achieved, "peak": peak,
+                "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(best, args.workload, src),
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_s * 1e3}
+    sweep_ms, sweep_cnt = phases["sweep_pass"]
+    sweep_bytes = algorithmic_bytes("sweep_pass", demag, percell) * ncell
+    sweep_roof = {"achieved": sweep_bytes / (sweep_ms / sweep_cnt * 1e-3) / 1e9, "peak": peak,
+                  "frac": sweep_bytes / (sweep_ms / sweep_cnt * 1e-3) / 1e9 / peak, "unit": "GB/s",
+                  "avg_launch_ms": sweep_ms / sweep_cnt}
+
+    # end to end through the public API: state from pinned host memory, observables back
+    e2e = None
+    if args.e2e_steps > 0:
+        host_m = []
+        for k in range(g.nchains):
+            buf = torch.empty((g.ncell[k], 4), dtype=torch.float32, pin_memory=True)
+            buf.copy_(torch.from_numpy(g.get_m(k)))
+            host_m.append(buf.numpy())
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.e2e_steps):
+            for k in range(g.nchains):
+                g.set_m(host_m[k], k)
+            g.sweep(SWEEPS_PER_STEP, seed)
+            for k in range(g.nchains):
+                ob = g.observables(k)
+                d2h += 8 * (3 + 2) + 8 * ob["hist"].size
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+        e2e = {"value": cells_per_step * args.e2e_steps * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(h.nbytes for h in host_m)),
+               "d2h_bytes_per_step": int(d2h // args.e2e_steps)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(specs, demag)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (demag FFT f64)" if args.fp64_demag else "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "cells": ncell,
+                       "sweeps_per_step": SWEEPS_PER_STEP, "demag": "once per iteration" if demag else "off",
+                       "l2": "working set larger than L2" if args.workload in ("chiral512", "granular", "probe8192")
+                       else "working set L2-resident (no flush)", "graphs": True},
+            "roofline": roofline, "roofline_sweep_pass": sweep_roof,
+            "phases_ms": {k: round(v[0] / max(v[1], 1), 5) for k, v in phases.items()},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "kernel_source": src,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,263 @@
+/*
+ * mmc.h -- C ABI of a GB300 (sm_103a) implementation of the parallel
+ * micromagnetic Monte Carlo (MMC) method of S. Lepadatu, "Micromagnetic Monte
+ * Carlo method with variable magnetization length based on the
+ * Landau-Lifshitz-Bloch equation" (arXiv:2106.05593).
+ *
+ * The problem statement follows the paper: a mesh of cells of volume V with
+ * magnetization m = M/Ms0 (Sec. II), material parameters Ms0, A0 (exchange,
+ * Eq. 10), D0 (interfacial DMI, Eq. 15), K1/K2 with easy axis e_A (uniaxial
+ * Eq. 11, or cubic Eq. 12), Curie temperature Tc and atomic moment mu (Eqs. 8-9),
+ * a temperature field T, an applied field, and the demagnetizing interaction by
+ * zero-padded FFT convolution with the Newell tensor (Sec. III, Eq. 14).
+ * mmc_sweep runs MMC iterations: each cell, one checkerboard sublattice at a
+ * time, proposes a rotation in a cone plus a multiplicative length change
+ * (Sec. II) and accepts it with Eq. 5.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns mmc_status (MMC_OK == 0, errors < 0).  Nothing
+ *    aborts, traps or throws across the ABI; mmc_status_str() gives text and
+ *    mmc_last_error() the message of the last failure on the calling thread.
+ *  - Units are SI: lengths in m, Ms0 in A/m, A0 in J/m, D0 in J/m^2, K in J/m^3,
+ *    T and Tc in K, mu in J/T, applied fields as mu0*H in tesla.
+ *  - Cell index q = i + nx*(j + ny*k) ("natural order").  Vector arrays of m
+ *    exchanged with the caller are float4 per cell (x, y, z, unused) in natural
+ *    order.
+ *  - The library owns all device memory it allocates (cudaMalloc at create, freed
+ *    at destroy).  Every pointer argument is a HOST pointer unless its comment
+ *    says "device"; host buffers are owned by the caller and read or written
+ *    only during the call.
+ *  - Work is issued on the CUDA stream given at create (NULL = legacy default
+ *    stream).  Calls that return results to host memory synchronize that stream.
+ *  - A context holds nchains independent Markov chains ("batch"); a plain
+ *    single-chain context is a batch of one.  Chains advance in lockstep: one
+ *    sweep counter, one seed; Philox counter word 2 carries the chain index.
+ */
+#ifndef MMC_H
+#define MMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MMC_OK = 0,
+    MMC_ERR_ARG = -1,         /* invalid argument (null, T <= 0, odd periodic extent, ...) */
+    MMC_ERR_CUDA = -2,        /* a CUDA runtime / cuFFT call failed */
+    MMC_ERR_TIMEOUT = -3,     /* a bounded device-side wait gave up */
+    MMC_ERR_NONFINITE = -4,   /* non-finite values in input or state */
+    MMC_ERR_UNSUPPORTED = -5, /* a combination this build does not implement */
+    MMC_ERR_NOMEM = -6        /* device or host allocation failed */
+} mmc_status;
+
+typedef struct mmc_ctx mmc_ctx;   /* opaque; owned by the library */
+
+/* Mesh (Sec. II): nx*ny*nz cells; periodic[a] != 0 makes axis a periodic for the
+ * exchange and DMI bonds and requires an even extent >= 2 on that axis.  The
+ * demagnetizing field always uses open (zero-padded) boundaries. */
+typedef struct {
+    int nx, ny, nz;
+    int periodic[3];
+} mmc_mesh;
+
+/* Material (Sec. II-IV).  Scalars apply to every cell unless the matching
+ * per-cell HOST array (ncell entries, natural order; e_A_cell: 3 per cell) is
+ * non-NULL.  Temperature scaling: A and D enter as A0, D0 (the paper's
+ * A/Me^2 = A0/Ms0^2); K1(T) = K1 m_e^3 and K2(T) = K2 m_e^10 for uniaxial,
+ * K1 m_e^10 and K2 m_e^21 for cubic anisotropy (m_e^{l(l+1)/2}). */
+typedef struct {
+    double Ms0;               /* A/m */
+    double A0;                /* J/m */
+    double D0;                /* J/m^2, interfacial DMI (in-plane bonds) */
+    double K1, K2;            /* J/m^3 at T = 0 */
+    double e_A[3];            /* uniaxial easy axis (normalized by the library) */
+    double Tc;                /* K */
+    double mu_atom;           /* J/T in Eq. 8; <= 0 selects one Bohr magneton */
+    int aniso_cubic;          /* 0 uniaxial (Eq. 11), 1 cubic along x, y, z (Eq. 12) */
+    const double *Ms0_cell;   /* optional per-cell Ms0 */
+    const double *K1_cell;    /* optional per-cell K1 */
+    const double *e_A_cell;   /* optional per-cell easy axis, 3 per cell */
+    const double *Tc_cell;    /* optional per-cell Tc */
+    const int *grain;         /* optional grain id per cell */
+    double grain_exch_scale;  /* exchange and DMI scale of bonds joining two grains */
+} mmc_material;
+
+/* Options.  mmc_default_options() fills the documented defaults. */
+typedef struct {
+    int demag;                /* 1: include the demag interaction (Eq. 14)          [0] */
+    int demag_per_pass;       /* 1: recompute H_d before each sublattice pass       [0] */
+    int demag_fp64;           /* 1: FP64 FFT convolution; 0: FP32 (own kernels)     [0] */
+    int demag_cufft;          /* 1: cuFFT transforms instead of the own FFT kernels [0] */
+    int adapt;                /* 1: adapt the cone angle every 100 sweeps (Sec. II) [1] */
+    double theta0_deg;        /* initial cone half-angle                           [30] */
+    double sigma_cap;         /* cap of Eq. 13                                   [0.03] */
+    int hist_bins;            /* |m| histogram bins on [0, hist_max)              [200] */
+    double hist_max;          /*                                                    [1] */
+    int use_graphs;           /* 1: capture 100-sweep blocks in CUDA graphs         [1] */
+} mmc_options;
+
+/* One chain of a batch. T_cell (optional, HOST) gives a per-cell temperature;
+ * otherwise T applies to all cells.  B is the applied field (tesla). */
+typedef struct {
+    mmc_mesh mesh;
+    double cellsize[3];
+    mmc_material material;
+    double T;
+    const double *T_cell;
+    double B[3];
+} mmc_chain_desc;
+
+/* Observables (Sec. II, Figs. 1-2): averages over the snapshots accumulated by
+ * mmc_sweep_sampled since the last reset, or over the current state when none.
+ * hist (optional HOST buffer of hist_bins + 1 counters, last = overflow) is
+ * filled with the |m| histogram of the same samples. */
+typedef struct {
+    double mean_m[3];         /* <m> */
+    double mean_len;          /* <|m|> */
+    double mean_len2;         /* <|m|^2> */
+    int64_t nsnap;            /* snapshots averaged (0: current state) */
+    int64_t nonfinite;        /* cells with a non-finite component */
+    double acc_rate;          /* acceptance rate of the last completed 100-sweep window */
+    double theta_deg;         /* current cone half-angle */
+    int64_t sweeps;           /* sweep counter */
+    int64_t *hist;            /* optional, hist_bins + 1 entries */
+} mmc_obs;
+
+/* ---------------------------------------------------------------------------
+ * Lifetime
+ * ------------------------------------------------------------------------- */
+
+/* Fill *opt with the defaults shown in brackets above. */
+mmc_status mmc_default_options(mmc_options *opt);
+
+/* Create a context of nchains chains (Sec. II-IV problem statement).
+ * Validates the inputs (MMC_ERR_ARG: null pointers, non-positive sizes or
+ * temperatures, odd periodic extents, FFT sizes above 4096), computes the
+ * thermodynamic tables m_e(T), chi(T) (Eqs. 8-9) and sigma (Eq. 13), the Newell
+ * tensor spectra (Eq. 14, FP64 on the host) and uploads everything once.  The
+ * initial state is m = m_e(T) along +x per cell (or 0.3 where m_e = 0); use
+ * mmc_set_m / mmc_init_random to change it.  cuda_stream is a cudaStream_t or
+ * NULL.  On success *out owns device memory until mmc_destroy. */
+mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_options *opt,
+                      void *cuda_stream, mmc_ctx **out);
+
+/* Convenience for one chain: mesh, cell size, material, T (scalar, or T_cell).
+ * Same semantics as mmc_create with nchains = 1 and zero applied field. */
+mmc_status mmc_create_single(const mmc_mesh *mesh, const double cellsize[3],
+                             const mmc_material *mat, double T, const double *T_cell,
+                             const mmc_options *opt, void *cuda_stream, mmc_ctx **out);
+
+/* Release every resource of ctx (NULL is accepted). */
+void mmc_destroy(mmc_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * State
+ * ------------------------------------------------------------------------- */
+
+/* Applied field of one chain (chain < 0: all chains), tesla. */
+mmc_status mmc_set_field(mmc_ctx *ctx, int chain, const double B[3]);
+
+/* Copy m of one chain in/out as float4 per cell in natural order.  src/dst are
+ * HOST pointers when is_device == 0, DEVICE pointers otherwise.  mmc_set_m
+ * rejects non-finite values (MMC_ERR_NONFINITE) and recomputes H_d. */
+mmc_status mmc_set_m(mmc_ctx *ctx, int chain, const float *src, int is_device);
+mmc_status mmc_get_m(mmc_ctx *ctx, int chain, float *dst, int is_device);
+
+/* Random initial directions from Philox counter (cell, 0, chain, 1), key seed:
+ * z = 2 u0 - 1, phi = 2 pi u1, length len (len <= 0: m_e, or the Eq. 7 rms
+ * length where m_e = 0). */
+mmc_status mmc_init_random(mmc_ctx *ctx, uint64_t seed, double len);
+
+/* ---------------------------------------------------------------------------
+ * Monte Carlo (Sec. II, III)
+ * ------------------------------------------------------------------------- */
+
+/* n MMC iterations of every chain.  Each iteration: (demag field, Eq. 14, if
+ * enabled) -> red pass ((i+j+k) even) -> [demag again if demag_per_pass] ->
+ * black pass; every 100 iterations of the global counter the cone angle is
+ * adapted (Sec. II).  Random numbers: Philox4x32-10 with counter
+ * (cell, sweep, chain, 0) and key (seed & 0xffffffff, seed >> 32); uniforms
+ * ((r >> 9) + 1/2) 2^-23.  Runs entirely on the device. */
+mmc_status mmc_sweep(mmc_ctx *ctx, int64_t n, uint64_t seed);
+
+/* As mmc_sweep, accumulating an observable snapshot every sample_every
+ * iterations (sample_every >= 1) into device accumulators read by
+ * mmc_observables. */
+mmc_status mmc_sweep_sampled(mmc_ctx *ctx, int64_t n, uint64_t seed, int sample_every);
+
+/* Recompute the demag field of every chain from the current state (Eq. 14). */
+mmc_status mmc_demag_update(mmc_ctx *ctx);
+
+/* One sublattice pass of one chain with explicit sweep index and cone angle,
+ * leaving the sweep counter and adaptation alone: diagnostic form used by
+ * parity checks.  dec (optional HOST, ncell floats) receives the decision value
+ * d = dF/kT - 4 ln(m'/m) + ln u3 (accept iff d < 0) of the cells of that
+ * colour, acc (optional HOST, ncell int8) 1/0 for them and -1 for the others. */
+mmc_status mmc_pass_debug(mmc_ctx *ctx, int chain, int color, uint32_t sweep, uint64_t seed,
+                          double theta_deg, float *dec, int8_t *acc);
+
+/* ---------------------------------------------------------------------------
+ * Measurements
+ * ------------------------------------------------------------------------- */
+
+/* Observables of one chain (see mmc_obs); reset != 0 clears the snapshot
+ * accumulators after reading them. */
+mmc_status mmc_observables(mmc_ctx *ctx, int chain, mmc_obs *out, int reset);
+
+/* Energy terms of one chain, in J: out[7] = {total, exchange, dmi, anisotropy,
+ * zeeman, longitudinal (Eq. 7), demag (E_d = -(mu0 V/2) sum Ms0 m.H_d)}.
+ * Sums accumulate in FP64; the demag field of the current state is recomputed
+ * with the FP64 convolution. */
+mmc_status mmc_energy(mmc_ctx *ctx, int chain, double out[7]);
+
+/* Demag field H_d (A/m) of one chain's current state, 3 doubles per cell in
+ * natural order (HOST), from the FP64 convolution. */
+mmc_status mmc_demag_field(mmc_ctx *ctx, int chain, double *H);
+
+/* Thermodynamic tables of one chain (HOST, ncell doubles each, any may be NULL):
+ * m_e (Eq. 9), chi (Eq. 8, 1/T), sigma (Eq. 13 capped). */
+mmc_status mmc_tables(mmc_ctx *ctx, int chain, double *me, double *chi, double *sigma);
+
+/* Energy and gradient of one chain for a caller-given state (differentiable
+ * form): m is a DEVICE array of 3*ncell values (double if fp64 != 0, else
+ * float) in natural order; dEdm (DEVICE, same type and size) receives dE/dm_i in
+ * J per unit m; E (HOST, 7 doubles) the terms as mmc_energy; dEdp (HOST, 5
+ * doubles) dE/d(Ms0, A0, D0, K1, chi) for a uniform material.  The demag field is
+ * recomputed from m in the requested precision; nothing is stored between
+ * calls. */
+mmc_status mmc_energy_grad(mmc_ctx *ctx, int chain, const void *m, int fp64,
+                           double E[7], void *dEdm, double dEdp[5]);
+
+/* Per-kernel timing: runs n MMC iterations eagerly (as mmc_sweep, without
+ * graphs) with CUDA events recorded on the context's stream around every kernel
+ * and returns, per kernel kind, the summed duration in ms (ms) and the number
+ * of launches (count).  Kinds: 0 demag rows forward, 1 demag columns, 2 demag
+ * rows inverse, 3 sublattice pass, 4 observables, 5 window/adaptation step.
+ * Both arrays have 6 entries (HOST). */
+mmc_status mmc_phase_times(mmc_ctx *ctx, int64_t n, uint64_t seed, double ms[6], int64_t count[6]);
+
+/* Number of kernels the library launched since create (all kinds). */
+int64_t mmc_kernel_launches(const mmc_ctx *ctx);
+
+/* Number of chains and cells of a chain. */
+int mmc_nchains(const mmc_ctx *ctx);
+int64_t mmc_ncell(const mmc_ctx *ctx, int chain);
+
+/* Checkpoint: serialize the full chain state (m of all chains, sweep counter,
+ * cone angle, window counters, applied fields) into buf.  With buf == NULL only
+ * *len is set to the required size.  mmc_restore accepts a buffer from a context
+ * created with the same chain descriptors; resuming reproduces the
+ * uninterrupted run bit for bit. */
+mmc_status mmc_checkpoint(mmc_ctx *ctx, void *buf, size_t *len);
+mmc_status mmc_restore(mmc_ctx *ctx, const void *buf, size_t len);
+
+const char *mmc_status_str(mmc_status s);
+const char *mmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMC_H */

@@ -443,8 +443,15 @@ orc_ctx *orc_create(const orc_problem *p)
     c->K2 = dup_d(p->K2, n, 0.0);
     c->Tc = dup_d(p->Tc, n, 0.0);
     c->T = dup_d(p->T, n, 0.0);
+    /* e_A is the symmetry-axis direction of Eq. 11: stored as a unit vector */
     c->eA = (double *)malloc(sizeof(double) * 3 * (size_t)n);
     for (int i = 0; i < 3 * n; ++i) c->eA[i] = p->eA ? p->eA[i] : (i % 3 == 2 ? 1.0 : 0.0);
+    for (int i = 0; i < n; ++i) {
+        double *e = c->eA + 3 * i;
+        double l = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        if (l > 0.0) { e[0] /= l; e[1] /= l; e[2] /= l; }
+        else { e[0] = 0.0; e[1] = 0.0; e[2] = 1.0; }
+    }
     c->grain = (int *)malloc(sizeof(int) * (size_t)n);
     for (int i = 0; i < n; ++i) c->grain[i] = p->grain ? p->grain[i] : 0;
     c->p.Ms0 = c->p.K1 = c->p.K2 = c->p.eA = c->p.Tc = c->p.T = NULL;

@@ -1,0 +1,1241 @@
+// C ABI of the GB300 MMC library (include/mmc.h): context set-up, host tables,
+// launch plans, the sweep loop (eager or CUDA-graph blocks of 100 iterations),
+// measurements and checkpoints.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/mmc.h"
+#include "mmc_internal.h"
+
+using namespace mmc;
+
+namespace {
+
+thread_local std::string g_err;
+
+mmc_status fail(mmc_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) return fail(MMC_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define MMC_TRY(expr)                 \
+  do {                                \
+    mmc_status s_ = (expr);           \
+    if (s_ != MMC_OK) return s_;      \
+  } while (0)
+
+// inside create: release the half-built context on failure
+#define MMC_TRY_OR(expr)                          \
+  do {                                            \
+    mmc_status s_ = (expr);                       \
+    if (s_ != MMC_OK) { mmc_destroy(c); return s_; } \
+  } while (0)
+#define CUDA_TRY_OR(expr)                                                                      \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      mmc_destroy(c);                                                                          \
+      return fail(MMC_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));           \
+    }                                                                                          \
+  } while (0)
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+int pad_len(int n, bool axis_active) {
+  if (!axis_active) return 1;
+  int p = 2;
+  while (p < 2 * n) p <<= 1;
+  return p;
+}
+
+struct ChainHost {
+  mmc_mesh mesh;
+  double h[3];
+  double V;
+  double T, Tc, Ms0, K1, K2, mu;
+  int cubic;
+  bool percell;
+  double Tref;
+  long long ncell, slots;
+  std::vector<double> me, chi, sigma;   // per cell (size 1 for uniform chains)
+  EnergyCoef ecoef;
+  std::vector<double> etab;             // per-cell energy table, 10 doubles per cell
+  std::vector<float> init_len;          // per-cell initial length (natural order)
+  std::vector<float> grain;             // natural order, or empty
+};
+
+struct DemagPlan {
+  bool fp64 = false;
+  ChainDev *d_ch = nullptr;             // chain table the plan indexes
+  int *rows_chain = nullptr;
+  long long *rows_first = nullptr;
+  int rows_blocks = 0, rows_threads = 0;
+  size_t rows_smem = 0;
+  int *cols_chain = nullptr;
+  long long *cols_first = nullptr;
+  int cols_blocks = 0, cols_threads = 0, cols_cc = 1;
+  size_t cols_smem = 0;
+  void *spec = nullptr;
+  bool ready = false;
+};
+
+struct SpecSet {
+  double h[3];
+  int Px, Py, Pz;
+  void *d32 = nullptr, *d64 = nullptr;
+};
+
+struct GraphEntry {
+  unsigned key0, key1;
+  int sample_every;
+  long long launches;
+  cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct mmc_ctx {
+  int nchains = 0;
+  mmc_options opt;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool any_demag = false, any_percell = false;
+  std::vector<ChainHost> hc;
+  std::vector<ChainDev> ch;
+  ChainDev *d_ch = nullptr;
+  ChainState *d_st = nullptr, *d_st_dbg = nullptr;
+  unsigned *d_sweep_base = nullptr, *d_dbg_sweep = nullptr;
+  float4 *d_m = nullptr, *d_heff = nullptr, *d_tab = nullptr;
+  float *d_ms = nullptr;
+  long long m_total = 0, tab_total = 0, ms_total = 0;
+  std::vector<SpecSet> specs;
+  void **d_nhat32 = nullptr, **d_nhat64 = nullptr;
+  void *d_tw32 = nullptr, *d_tw64 = nullptr;
+  int *d_sw_chain = nullptr;
+  long long *d_sw_first = nullptr;
+  std::vector<long long> sw_first;
+  int sw_blocks = 0;
+  int *d_obs_chain = nullptr;
+  long long *d_obs_first = nullptr;
+  int obs_blocks = 0;
+  double *d_part = nullptr;
+  unsigned long long *d_hist_acc = nullptr, *d_hist_cur = nullptr;
+  double *d_obs_out = nullptr;
+  DemagPlan batch_plan;
+  std::vector<DemagPlan> single64;      // per chain, built lazily
+  double *d_Hd = nullptr, *d_eout = nullptr, *d_etab = nullptr;
+  float4 *d_nat = nullptr;
+  float *d_dec = nullptr;
+  signed char *d_acc = nullptr;
+  long long max_ncell = 0, max_slots = 0;
+  long long launches = 0;
+  uint64_t host_sweep = 0;
+  std::vector<GraphEntry> graphs;
+  std::vector<void *> allocs;
+
+  Launch L() { return Launch{stream, &launches}; }
+};
+
+namespace {
+
+mmc_status dalloc(mmc_ctx *c, void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(MMC_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  return MMC_OK;
+}
+
+template <typename T>
+mmc_status dalloc_t(mmc_ctx *c, T **p, size_t count) {
+  void *v = nullptr;
+  mmc_status s = dalloc(c, &v, count * sizeof(T));
+  *p = static_cast<T *>(v);
+  return s;
+}
+
+template <typename T>
+mmc_status upload(mmc_ctx *c, T **p, const std::vector<T> &v) {
+  MMC_TRY(dalloc_t(c, p, std::max<size_t>(v.size(), 1)));
+  if (!v.empty()) CUDA_TRY(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return MMC_OK;
+}
+
+// thermodynamic state of one (T, Tc) pair, Eqs. 7-9 and 13
+struct Thermo {
+  double me, chi, sigma, c2, c4, me2;   // F_l = c2 m^2 + c4 (m^2 - me2)^2
+};
+
+Thermo thermo(double T, double Tc, double mu, double V, double Ms0, double cap) {
+  Thermo t;
+  t.me = me_of_T(T, Tc);
+  t.chi = chi_of_T(T, Tc, mu);
+  t.sigma = sigma_of_T(T, Tc, mu, V, Ms0, cap);
+  double c2, c4;
+  long_coeffs(T, Tc, mu, V, Ms0, &c2, &c4);
+  const double Tg = std::fabs(T - Tc) < 1e-3 ? (T < Tc ? Tc - 1e-3 : Tc + 1e-3) : T;
+  if (Tg < Tc) {
+    t.c2 = 0.0; t.c4 = c4; t.me2 = t.me * t.me;
+  } else {
+    t.c2 = c2; t.c4 = c4; t.me2 = 0.0;
+  }
+  return t;
+}
+
+void split_f(double v, float &hi, float &lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+template <typename F>
+void parallel_for(long long n, F fn) {
+  const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (n < 4096 || nth == 1) {
+    for (long long i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nth; ++t)
+    th.emplace_back([&, t]() {
+      for (long long i = t; i < n; i += nth) fn(i);
+    });
+  for (auto &x : th) x.join();
+}
+
+mmc_status validate(const mmc_chain_desc &d, const mmc_options &o, int idx) {
+  const std::string w = "chain " + std::to_string(idx) + ": ";
+  const mmc_mesh &m = d.mesh;
+  if (m.nx < 1 || m.ny < 1 || m.nz < 1) return fail(MMC_ERR_ARG, w + "mesh extents must be >= 1");
+  const long long n = 1LL * m.nx * m.ny * m.nz;
+  if (n >= (1LL << 31)) return fail(MMC_ERR_ARG, w + "more than 2^31 cells");
+  const int ext[3] = {m.nx, m.ny, m.nz};
+  for (int a = 0; a < 3; ++a)
+    if (m.periodic[a] && (ext[a] < 2 || ext[a] % 2))
+      return fail(MMC_ERR_ARG, w + "a periodic extent must be even and >= 2");
+  for (int a = 0; a < 3; ++a)
+    if (!(d.cellsize[a] > 0.0)) return fail(MMC_ERR_ARG, w + "cell size must be > 0");
+  const mmc_material &mt = d.material;
+  if (!(mt.Ms0 > 0.0) && !mt.Ms0_cell) return fail(MMC_ERR_ARG, w + "Ms0 must be > 0");
+  if (!(mt.Tc > 0.0) && !mt.Tc_cell) return fail(MMC_ERR_ARG, w + "Tc must be > 0");
+  if (!d.T_cell && !(d.T > 0.0)) return fail(MMC_ERR_ARG, w + "T must be > 0");
+  if (d.T_cell)
+    for (long long i = 0; i < n; ++i)
+      if (!(d.T_cell[i] > 0.0)) return fail(MMC_ERR_ARG, w + "T_cell must be > 0 everywhere");
+  if (mt.Ms0_cell)
+    for (long long i = 0; i < n; ++i)
+      if (!(mt.Ms0_cell[i] > 0.0)) return fail(MMC_ERR_ARG, w + "Ms0_cell must be > 0");
+  if (mt.Tc_cell)
+    for (long long i = 0; i < n; ++i)
+      if (!(mt.Tc_cell[i] > 0.0)) return fail(MMC_ERR_ARG, w + "Tc_cell must be > 0");
+  const bool percell = mt.Ms0_cell || mt.K1_cell || mt.e_A_cell || mt.Tc_cell || d.T_cell;
+  if (percell && mt.aniso_cubic)
+    return fail(MMC_ERR_UNSUPPORTED, w + "cubic anisotropy with per-cell material or temperature");
+  if (o.demag) {
+    const int P[3] = {pad_len(m.nx, true), pad_len(m.ny, true), pad_len(m.nz, m.nz > 1)};
+    for (int a = 0; a < 3; ++a)
+      if (P[a] > kMaxFFT) return fail(MMC_ERR_ARG, w + "padded FFT length above 4096");
+    if (1LL * P[1] * P[2] > 8192) return fail(MMC_ERR_UNSUPPORTED, w + "padded ny*nz plane above 8192");
+  }
+  return MMC_OK;
+}
+
+// tables of one chain (host)
+void build_chain(ChainHost &H, ChainDev &D, const mmc_chain_desc &d, const mmc_options &o, int idx) {
+  const mmc_material &mt = d.material;
+  H.mesh = d.mesh;
+  for (int a = 0; a < 3; ++a) H.h[a] = d.cellsize[a];
+  H.V = H.h[0] * H.h[1] * H.h[2];
+  H.T = d.T; H.Tc = mt.Tc; H.Ms0 = mt.Ms0; H.K1 = mt.K1; H.K2 = mt.K2;
+  H.mu = mt.mu_atom > 0 ? mt.mu_atom : muB;
+  H.cubic = mt.aniso_cubic;
+  H.percell = mt.Ms0_cell || mt.K1_cell || mt.e_A_cell || mt.Tc_cell || d.T_cell;
+  const int nx = d.mesh.nx, ny = d.mesh.ny, nz = d.mesh.nz;
+  H.ncell = 1LL * nx * ny * nz;
+  const int hx = (nx + 1) / 2;
+  H.slots = 1LL * hx * ny * nz;
+
+  std::memset(&D, 0, sizeof(D));
+  D.nx = nx; D.ny = ny; D.nz = nz; D.hx = hx; D.nrows = ny * nz;
+  D.pbc = (d.mesh.periodic[0] ? 1 : 0) | (d.mesh.periodic[1] ? 2 : 0) | (d.mesh.periodic[2] ? 4 : 0);
+  D.chain = idx;
+  D.ncell = H.ncell;
+  D.h_off = -1; D.t_off = -1; D.ms_off = -1;
+  D.Bx = (float)d.B[0]; D.By = (float)d.B[1]; D.Bz = (float)d.B[2];
+  D.gscale = (float)(mt.grain ? mt.grain_exch_scale : 1.0);
+  D.Ms0 = (float)mt.Ms0;
+  double e[3] = {mt.e_A[0], mt.e_A[1], mt.e_A[2]};
+  double en = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+  if (!(en > 0)) { e[0] = 0; e[1] = 0; e[2] = 1; en = 1; }
+  for (int a = 0; a < 3; ++a) e[a] /= en;
+  if (e[2] < 0) for (int a = 0; a < 3; ++a) e[a] = -e[a];   // uniaxial: e and -e are the same axis
+  int flags = 0;
+  if (mt.grain) flags |= F_GRAIN;
+  if (mt.D0 != 0.0) flags |= F_DMI;
+  if (mt.aniso_cubic) flags |= F_CUBIC;
+  else if (mt.K1 != 0.0 || mt.K2 != 0.0 || mt.K1_cell) flags |= F_ANIS;
+  if (o.demag) flags |= F_DEMAG;
+  D.flags = flags;
+  const int l1 = mt.aniso_cubic ? 10 : 3, l2 = mt.aniso_cubic ? 21 : 10;
+
+  // energy coefficients (J)
+  EnergyCoef &E = H.ecoef;
+  std::memset(&E, 0, sizeof(E));
+  for (int a = 0; a < 3; ++a) E.cex[a] = H.V * mt.A0 / (H.h[a] * H.h[a]);
+  for (int a = 0; a < 2; ++a) E.cdmi[a] = H.V * mt.D0 / H.h[a];
+  E.V = H.V;
+  E.cubic = mt.aniso_cubic;
+  for (int a = 0; a < 3; ++a) { E.B[a] = d.B[a]; E.e[a] = e[a]; }
+  E.Ms0 = mt.Ms0;
+
+  if (!H.percell) {
+    const double kT = kB * d.T;
+    H.Tref = d.T;
+    const Thermo t = thermo(d.T, mt.Tc, H.mu, H.V, mt.Ms0, o.sigma_cap);
+    H.me = {t.me}; H.chi = {t.chi}; H.sigma = {t.sigma};
+    D.p2 = (float)(t.c2 / kT);
+    D.p4 = (float)(t.c4 / kT);
+    split_f(t.me2, D.me2h, D.me2l);
+    D.sigma = (float)t.sigma;
+    D.zee = (float)(H.V * mt.Ms0 / kT);
+    const double K1T = mt.K1 * std::pow(t.me, l1), K2T = mt.K2 * std::pow(t.me, l2);
+    D.k1 = (float)(H.V * K1T / kT);
+    D.k2 = (float)(H.V * K2T / kT);
+    for (int a = 0; a < 3; ++a) (&D.wx)[a] = (float)(E.cex[a] / kT);
+    D.cdx = (float)(E.cdmi[0] / kT);
+    D.cdy = (float)(E.cdmi[1] / kT);
+    D.ex = (float)e[0]; D.ey = (float)e[1]; D.ez = (float)e[2];
+    E.c2 = t.c2; E.c4 = t.c4; E.me2 = t.me2; E.K1T = K1T; E.K2T = K2T;
+    const double len = t.me > 0 ? t.me : rms_len_eq7(d.T, mt.Tc, H.mu, H.V, mt.Ms0);
+    H.init_len.assign((size_t)H.ncell, (float)len);
+  } else {
+    double Tref = 0;
+    for (long long i = 0; i < H.ncell; ++i) Tref = std::max(Tref, d.T_cell ? d.T_cell[i] : d.T);
+    H.Tref = Tref;
+    const double kTr = kB * Tref;
+    for (int a = 0; a < 3; ++a) (&D.wx)[a] = (float)(E.cex[a] / kTr);
+    D.cdx = (float)(E.cdmi[0] / kTr);
+    D.cdy = (float)(E.cdmi[1] / kTr);
+    H.me.assign((size_t)H.ncell, 0); H.chi.assign((size_t)H.ncell, 0); H.sigma.assign((size_t)H.ncell, 0);
+    H.etab.assign((size_t)H.ncell * 10, 0.0);
+    H.init_len.assign((size_t)H.ncell, 0.f);
+    const double cap = o.sigma_cap, mu = H.mu, V = H.V, K2 = mt.K2;
+    parallel_for(H.ncell, [&](long long i) {
+      const double T = d.T_cell ? d.T_cell[i] : d.T;
+      const double Tc = mt.Tc_cell ? mt.Tc_cell[i] : mt.Tc;
+      const double Ms = mt.Ms0_cell ? mt.Ms0_cell[i] : mt.Ms0;
+      const double K1 = mt.K1_cell ? mt.K1_cell[i] : mt.K1;
+      const Thermo t = thermo(T, Tc, mu, V, Ms, cap);
+      H.me[i] = t.me; H.chi[i] = t.chi; H.sigma[i] = t.sigma;
+      double ee[3] = {e[0], e[1], e[2]};
+      if (mt.e_A_cell) {
+        double n2 = 0;
+        for (int a = 0; a < 3; ++a) { ee[a] = mt.e_A_cell[3 * i + a]; n2 += ee[a] * ee[a]; }
+        n2 = std::sqrt(n2);
+        if (!(n2 > 0)) { ee[0] = 0; ee[1] = 0; ee[2] = 1; n2 = 1; }
+        for (int a = 0; a < 3; ++a) ee[a] /= n2;
+        if (ee[2] < 0) for (int a = 0; a < 3; ++a) ee[a] = -ee[a];
+      }
+      double *et = &H.etab[10 * i];
+      et[0] = t.c2; et[1] = t.c4; et[2] = t.me2; et[3] = Ms;
+      et[4] = K1 * std::pow(t.me, l1); et[5] = K2 * std::pow(t.me, l2);
+      et[6] = ee[0]; et[7] = ee[1]; et[8] = ee[2]; et[9] = kB * T;
+      H.init_len[i] = (float)(t.me > 0 ? t.me : 0.3);
+    });
+  }
+  if (mt.grain) {
+    H.grain.resize((size_t)H.ncell);
+    for (long long i = 0; i < H.ncell; ++i) H.grain[i] = (float)mt.grain[i];
+  }
+}
+
+// split-layout index of natural cell (i, row)
+inline long long split_index(const ChainDev &D, int i, int row) {
+  const int j = row % D.ny, k = row / D.ny;
+  const int col = (i + j + k) & 1;
+  return (long long)col * D.nrows * D.hx + (long long)row * D.hx + (i >> 1);
+}
+
+mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &chains, bool fp64,
+                            bool single) {
+  const size_t csz = fp64 ? 16 : 8;
+  std::vector<ChainDev> table;
+  long long spec_elems = 0;
+  int maxPx = 1, maxPyPz = 1;
+  for (int ci : chains) {
+    ChainDev D = c->ch[ci];
+    if (single) {
+      D.s_off = spec_elems;
+    }
+    spec_elems += 3LL * D.nrows * D.Sx;
+    table.push_back(D);
+    maxPx = std::max(maxPx, D.Px);
+    maxPyPz = std::max(maxPyPz, D.Py * D.Pz);
+  }
+  if (single) {
+    MMC_TRY(upload(c, &P.d_ch, table));
+  } else {
+    P.d_ch = c->d_ch;
+  }
+  // rows kernels
+  const int Gmax = std::max(maxPx / 8, 1);
+  int T = std::min(512, std::max(64, 3 * Gmax));
+  T = (T + 31) / 32 * 32;
+  if (T < Gmax) T = Gmax;
+  std::vector<int> rc;
+  std::vector<long long> rf;
+  size_t rsmem = 0;
+  for (size_t t = 0; t < table.size(); ++t) {
+    const ChainDev &D = table[t];
+    const int G = std::max(D.Px / 8, 1);
+    const int np = std::max(1, std::min(8, T / (3 * G)));
+    const int pairs = (D.nrows + 1) / 2;
+    const int nb = (pairs + np - 1) / np;
+    rf.push_back((long long)rc.size());
+    for (int b = 0; b < nb; ++b) rc.push_back((int)t);
+    rsmem = std::max(rsmem, (size_t)3 * np * D.Px * csz);
+  }
+  rf.push_back((long long)rc.size());
+  // cols kernel
+  int cc = 8;
+  while (cc > 1 && (size_t)3 * cc * maxPyPz * csz > 100 * 1024) cc >>= 1;
+  const size_t csmem = (size_t)3 * cc * maxPyPz * csz;
+  if (csmem > 200 * 1024) return fail(MMC_ERR_UNSUPPORTED, "column FFT plane too large for shared memory");
+  std::vector<int> colc;
+  std::vector<long long> colf;
+  int Gy = 1;
+  for (size_t t = 0; t < table.size(); ++t) {
+    const ChainDev &D = table[t];
+    Gy = std::max(Gy, std::max(D.Py / 8, std::max(D.Pz / 8, 1)));
+    const int nb = (D.Px / 2 + 1 + cc - 1) / cc;
+    colf.push_back((long long)colc.size());
+    for (int b = 0; b < nb; ++b) colc.push_back((int)t);
+  }
+  colf.push_back((long long)colc.size());
+  int Tc = std::min(512, std::max(128, 3 * cc * Gy));
+  Tc = (Tc + 31) / 32 * 32;
+  if (Tc < Gy) Tc = Gy;
+  MMC_TRY(upload(c, &P.rows_chain, rc));
+  MMC_TRY(upload(c, &P.rows_first, rf));
+  MMC_TRY(upload(c, &P.cols_chain, colc));
+  MMC_TRY(upload(c, &P.cols_first, colf));
+  P.rows_blocks = (int)rc.size();
+  P.rows_threads = T;
+  P.rows_smem = rsmem;
+  P.cols_blocks = (int)colc.size();
+  P.cols_threads = Tc;
+  P.cols_cc = cc;
+  P.cols_smem = csmem;
+  P.fp64 = fp64;
+  MMC_TRY(dalloc(c, &P.spec, (size_t)spec_elems * csz));
+  P.ready = true;
+  return MMC_OK;
+}
+
+DemagLaunch make_demag_launch(mmc_ctx *c, const DemagPlan &P, float4 *heff, double *Hd, int Hd_chain) {
+  DemagLaunch D;
+  D.chains = P.d_ch;
+  D.m = c->d_m;
+  D.tab = c->d_tab;
+  D.ms = c->d_ms;
+  D.spec = P.spec;
+  D.nhat = P.fp64 ? (const void *const *)c->d_nhat64 : (const void *const *)c->d_nhat32;
+  D.twiddle = P.fp64 ? c->d_tw64 : c->d_tw32;
+  D.heff = heff;
+  D.Hd = Hd;
+  D.Hd_chain = Hd_chain;
+  D.rows_chain = P.rows_chain;
+  D.rows_first = P.rows_first;
+  D.rows_blocks = P.rows_blocks;
+  D.rows_threads = P.rows_threads;
+  D.rows_smem = P.rows_smem;
+  D.cols_chain = P.cols_chain;
+  D.cols_first = P.cols_first;
+  D.cols_blocks = P.cols_blocks;
+  D.cols_threads = P.cols_threads;
+  D.cols_per_block = P.cols_cc;
+  D.cols_smem = P.cols_smem;
+  D.ev = nullptr;
+  return D;
+}
+
+mmc_status single_plan(mmc_ctx *c, int chain, DemagPlan **out) {
+  if ((int)c->single64.size() < c->nchains) c->single64.resize(c->nchains);
+  DemagPlan &P = c->single64[chain];
+  if (!P.ready) MMC_TRY(build_demag_plan(c, P, std::vector<int>{chain}, true, true));
+  *out = &P;
+  return MMC_OK;
+}
+
+SweepLaunch sweep_launch(mmc_ctx *c, int color, unsigned off, unsigned key0, unsigned key1) {
+  SweepLaunch P;
+  P.chains = c->d_ch;
+  P.st = c->d_st;
+  P.blk_chain = c->d_sw_chain;
+  P.blk_first = c->d_sw_first;
+  P.blk_base = 0;
+  P.nblocks = c->sw_blocks;
+  P.m = c->d_m;
+  P.heff = c->d_heff;
+  P.tab = c->d_tab;
+  P.sweep_base = c->d_sweep_base;
+  P.sweep_off = off;
+  P.key0 = key0;
+  P.key1 = key1;
+  P.color = color;
+  P.percell = c->any_percell;
+  P.omc_override = -1.f;
+  P.dec_dbg = nullptr;
+  P.acc_dbg = nullptr;
+  return P;
+}
+
+ObsLaunch obs_launch(mmc_ctx *c, int accumulate) {
+  ObsLaunch P;
+  P.chains = c->d_ch;
+  P.st = c->d_st;
+  P.blk_chain = c->d_obs_chain;
+  P.blk_first = c->d_obs_first;
+  P.nblocks = c->obs_blocks;
+  P.nchains = c->nchains;
+  P.m = c->d_m;
+  P.part = c->d_part;
+  P.hist = accumulate ? c->d_hist_acc : c->d_hist_cur;
+  P.bins = c->opt.hist_bins;
+  P.scale = (float)c->opt.hist_bins / (float)c->opt.hist_max;
+  P.out = c->d_obs_out;
+  P.accumulate = accumulate;
+  return P;
+}
+
+// optional per-kernel event timing (mmc_phase_times)
+struct PhaseTimer {
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, std::pair<int, int>>> marks;   // (kind, (ev0, ev1))
+  size_t used = 0;
+  cudaEvent_t next() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+};
+
+void issue_demag(mmc_ctx *c, PhaseTimer *pt = nullptr) {
+  Launch L = c->L();
+  DemagLaunch D = make_demag_launch(c, c->batch_plan, c->d_heff, nullptr, -1);
+  cudaEvent_t ev[4];
+  if (pt) {
+    int idx[4];
+    for (int k = 0; k < 4; ++k) { idx[k] = (int)pt->used; ev[k] = pt->next(); }
+    for (int k = 0; k < 3; ++k) pt->marks.push_back({k, {idx[k], idx[k + 1]}});
+    D.ev = ev;
+  }
+  launch_demag(L, D, c->batch_plan.fp64);
+}
+
+template <typename F>
+void timed(mmc_ctx *c, PhaseTimer *pt, int kind, F fn) {
+  if (!pt) { fn(); return; }
+  const int i0 = (int)pt->used;
+  cudaEventRecord(pt->next(), c->stream);
+  fn();
+  const int i1 = (int)pt->used;
+  cudaEventRecord(pt->next(), c->stream);
+  pt->marks.push_back({kind, {i0, i1}});
+}
+
+// k sweeps starting at global sweep index `start` (device base == start)
+void issue_block(mmc_ctx *c, int k, unsigned key0, unsigned key1, int sample_every, uint64_t start,
+                 PhaseTimer *pt = nullptr) {
+  Launch L = c->L();
+  for (int off = 0; off < k; ++off) {
+    if (c->any_demag) issue_demag(c, pt);
+    timed(c, pt, 3, [&] { launch_sweep_pass(L, sweep_launch(c, 0, (unsigned)off, key0, key1)); });
+    if (c->any_demag && c->opt.demag_per_pass) issue_demag(c, pt);
+    timed(c, pt, 3, [&] { launch_sweep_pass(L, sweep_launch(c, 1, (unsigned)off, key0, key1)); });
+    if (sample_every > 0 && (start + off + 1) % (uint64_t)sample_every == 0)
+      timed(c, pt, 4, [&] { launch_obs(L, obs_launch(c, 1)); });
+  }
+  const int adapt_now = ((start + k) % 100 == 0) ? 1 : 0;
+  timed(c, pt, 5, [&] {
+    launch_advance(L, c->d_st, c->nchains, (unsigned)k, c->d_sweep_base, adapt_now, c->opt.adapt, 1.f, 180.f);
+  });
+}
+
+mmc_status check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(MMC_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return MMC_OK;
+}
+
+mmc_status sweep_impl(mmc_ctx *c, int64_t n, uint64_t seed, int sample_every) {
+  if (!c) return fail(MMC_ERR_ARG, "null context");
+  if (n < 0) return fail(MMC_ERR_ARG, "negative sweep count");
+  if (sample_every < 0) return fail(MMC_ERR_ARG, "negative sample interval");
+  const unsigned key0 = (unsigned)(seed & 0xffffffffu), key1 = (unsigned)(seed >> 32);
+  const bool graph_ok = c->opt.use_graphs && (sample_every == 0 || 100 % sample_every == 0);
+  while (n > 0) {
+    const int k = (int)std::min<int64_t>(n, 100 - (int64_t)(c->host_sweep % 100));
+    if (k == 100 && graph_ok) {
+      GraphEntry *g = nullptr;
+      for (auto &e : c->graphs)
+        if (e.key0 == key0 && e.key1 == key1 && e.sample_every == sample_every) g = &e;
+      if (!g) {
+        GraphEntry e;
+        e.key0 = key0; e.key1 = key1; e.sample_every = sample_every;
+        const long long before = c->launches;
+        CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        issue_block(c, 100, key0, key1, sample_every, c->host_sweep);
+        cudaGraph_t graph;
+        cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+        if (ce != cudaSuccess) return fail(MMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        e.launches = c->launches - before;
+        c->launches = before;
+        ce = cudaGraphInstantiate(&e.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return fail(MMC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        c->graphs.push_back(e);
+        g = &c->graphs.back();
+      }
+      CUDA_TRY(cudaGraphLaunch(g->exec, c->stream));
+      c->launches += g->launches;
+    } else {
+      issue_block(c, k, key0, key1, sample_every, c->host_sweep);
+      MMC_TRY(check_launch());
+    }
+    c->host_sweep += (uint64_t)k;
+    n -= k;
+  }
+  return MMC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+extern "C" {
+
+mmc_status mmc_default_options(mmc_options *o) {
+  if (!o) return fail(MMC_ERR_ARG, "null options");
+  std::memset(o, 0, sizeof(*o));
+  o->adapt = 1;
+  o->theta0_deg = 30.0;
+  o->sigma_cap = 0.03;
+  o->hist_bins = 200;
+  o->hist_max = 1.0;
+  o->use_graphs = 1;
+  return MMC_OK;
+}
+
+void mmc_destroy(mmc_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+  for (void *p : c->allocs) cudaFree(p);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_options *opt,
+                      void *stream, mmc_ctx **out) {
+  if (!out) return fail(MMC_ERR_ARG, "null output pointer");
+  *out = nullptr;
+  if (!chains || nchains < 1) return fail(MMC_ERR_ARG, "need at least one chain");
+  mmc_options o;
+  if (opt) o = *opt; else mmc_default_options(&o);
+  if (o.hist_bins < 1 || o.hist_bins > kHistMax) return fail(MMC_ERR_ARG, "hist_bins must be in [1, 1024]");
+  if (!(o.hist_max > 0)) return fail(MMC_ERR_ARG, "hist_max must be > 0");
+  if (!(o.sigma_cap > 0 && o.sigma_cap < 1)) return fail(MMC_ERR_ARG, "sigma_cap must be in (0, 1)");
+  if (!(o.theta0_deg >= 1 && o.theta0_deg <= 180)) return fail(MMC_ERR_ARG, "theta0_deg must be in [1, 180]");
+  if (o.demag_cufft) return fail(MMC_ERR_UNSUPPORTED, "cuFFT demag path not available in this build");
+  for (int i = 0; i < nchains; ++i) MMC_TRY(validate(chains[i], o, i));
+
+  mmc_ctx *c = new mmc_ctx();
+  c->nchains = nchains;
+  c->opt = o;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreate(&c->stream);
+    if (e != cudaSuccess) {
+      delete c;
+      return fail(MMC_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    c->own_stream = true;
+  }
+  CUDA_TRY_OR(demag_set_smem_limits());
+  c->hc.resize(nchains);
+  c->ch.resize(nchains);
+  for (int i = 0; i < nchains; ++i) {
+    build_chain(c->hc[i], c->ch[i], chains[i], o, i);
+    c->any_demag |= (o.demag != 0);
+    c->any_percell |= c->hc[i].percell;
+    c->max_ncell = std::max(c->max_ncell, c->hc[i].ncell);
+    c->max_slots = std::max(c->max_slots, c->hc[i].slots);
+  }
+  // arenas
+  long long moff = 0, toff = 0, msoff = 0, soff = 0;
+  for (int i = 0; i < nchains; ++i) {
+    ChainDev &D = c->ch[i];
+    const long long S = c->hc[i].slots;
+    D.m_off = moff;
+    if (o.demag) D.h_off = moff;
+    moff += 2 * S;
+    if (c->hc[i].percell) {
+      D.t_off = toff;
+      toff += 6 * S;
+      D.ms_off = msoff;
+      msoff += 2 * S;
+    }
+    D.Px = D.Py = D.Pz = 1;
+    if (o.demag) {
+      D.Px = pad_len(D.nx, true);
+      D.Py = pad_len(D.ny, true);
+      D.Pz = pad_len(D.nz, D.nz > 1);
+      D.lx = ilog2(D.Px); D.ly = ilog2(D.Py); D.lz = ilog2(D.Pz);
+      D.Sx = (D.Px / 2 + 1 + 7) / 8 * 8;
+      D.s_off = soff;
+      soff += 3LL * D.nrows * D.Sx;
+      int found = -1;
+      for (size_t s = 0; s < c->specs.size(); ++s) {
+        const SpecSet &ss = c->specs[s];
+        if (ss.Px == D.Px && ss.Py == D.Py && ss.Pz == D.Pz && ss.h[0] == c->hc[i].h[0] &&
+            ss.h[1] == c->hc[i].h[1] && ss.h[2] == c->hc[i].h[2])
+          found = (int)s;
+      }
+      if (found < 0) {
+        SpecSet ss;
+        for (int a = 0; a < 3; ++a) ss.h[a] = c->hc[i].h[a];
+        ss.Px = D.Px; ss.Py = D.Py; ss.Pz = D.Pz;
+        c->specs.push_back(ss);
+        found = (int)c->specs.size() - 1;
+      }
+      D.spec = found;
+    }
+  }
+  c->m_total = moff;
+  c->tab_total = toff;
+  c->ms_total = msoff;
+
+  // initial state and per-cell tables, split layout
+  {
+    std::vector<float4> m((size_t)moff, make_float4(0, 0, 0, 0));
+    std::vector<float4> tab((size_t)std::max(toff, 1LL), make_float4(0, 0, 0, 0));
+    std::vector<float> ms((size_t)std::max(msoff, 1LL), 0.f);
+    std::vector<double> etab_all;
+    for (int ci = 0; ci < nchains; ++ci) {
+      const ChainDev &D = c->ch[ci];
+      const ChainHost &H = c->hc[ci];
+      const long long S = H.slots;
+      for (int row = 0; row < D.nrows; ++row)
+        for (int i = 0; i < D.nx; ++i) {
+          const long long nat = i + (long long)D.nx * row;
+          const long long si = split_index(D, i, row);
+          const float g = H.grain.empty() ? 0.f : H.grain[(size_t)nat];
+          m[(size_t)(D.m_off + si)] = make_float4(H.init_len[(size_t)nat], 0.f, 0.f, g);
+          if (H.percell) {
+            const double *et = &H.etab[10 * nat];
+            const double kT = et[9];
+            const float bs = (float)(kB * H.Tref / kT);
+            tab[(size_t)(D.t_off + si)] = make_float4((float)(et[0] / kT), (float)(et[1] / kT), (float)et[2],
+                                                      (float)H.sigma[(size_t)nat]);
+            tab[(size_t)(D.t_off + 2 * S + si)] =
+                make_float4((float)(H.V * et[3] / kT), (float)(H.V * et[4] / kT), (float)(H.V * et[5] / kT), bs);
+            tab[(size_t)(D.t_off + 4 * S + si)] = make_float4((float)et[6], (float)et[7], (float)et[8], 0.f);
+            ms[(size_t)(D.ms_off + si)] = (float)et[3];
+          }
+        }
+    }
+    MMC_TRY_OR(upload(c, &c->d_m, m));
+    if (toff) MMC_TRY_OR(upload(c, &c->d_tab, tab));
+    if (msoff) MMC_TRY_OR(upload(c, &c->d_ms, ms));
+    if (o.demag) MMC_TRY_OR(dalloc_t(c, &c->d_heff, (size_t)moff));
+  }
+  // tensor spectra and twiddles
+  if (o.demag) {
+    std::vector<void *> p32, p64;
+    for (auto &ss : c->specs) {
+      std::vector<double> sp;
+      demag_spectra(ss.h, ss.Px, ss.Py, ss.Pz, sp);
+      std::vector<float> spf(sp.begin(), sp.end());
+      float *d32 = nullptr;
+      double *d64 = nullptr;
+      MMC_TRY_OR(upload(c, &d32, spf));
+      MMC_TRY_OR(upload(c, &d64, sp));
+      ss.d32 = d32;
+      ss.d64 = d64;
+      p32.push_back(d32);
+      p64.push_back(d64);
+    }
+    MMC_TRY_OR(upload(c, &c->d_nhat32, p32));
+    MMC_TRY_OR(upload(c, &c->d_nhat64, p64));
+    std::vector<float2> tw32(kMaxFFT);
+    std::vector<double2> tw64(kMaxFFT);
+    for (int t = 0; t < kMaxFFT; ++t) {
+      const double a = -2.0 * kPi * t / kMaxFFT;
+      tw64[t] = make_double2(std::cos(a), std::sin(a));
+      tw32[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    float2 *t32 = nullptr;
+    double2 *t64 = nullptr;
+    MMC_TRY_OR(upload(c, &t32, tw32));
+    MMC_TRY_OR(upload(c, &t64, tw64));
+    c->d_tw32 = t32;
+    c->d_tw64 = t64;
+  }
+  MMC_TRY_OR(upload(c, &c->d_ch, c->ch));
+  {
+    std::vector<ChainState> st((size_t)nchains);
+    std::memset(st.data(), 0, st.size() * sizeof(ChainState));
+    for (auto &s : st) {
+      s.theta_deg = (float)o.theta0_deg;
+      s.omc = (float)(1.0 - std::cos(o.theta0_deg * kPi / 180.0));
+    }
+    MMC_TRY_OR(upload(c, &c->d_st, st));
+    MMC_TRY_OR(upload(c, &c->d_st_dbg, st));
+    std::vector<unsigned> z(1, 0u);
+    MMC_TRY_OR(upload(c, &c->d_sweep_base, z));
+    MMC_TRY_OR(upload(c, &c->d_dbg_sweep, z));
+  }
+  // block tables
+  {
+    std::vector<int> bc;
+    std::vector<long long> bf;
+    for (int ci = 0; ci < nchains; ++ci) {
+      bf.push_back((long long)bc.size());
+      const long long nb = (c->hc[ci].slots + kSweepBlock - 1) / kSweepBlock;
+      for (long long b = 0; b < nb; ++b) bc.push_back(ci);
+    }
+    bf.push_back((long long)bc.size());
+    c->sw_first = bf;
+    c->sw_blocks = (int)bc.size();
+    MMC_TRY_OR(upload(c, &c->d_sw_chain, bc));
+    MMC_TRY_OR(upload(c, &c->d_sw_first, bf));
+    std::vector<int> oc;
+    std::vector<long long> of;
+    for (int ci = 0; ci < nchains; ++ci) {
+      of.push_back((long long)oc.size());
+      const long long nb = (2 * c->hc[ci].slots + kReduceBlock * 4 - 1) / (kReduceBlock * 4);
+      for (long long b = 0; b < nb; ++b) oc.push_back(ci);
+    }
+    of.push_back((long long)oc.size());
+    c->obs_blocks = (int)oc.size();
+    MMC_TRY_OR(upload(c, &c->d_obs_chain, oc));
+    MMC_TRY_OR(upload(c, &c->d_obs_first, of));
+    const long long eblocks = (2 * c->max_slots + kReduceBlock * 4 - 1) / (kReduceBlock * 4);
+    MMC_TRY_OR(dalloc_t(c, &c->d_part, (size_t)8 * std::max<long long>(c->obs_blocks, eblocks)));
+    const size_t hn = (size_t)nchains * (o.hist_bins + 1);
+    MMC_TRY_OR(dalloc_t(c, &c->d_hist_acc, hn));
+    MMC_TRY_OR(dalloc_t(c, &c->d_hist_cur, hn));
+    CUDA_TRY_OR(cudaMemset(c->d_hist_acc, 0, hn * sizeof(unsigned long long)));
+    MMC_TRY_OR(dalloc_t(c, &c->d_obs_out, (size_t)8 * nchains));
+    MMC_TRY_OR(dalloc_t(c, &c->d_Hd, (size_t)3 * c->max_ncell));
+    MMC_TRY_OR(dalloc_t(c, &c->d_eout, 8));
+    MMC_TRY_OR(dalloc_t(c, &c->d_nat, (size_t)c->max_ncell));
+    MMC_TRY_OR(dalloc_t(c, &c->d_dec, (size_t)c->max_ncell));
+    MMC_TRY_OR(dalloc_t(c, &c->d_acc, (size_t)c->max_ncell));
+  }
+  if (o.demag) {
+    std::vector<int> all(nchains);
+    for (int i = 0; i < nchains; ++i) all[i] = i;
+    MMC_TRY_OR(build_demag_plan(c, c->batch_plan, all, o.demag_fp64 != 0, false));
+  }
+  CUDA_TRY_OR(cudaDeviceSynchronize());
+  *out = c;
+  return MMC_OK;
+}
+
+mmc_status mmc_create_single(const mmc_mesh *mesh, const double cellsize[3], const mmc_material *mat,
+                             double T, const double *T_cell, const mmc_options *opt, void *stream,
+                             mmc_ctx **out) {
+  if (!mesh || !cellsize || !mat) return fail(MMC_ERR_ARG, "null mesh, cell size or material");
+  mmc_chain_desc d;
+  std::memset(&d, 0, sizeof(d));
+  d.mesh = *mesh;
+  for (int a = 0; a < 3; ++a) d.cellsize[a] = cellsize[a];
+  d.material = *mat;
+  d.T = T;
+  d.T_cell = T_cell;
+  return mmc_create(&d, 1, opt, stream, out);
+}
+
+static mmc_status check_chain(mmc_ctx *c, int chain) {
+  if (!c) return fail(MMC_ERR_ARG, "null context");
+  if (chain < 0 || chain >= c->nchains) return fail(MMC_ERR_ARG, "chain index out of range");
+  return MMC_OK;
+}
+
+mmc_status mmc_set_field(mmc_ctx *c, int chain, const double B[3]) {
+  if (!c || !B) return fail(MMC_ERR_ARG, "null argument");
+  if (chain >= c->nchains) return fail(MMC_ERR_ARG, "chain index out of range");
+  for (int i = 0; i < c->nchains; ++i) {
+    if (chain >= 0 && i != chain) continue;
+    c->ch[i].Bx = (float)B[0];
+    c->ch[i].By = (float)B[1];
+    c->ch[i].Bz = (float)B[2];
+    for (int a = 0; a < 3; ++a) c->hc[i].ecoef.B[a] = B[a];
+    CUDA_TRY(cudaMemcpyAsync(c->d_ch + i, &c->ch[i], sizeof(ChainDev), cudaMemcpyHostToDevice, c->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MMC_OK;
+}
+
+mmc_status mmc_demag_update(mmc_ctx *c) {
+  if (!c) return fail(MMC_ERR_ARG, "null context");
+  if (!c->any_demag) return MMC_OK;
+  issue_demag(c);
+  MMC_TRY(check_launch());
+  return MMC_OK;
+}
+
+mmc_status mmc_set_m(mmc_ctx *c, int chain, const float *src, int is_device) {
+  MMC_TRY(check_chain(c, chain));
+  if (!src) return fail(MMC_ERR_ARG, "null source");
+  const long long n = c->hc[chain].ncell;
+  if (!is_device) {
+    for (long long i = 0; i < 4 * n; ++i)
+      if ((i & 3) != 3 && !std::isfinite(src[i])) return fail(MMC_ERR_NONFINITE, "non-finite value in m");
+    CUDA_TRY(cudaMemcpyAsync(c->d_nat, src, (size_t)n * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(c->d_nat, src, (size_t)n * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  Launch L = c->L();
+  launch_pack(L, c->d_ch, chain, c->hc[chain].slots, c->d_m, c->d_nat, 1);
+  MMC_TRY(check_launch());
+  MMC_TRY(mmc_demag_update(c));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MMC_OK;
+}
+
+mmc_status mmc_get_m(mmc_ctx *c, int chain, float *dst, int is_device) {
+  MMC_TRY(check_chain(c, chain));
+  if (!dst) return fail(MMC_ERR_ARG, "null destination");
+  const long long n = c->hc[chain].ncell;
+  Launch L = c->L();
+  launch_pack(L, c->d_ch, chain, c->hc[chain].slots, c->d_m, c->d_nat, 0);
+  MMC_TRY(check_launch());
+  CUDA_TRY(cudaMemcpyAsync(dst, c->d_nat, (size_t)n * sizeof(float4),
+                           is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MMC_OK;
+}
+
+mmc_status mmc_init_random(mmc_ctx *c, uint64_t seed, double len) {
+  if (!c) return fail(MMC_ERR_ARG, "null context");
+  Launch L = c->L();
+  float *d_len = nullptr;
+  for (int ci = 0; ci < c->nchains; ++ci) {
+    const ChainHost &H = c->hc[ci];
+    const float *lp = nullptr;
+    float lu = (float)len;
+    if (!(len > 0)) {
+      if (H.percell) {
+        if (!d_len) MMC_TRY(dalloc_t(c, &d_len, (size_t)c->max_ncell));
+        CUDA_TRY(cudaMemcpyAsync(d_len, H.init_len.data(), (size_t)H.ncell * sizeof(float),
+                                 cudaMemcpyHostToDevice, c->stream));
+        lp = d_len;
+      } else {
+        lu = H.init_len[0];
+      }
+    }
+    launch_init_random(L, c->d_ch, ci, H.slots, c->d_m, (unsigned)(seed & 0xffffffffu),
+                       (unsigned)(seed >> 32), lp, lu);
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  MMC_TRY(check_launch());
+  MMC_TRY(mmc_demag_update(c));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MMC_OK;
+}
+
+mmc_status mmc_sweep(mmc_ctx *c, int64_t n, uint64_t seed) {
+  MMC_TRY(sweep_impl(c, n, seed, 0));
+  return MMC_OK;
+}
+
+mmc_status mmc_sweep_sampled(mmc_ctx *c, int64_t n, uint64_t seed, int sample_every) {
+  if (sample_every < 1) return fail(MMC_ERR_ARG, "sample_every must be >= 1");
+  MMC_TRY(sweep_impl(c, n, seed, sample_every));
+  return MMC_OK;
+}
+
+mmc_status mmc_pass_debug(mmc_ctx *c, int chain, int color, uint32_t sweep, uint64_t seed,
+                          double theta_deg, float *dec, int8_t *acc) {
+  MMC_TRY(check_chain(c, chain));
+  if (color != 0 && color != 1) return fail(MMC_ERR_ARG, "color must be 0 or 1");
+  if (!(theta_deg >= 0 && theta_deg <= 180)) return fail(MMC_ERR_ARG, "theta_deg must be in [0, 180]");
+  const long long n = c->hc[chain].ncell;
+  CUDA_TRY(cudaMemcpyAsync(c->d_dbg_sweep, &sweep, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->d_dec, 0, (size_t)n * sizeof(float), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->d_acc, 0xff, (size_t)n, c->stream));
+  SweepLaunch P = sweep_launch(c, color, 0u, (unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32));
+  P.st = c->d_st_dbg;
+  P.sweep_base = c->d_dbg_sweep;
+  P.blk_base = (int)c->sw_first[chain];
+  P.nblocks = (int)(c->sw_first[chain + 1] - c->sw_first[chain]);
+  P.omc_override = (float)(1.0 - std::cos(theta_deg * kPi / 180.0));
+  P.dec_dbg = c->d_dec;
+  P.acc_dbg = c->d_acc;
+  Launch L = c->L();
+  launch_sweep_pass(L, P);
+  MMC_TRY(check_launch());
+  if (dec) CUDA_TRY(cudaMemcpyAsync(dec, c->d_dec, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  if (acc) CUDA_TRY(cudaMemcpyAsync(acc, c->d_acc, (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MMC_OK;
+}
+
+mmc_status mmc_observables(mmc_ctx *c, int chain, mmc_obs *out, int reset) {
+  MMC_TRY(check_chain(c, chain));
+  if (!out) return fail(MMC_ERR_ARG, "null output");
+  ChainState s;
+  CUDA_TRY(cudaMemcpyAsync(&s, c->d_st + chain, sizeof(ChainState), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const int nb = c->opt.hist_bins + 1;
+  std::vector<unsigned long long> h((size_t)nb, 0);
+  if (s.nsnap == 0) {
+    CUDA_TRY(cudaMemsetAsync(c->d_hist_cur, 0, (size_t)c->nchains * nb * sizeof(unsigned long long), c->stream));
+    Launch L = c->L();
+    launch_obs(L, obs_launch(c, 0));
+    MMC_TRY(check_launch());
+    double o[8];
+    CUDA_TRY(cudaMemcpyAsync(o, c->d_obs_out + 8 * chain, sizeof(o), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(h.data(), c->d_hist_cur + (size_t)chain * nb, nb * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const double nv = o[6] > 0 ? o[6] : 1.0;
+    for (int a = 0; a < 3; ++a) out->mean_m[a] = o[a] / nv;
+    out->mean_len = o[3] / nv;
+    out->mean_len2 = o[4] / nv;
+    out->nonfinite = (int64_t)o[5];
+    out->nsnap = 0;
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(h.data(), c->d_hist_acc + (size_t)chain * nb, nb * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const double ns = s.nsamples > 0 ? (double)s.nsamples : 1.0;
+    for (int a = 0; a < 3; ++a) out->mean_m[a] = s.sum_m[a] / ns;
+    out->mean_len = s.sum_len / ns;
+    out->mean_len2 = s.sum_len2 / ns;
+    out->nonfinite = (int64_t)s.nonfinite;
+    out->nsnap = (int64_t)s.nsnap;
+  }
+  if (out->hist)
+    for (int b = 0; b < nb; ++b) out->hist[b] = (int64_t)h[(size_t)b];
+  out->acc_rate = s.last_att > 0 ? (double)s.last_acc / (double)s.last_att : 0.0;
+  out->theta_deg = s.theta_deg;
+  out->sweeps = (int64_t)c->host_sweep;
+  if (reset) {
+    ChainState z = s;
+    z.sum_m[0] = z.sum_m[1] = z.sum_m[2] = 0;
+    z.sum_len = z.sum_len2 = 0;
+    z.nsamples = z.nsnap = z.nonfinite = 0;
+    CUDA_TRY(cudaMemcpyAsync(c->d_st + chain, &z, sizeof(ChainState), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->d_hist_acc + (size_t)chain * nb, 0, nb * sizeof(unsigned long long), c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  return MMC_OK;
+}
+
+static mmc_status demag64_chain(mmc_ctx *c, int chain) {
+  DemagPlan *P = nullptr;
+  MMC_TRY(single_plan(c, chain, &P));
+  Launch L = c->L();
+  launch_demag(L, make_demag_launch(c, *P, nullptr, c->d_Hd, 0), true);
+  return check_launch();
+}
+
+mmc_status mmc_demag_field(mmc_ctx *c, int chain, double *H) {
+  MMC_TRY(check_chain(c, chain));
+  if (!H) return fail(MMC_ERR_ARG, "null output");
+  const long long n = c->hc[chain].ncell;
+  if (!c->any_demag) {
+    std::memset(H, 0, (size_t)n * 3 * sizeof(double));
+    return MMC_OK;
+  }
+  MMC_TRY(demag64_chain(c, chain));
+  CUDA_TRY(cudaMemcpyAsync(H, c->d_Hd, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MMC_OK;
+}
+
+mmc_status mmc_energy(mmc_ctx *c, int chain, double out[7]) {
+  MMC_TRY(check_chain(c, chain));
+  if (!out) return fail(MMC_ERR_ARG, "null output");
+  const ChainHost &H = c->hc[chain];
+  if (c->any_demag) MMC_TRY(demag64_chain(c, chain));
+  double *etab = nullptr;
+  if (H.percell) {
+    if (!c->d_etab) MMC_TRY(dalloc_t(c, &c->d_etab, (size_t)10 * c->max_ncell));
+    CUDA_TRY(cudaMemcpyAsync(c->d_etab, H.etab.data(), H.etab.size() * sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream));
+    etab = c->d_etab;
+  }
+  Launch L = c->L();
+  launch_energy(L, c->d_ch, chain, H.slots, c->d_m, etab, c->any_demag ? c->d_Hd : nullptr, H.ecoef, c->d_part,
+                c->d_eout);
+  MMC_TRY(check_launch());
+  CUDA_TRY(cudaMemcpyAsync(out, c->d_eout, 7 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MMC_OK;
+}
+
+mmc_status mmc_tables(mmc_ctx *c, int chain, double *me, double *chi, double *sigma) {
+  MMC_TRY(check_chain(c, chain));
+  const ChainHost &H = c->hc[chain];
+  for (long long i = 0; i < H.ncell; ++i) {
+    const size_t k = H.percell ? (size_t)i : 0;
+    if (me) me[i] = H.me[k];
+    if (chi) chi[i] = H.chi[k];
+    if (sigma) sigma[i] = H.sigma[k];
+  }
+  return MMC_OK;
+}
+
+mmc_status mmc_energy_grad(mmc_ctx *c, int chain, const void *m, int fp64, double E[7], void *dEdm,
+                           double dEdp[5]) {
+  (void)m; (void)fp64; (void)E; (void)dEdm; (void)dEdp;
+  MMC_TRY(check_chain(c, chain));
+  return fail(MMC_ERR_UNSUPPORTED, "energy gradient not available in this build");
+}
+
+mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[6], int64_t count[6]) {
+  if (!c || !ms || !count) return fail(MMC_ERR_ARG, "null argument");
+  if (n < 0) return fail(MMC_ERR_ARG, "negative sweep count");
+  for (int k = 0; k < 6; ++k) { ms[k] = 0; count[k] = 0; }
+  const unsigned key0 = (unsigned)(seed & 0xffffffffu), key1 = (unsigned)(seed >> 32);
+  PhaseTimer pt;
+  mmc_status st = MMC_OK;
+  while (n > 0 && st == MMC_OK) {
+    const int k = (int)std::min<int64_t>(n, 100 - (int64_t)(c->host_sweep % 100));
+    pt.used = 0;
+    pt.marks.clear();
+    issue_block(c, k, key0, key1, 0, c->host_sweep, &pt);
+    st = check_launch();
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { st = fail(MMC_ERR_CUDA, cudaGetErrorString(e)); break; }
+    for (auto &mk : pt.marks) {
+      float t = 0;
+      cudaEventElapsedTime(&t, pt.pool[mk.second.first], pt.pool[mk.second.second]);
+      ms[mk.first] += t;
+      count[mk.first] += 1;
+    }
+    c->host_sweep += (uint64_t)k;
+    n -= k;
+  }
+  for (auto e : pt.pool) cudaEventDestroy(e);
+  return st;
+}
+
+int64_t mmc_kernel_launches(const mmc_ctx *c) { return c ? c->launches : 0; }
+int mmc_nchains(const mmc_ctx *c) { return c ? c->nchains : 0; }
+int64_t mmc_ncell(const mmc_ctx *c, int chain) {
+  if (!c || chain < 0 || chain >= c->nchains) return 0;
+  return c->hc[chain].ncell;
+}
+
+struct CkptHeader {
+  char magic[8];
+  int32_t version, nchains;
+  int64_t m_total;
+  uint64_t host_sweep;
+};
+
+mmc_status mmc_checkpoint(mmc_ctx *c, void *buf, size_t *len) {
+  if (!c || !len) return fail(MMC_ERR_ARG, "null argument");
+  const size_t need = sizeof(CkptHeader) + (size_t)c->nchains * (sizeof(ChainState) + 3 * sizeof(float)) +
+                      (size_t)c->m_total * sizeof(float4);
+  if (!buf) {
+    *len = need;
+    return MMC_OK;
+  }
+  if (*len < need) return fail(MMC_ERR_ARG, "checkpoint buffer too small");
+  char *p = (char *)buf;
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "MMCCKPT", 8);
+  h.version = 1;
+  h.nchains = c->nchains;
+  h.m_total = c->m_total;
+  h.host_sweep = c->host_sweep;
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  CUDA_TRY(cudaMemcpyAsync(p, c->d_st, (size_t)c->nchains * sizeof(ChainState), cudaMemcpyDeviceToHost, c->stream));
+  p += (size_t)c->nchains * sizeof(ChainState);
+  for (int i = 0; i < c->nchains; ++i) {
+    const float B[3] = {c->ch[i].Bx, c->ch[i].By, c->ch[i].Bz};
+    std::memcpy(p, B, sizeof(B));
+    p += sizeof(B);
+  }
+  CUDA_TRY(cudaMemcpyAsync(p, c->d_m, (size_t)c->m_total * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  *len = need;
+  return MMC_OK;
+}
+
+mmc_status mmc_restore(mmc_ctx *c, const void *buf, size_t len) {
+  if (!c || !buf) return fail(MMC_ERR_ARG, "null argument");
+  const size_t need = sizeof(CkptHeader) + (size_t)c->nchains * (sizeof(ChainState) + 3 * sizeof(float)) +
+                      (size_t)c->m_total * sizeof(float4);
+  if (len < need) return fail(MMC_ERR_ARG, "checkpoint too short");
+  const char *p = (const char *)buf;
+  CkptHeader h;
+  std::memcpy(&h, p, sizeof(h));
+  if (std::memcmp(h.magic, "MMCCKPT", 8) != 0 || h.version != 1 || h.nchains != c->nchains ||
+      h.m_total != c->m_total)
+    return fail(MMC_ERR_ARG, "checkpoint does not match this context");
+  p += sizeof(h);
+  CUDA_TRY(cudaMemcpyAsync(c->d_st, p, (size_t)c->nchains * sizeof(ChainState), cudaMemcpyHostToDevice, c->stream));
+  p += (size_t)c->nchains * sizeof(ChainState);
+  for (int i = 0; i < c->nchains; ++i) {
+    float B[3];
+    std::memcpy(B, p, sizeof(B));
+    p += sizeof(B);
+    c->ch[i].Bx = B[0]; c->ch[i].By = B[1]; c->ch[i].Bz = B[2];
+    for (int a = 0; a < 3; ++a) c->hc[i].ecoef.B[a] = B[a];
+  }
+  CUDA_TRY(cudaMemcpyAsync(c->d_ch, c->ch.data(), c->ch.size() * sizeof(ChainDev), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(c->d_m, p, (size_t)c->m_total * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
+  c->host_sweep = h.host_sweep;
+  const unsigned base = (unsigned)h.host_sweep;
+  CUDA_TRY(cudaMemcpyAsync(c->d_sweep_base, &base, sizeof(base), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MMC_OK;
+}
+
+const char *mmc_status_str(mmc_status s) {
+  switch (s) {
+    case MMC_OK: return "ok";
+    case MMC_ERR_ARG: return "invalid argument";
+    case MMC_ERR_CUDA: return "CUDA error";
+    case MMC_ERR_TIMEOUT: return "device wait timed out";
+    case MMC_ERR_NONFINITE: return "non-finite value";
+    case MMC_ERR_UNSUPPORTED: return "unsupported combination";
+    case MMC_ERR_NOMEM: return "out of memory";
+  }
+  return "unknown status";
+}
+
+const char *mmc_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

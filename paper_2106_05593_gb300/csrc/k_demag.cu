@@ -1,0 +1,313 @@
+// Demagnetizing field by zero-padded FFT convolution with the Newell tensor
+// (Sec. III, Eq. 14): H_d = -IFFT( N^ . FFT(Ms0 m) ), for every chain of a batch.
+//
+// Three kernels per update, each batched over chains:
+//  rows_fwd  two rows per sequence pair: the real rows Mx, My of row r, of row
+//            r+1, and (Mz_r, Mz_{r+1}) are packed as three complex sequences,
+//            zero padded to Px, transformed, and split into the half spectra
+//            (kx in [0, Px/2]) of the six real rows.  Output: spectrum buffer
+//            S[comp][row][kx] (row-major, stride Sx).
+//  cols      C adjacent kx columns per block: FFT along y (and z), pointwise
+//            H^ = -N^ M^ with the real tensor spectra (symmetric quadrant),
+//            inverse transforms, rows outside the mesh dropped; in place in S.
+//  rows_inv  inverse row transforms (two real rows per complex sequence),
+//            crop to nx, scale by 1/(Px Py Pz), and write the sweep's static
+//            field h_eff = zee (B + mu0 H_d) in the split layout, optionally
+//            also H_d in FP64, natural order.
+// The FFTs are the shared-memory Stockham transforms of fft.cuh; R = float or
+// double selects the arithmetic of the whole convolution.
+#include "fft.cuh"
+#include "mmc_internal.h"
+
+namespace mmc {
+
+template <typename R>
+struct DemagArgs {
+  using C = typename Cx<R>::T;
+  const ChainDev *chains;
+  const int *blk_chain;
+  const long long *blk_first;
+  const float4 *m;
+  const float4 *tab;
+  const float *ms;
+  C *S;
+  const R *const *nhat;
+  const C *tw;
+  float4 *heff;
+  double *Hd;
+  int Hd_chain;
+};
+
+__device__ __forceinline__ int pairs_per_block(int Px) {
+  const int G = Px >= 8 ? Px >> 3 : 1;
+  int np = (int)blockDim.x / (3 * G);
+  return np < 1 ? 1 : (np > 8 ? 8 : np);
+}
+
+// M = Ms0 m of cell (x, row r) from the split layout
+__device__ __forceinline__ float3 load_M(const ChainDev &ch, const float4 *m, const float *ms,
+                                         int r, int x) {
+  const int j = r % ch.ny, k = r / ch.ny;
+  const int col = (x + j + k) & 1;
+  const long long S = (long long)ch.nrows * ch.hx;
+  const long long idx = (long long)col * S + (long long)r * ch.hx + (x >> 1);
+  const float4 v = m[ch.m_off + idx];
+  const float Ms = ch.ms_off >= 0 ? ms[ch.ms_off + idx] : ch.Ms0;
+  return make_float3(Ms * v.x, Ms * v.y, Ms * v.z);
+}
+
+template <typename R>
+__global__ void k_rows_fwd(DemagArgs<R> A) {
+  using C = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *buf = reinterpret_cast<C *>(smem_raw);
+  const int c = A.blk_chain[blockIdx.x];
+  const ChainDev &ch = A.chains[c];
+  const int Px = ch.Px, lx = ch.lx, nx = ch.nx, nrows = ch.nrows, Sx = ch.Sx;
+  const int np = pairs_per_block(Px);
+  const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
+  const int totpairs = (nrows + 1) / 2;
+  for (int idx = threadIdx.x; idx < np * Px; idx += blockDim.x) {
+    const int qq = idx >> lx, x = idx & (Px - 1);
+    const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
+    float3 M0 = make_float3(0.f, 0.f, 0.f), M1 = M0;
+    if (pr < totpairs && x < nx) {
+      M0 = load_M(ch, A.m, A.ms, r0, x);
+      if (r1 < nrows) M1 = load_M(ch, A.m, A.ms, r1, x);
+    }
+    C z;
+    z.x = M0.x; z.y = M0.y; buf[(3 * qq + 0) * Px + x] = z;
+    z.x = M1.x; z.y = M1.y; buf[(3 * qq + 1) * Px + x] = z;
+    z.x = M0.z; z.y = M1.z; buf[(3 * qq + 2) * Px + x] = z;
+  }
+  __syncthreads();
+  fft_smem<C>(buf, lx, 3 * np, SeqMap{1, Px, 0, 1}, A.tw, false);
+  const int half = Px / 2 + 1;
+  const long long plane = (long long)nrows * Sx;
+  C *S = A.S + ch.s_off;
+  for (int idx = threadIdx.x; idx < np * half; idx += blockDim.x) {
+    const int qq = idx / half, kx = idx - qq * half;
+    const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
+    if (pr >= totpairs) continue;
+    const int km = (Px - kx) & (Px - 1);
+#pragma unroll
+    for (int sq = 0; sq < 3; ++sq) {
+      const C Z = buf[(3 * qq + sq) * Px + kx], Zm = buf[(3 * qq + sq) * Px + km];
+      // a = (Z + conj(Zm)) / 2, b = (Z - conj(Zm)) / (2i)
+      C a, b;
+      a.x = (R)0.5 * (Z.x + Zm.x); a.y = (R)0.5 * (Z.y - Zm.y);
+      b.x = (R)0.5 * (Z.y + Zm.y); b.y = (R)0.5 * (Zm.x - Z.x);
+      if (sq == 0) {
+        S[0 * plane + (long long)r0 * Sx + kx] = a;
+        S[1 * plane + (long long)r0 * Sx + kx] = b;
+      } else if (sq == 1) {
+        if (r1 < nrows) {
+          S[0 * plane + (long long)r1 * Sx + kx] = a;
+          S[1 * plane + (long long)r1 * Sx + kx] = b;
+        }
+      } else {
+        S[2 * plane + (long long)r0 * Sx + kx] = a;
+        if (r1 < nrows) S[2 * plane + (long long)r1 * Sx + kx] = b;
+      }
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_cols(DemagArgs<R> A, int CC) {
+  using C = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *buf = reinterpret_cast<C *>(smem_raw);
+  const int c = A.blk_chain[blockIdx.x];
+  const ChainDev &ch = A.chains[c];
+  const int Px = ch.Px, Py = ch.Py, Pz = ch.Pz, ly = ch.ly, lz = ch.lz;
+  const int ny = ch.ny, nz = ch.nz, nrows = ch.nrows, Sx = ch.Sx;
+  const int kx0 = (int)(blockIdx.x - A.blk_first[c]) * CC;
+  const int ncolq = Px / 2 + 1;
+  const int PyPz = Py * Pz;
+  const long long plane = (long long)nrows * Sx;
+  C *S = A.S + ch.s_off;
+  const int tot = 3 * CC * PyPz;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) { buf[idx].x = 0; buf[idx].y = 0; }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 3 * nrows * CC; idx += blockDim.x) {
+    const int col = idx % CC, rest = idx / CC;
+    const int r = rest % nrows, comp = rest / nrows;
+    const int kx = kx0 + col;
+    if (kx < ncolq) {
+      const int j = r % ny, k = r / ny;
+      buf[((comp * CC + col) * Pz + k) * Py + j] = S[comp * plane + (long long)r * Sx + kx];
+    }
+  }
+  __syncthreads();
+  fft_smem<C>(buf, ly, 3 * CC * nz, SeqMap{nz, PyPz, Py, 1}, A.tw, false);
+  if (Pz > 1) fft_smem<C>(buf, lz, 3 * CC * Py, SeqMap{Py, PyPz, 1, Py}, A.tw, false);
+  // pointwise H^ = -N^ M^ with the real quadrant spectra
+  const int qx = Px / 2 + 1, qy = Py / 2 + 1, qz = Pz / 2 + 1;
+  const long long Q = (long long)qx * qy * qz;
+  const R *nh = A.nhat[ch.spec];
+  for (int idx = threadIdx.x; idx < CC * PyPz; idx += blockDim.x) {
+    const int col = idx / PyPz, rem = idx - col * PyPz;
+    const int kz = rem / Py, ky = rem - kz * Py;
+    const int kx = kx0 + col;
+    if (kx >= ncolq) continue;
+    const int kyq = ky <= Py / 2 ? ky : Py - ky;
+    const int kzq = kz <= Pz / 2 ? kz : Pz - kz;
+    const R sy = ky <= Py / 2 ? (R)1 : (R)-1;
+    const R sz = kz <= Pz / 2 ? (R)1 : (R)-1;
+    const long long qi = ((long long)kzq * qy + kyq) * qx + kx;
+    const R Nxx = nh[qi], Nyy = nh[Q + qi], Nzz = nh[2 * Q + qi], Nxy = sy * nh[3 * Q + qi];
+    R Nxz = 0, Nyz = 0;
+    if (Pz > 1) { Nxz = sz * nh[4 * Q + qi]; Nyz = sy * sz * nh[5 * Q + qi]; }
+    const int b0 = ((0 * CC + col) * Pz + kz) * Py + ky;
+    const int b1 = ((1 * CC + col) * Pz + kz) * Py + ky;
+    const int b2 = ((2 * CC + col) * Pz + kz) * Py + ky;
+    const C Mx = buf[b0], My = buf[b1], Mz = buf[b2];
+    C hx_, hy_, hz_;
+    hx_.x = -(Nxx * Mx.x + Nxy * My.x + Nxz * Mz.x);
+    hx_.y = -(Nxx * Mx.y + Nxy * My.y + Nxz * Mz.y);
+    hy_.x = -(Nxy * Mx.x + Nyy * My.x + Nyz * Mz.x);
+    hy_.y = -(Nxy * Mx.y + Nyy * My.y + Nyz * Mz.y);
+    hz_.x = -(Nxz * Mx.x + Nyz * My.x + Nzz * Mz.x);
+    hz_.y = -(Nxz * Mx.y + Nyz * My.y + Nzz * Mz.y);
+    buf[b0] = hx_; buf[b1] = hy_; buf[b2] = hz_;
+  }
+  __syncthreads();
+  if (Pz > 1) fft_smem<C>(buf, lz, 3 * CC * Py, SeqMap{Py, PyPz, 1, Py}, A.tw, true);
+  fft_smem<C>(buf, ly, 3 * CC * nz, SeqMap{nz, PyPz, Py, 1}, A.tw, true);
+  for (int idx = threadIdx.x; idx < 3 * nrows * CC; idx += blockDim.x) {
+    const int col = idx % CC, rest = idx / CC;
+    const int r = rest % nrows, comp = rest / nrows;
+    const int kx = kx0 + col;
+    if (kx < ncolq) {
+      const int j = r % ny, k = r / ny;
+      S[comp * plane + (long long)r * Sx + kx] = buf[((comp * CC + col) * Pz + k) * Py + j];
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_rows_inv(DemagArgs<R> A) {
+  using C = typename Cx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *buf = reinterpret_cast<C *>(smem_raw);
+  const int c = A.blk_chain[blockIdx.x];
+  const ChainDev &ch = A.chains[c];
+  const int Px = ch.Px, lx = ch.lx, nx = ch.nx, nrows = ch.nrows, Sx = ch.Sx;
+  const int np = pairs_per_block(Px);
+  const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
+  const int totpairs = (nrows + 1) / 2;
+  const int half = Px / 2 + 1;
+  const long long plane = (long long)nrows * Sx;
+  const C *S = A.S + ch.s_off;
+  for (int idx = threadIdx.x; idx < np * half; idx += blockDim.x) {
+    const int qq = idx / half, kx = idx - qq * half;
+    const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
+    C a[3], b[3];
+    for (int t = 0; t < 3; ++t) { a[t].x = 0; a[t].y = 0; b[t] = a[t]; }
+    if (pr < totpairs) {
+      a[0] = S[0 * plane + (long long)r0 * Sx + kx];
+      b[0] = S[1 * plane + (long long)r0 * Sx + kx];
+      a[2] = S[2 * plane + (long long)r0 * Sx + kx];
+      if (r1 < nrows) {
+        a[1] = S[0 * plane + (long long)r1 * Sx + kx];
+        b[1] = S[1 * plane + (long long)r1 * Sx + kx];
+        b[2] = S[2 * plane + (long long)r1 * Sx + kx];
+      }
+    }
+    const bool edge = (kx == 0) || (2 * kx == Px);
+#pragma unroll
+    for (int sq = 0; sq < 3; ++sq) {
+      // z = a + i b for two real rows with Hermitian half spectra a, b
+      C zk, zm;
+      if (edge) {
+        zk.x = a[sq].x; zk.y = b[sq].x;
+        buf[(3 * qq + sq) * Px + kx] = zk;
+      } else {
+        zk.x = a[sq].x - b[sq].y; zk.y = a[sq].y + b[sq].x;
+        zm.x = a[sq].x + b[sq].y; zm.y = b[sq].x - a[sq].y;
+        buf[(3 * qq + sq) * Px + kx] = zk;
+        buf[(3 * qq + sq) * Px + (Px - kx)] = zm;
+      }
+    }
+  }
+  __syncthreads();
+  fft_smem<C>(buf, lx, 3 * np, SeqMap{1, Px, 0, 1}, A.tw, true);
+  const R scale = (R)1 / ((R)Px * (R)ch.Py * (R)ch.Pz);
+  const long long Sl = (long long)nrows * ch.hx;
+  const bool percell = ch.t_off >= 0;
+  const double mu0d = mu0;
+  for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
+    const int qq = idx / nx, x = idx - qq * nx;
+    const int pr = pair0 + qq;
+    if (pr >= totpairs) continue;
+    const C z0 = buf[(3 * qq + 0) * Px + x], z1 = buf[(3 * qq + 1) * Px + x], z2 = buf[(3 * qq + 2) * Px + x];
+    for (int h = 0; h < 2; ++h) {
+      const int r = 2 * pr + h;
+      if (r >= nrows) break;
+      const R Hx = (h == 0 ? z0.x : z1.x) * scale;
+      const R Hy = (h == 0 ? z0.y : z1.y) * scale;
+      const R Hz = (h == 0 ? z2.x : z2.y) * scale;
+      const int j = r % ch.ny, k = r / ch.ny;
+      const int colr = (x + j + k) & 1;
+      const long long li = (long long)colr * Sl + (long long)r * ch.hx + (x >> 1);
+      if (A.heff) {
+        const float zee = percell ? A.tab[ch.t_off + 2 * Sl + li].x : ch.zee;
+        const float mu0f = (float)mu0d;
+        A.heff[ch.h_off + li] = make_float4(zee * (ch.Bx + mu0f * (float)Hx), zee * (ch.By + mu0f * (float)Hy),
+                                            zee * (ch.Bz + mu0f * (float)Hz), 0.f);
+      }
+      if (A.Hd && c == A.Hd_chain) {
+        const long long nat = x + (long long)nx * r;
+        A.Hd[3 * nat + 0] = (double)Hx;
+        A.Hd[3 * nat + 1] = (double)Hy;
+        A.Hd[3 * nat + 2] = (double)Hz;
+      }
+    }
+  }
+}
+
+template <typename R>
+void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
+  using C = typename Cx<R>::T;
+  DemagArgs<R> A;
+  A.chains = P.chains; A.m = P.m; A.tab = P.tab; A.ms = P.ms;
+  A.S = reinterpret_cast<C *>(P.spec);
+  A.nhat = reinterpret_cast<const R *const *>(P.nhat);
+  A.tw = reinterpret_cast<const C *>(P.twiddle);
+  A.heff = P.heff; A.Hd = P.Hd; A.Hd_chain = P.Hd_chain;
+  A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
+  if (P.ev) cudaEventRecord(P.ev[0], L.stream);
+  k_rows_fwd<R><<<P.rows_blocks, P.rows_threads, P.rows_smem, L.stream>>>(A);
+  if (P.ev) cudaEventRecord(P.ev[1], L.stream);
+  A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
+  k_cols<R><<<P.cols_blocks, P.cols_threads, P.cols_smem, L.stream>>>(A, P.cols_per_block);
+  if (P.ev) cudaEventRecord(P.ev[2], L.stream);
+  A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
+  k_rows_inv<R><<<P.rows_blocks, P.rows_threads, P.rows_smem, L.stream>>>(A);
+  if (P.ev) cudaEventRecord(P.ev[3], L.stream);
+  *L.counter += 3;
+}
+
+void launch_demag(const Launch &L, const DemagLaunch &P, bool fp64) {
+  if (fp64) launch_demag_impl<double>(L, P);
+  else launch_demag_impl<float>(L, P);
+}
+
+cudaError_t demag_set_smem_limits() {
+  cudaError_t e = cudaSuccess;
+  const int lim = 200 * 1024;
+  e = cudaFuncSetAttribute(k_rows_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_rows_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_cols<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_cols<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_rows_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_rows_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+}  // namespace mmc

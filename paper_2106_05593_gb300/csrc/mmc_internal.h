@@ -1,0 +1,181 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the C ABI (include/mmc.h is).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace mmc {
+
+// CODATA 2018 SI values
+constexpr double kB = 1.380649e-23;
+constexpr double muB = 9.2740100783e-24;
+constexpr double mu0 = 1.25663706212e-6;
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kMaxFFT = 4096;        // largest padded FFT length per axis (twiddle table length)
+constexpr int kHistMax = 1024;       // largest histogram bin count
+constexpr int kSweepBlock = 256;     // threads per sweep-pass block
+constexpr int kReduceBlock = 256;
+
+// chain flag bits
+enum : int {
+  F_GRAIN = 2,     // grain ids in m.w, bonds between grains scaled
+  F_DMI = 4,
+  F_ANIS = 8,      // uniaxial anisotropy present
+  F_CUBIC = 16,    // cubic anisotropy
+  F_DEMAG = 32,    // h_eff array present (demag on)
+};
+
+// Per-chain constants, device resident.  Energies are in units of kT (of the
+// chain temperature, or of a reference T_ref for per-cell chains, whose table
+// carries bscale = T_ref / T_cell for the bond weights).
+struct ChainDev {
+  int nx, ny, nz;
+  int hx;             // sublattice slots per row: (nx + 1) / 2
+  int nrows;          // ny * nz
+  int pbc;            // bit a: axis a periodic
+  int flags;
+  int chain;          // chain index (Philox counter word 2)
+  long long ncell;
+  long long m_off;    // float4 index of the red array in the m arena; black follows
+  long long h_off;    // float4 index of the red h_eff array (split layout), or -1
+  long long t_off;    // float4 index of the per-cell table (3 x 2 x nrows*hx float4), or -1
+  long long ms_off;   // float index of per-cell Ms0 (split layout), or -1
+  long long s_off;    // complex element index of the spectrum buffer
+  int spec;           // tensor-spectrum set index
+  int Px, Py, Pz;     // padded FFT sizes
+  int lx, ly, lz;     // log2 of the padded sizes
+  int Sx;             // row stride (complex elements) of the spectrum buffer
+  float wx, wy, wz;   // exchange bond weights V A0 / (h^2 kT)
+  float cdx, cdy;     // DMI weights V D0 / (h kT)
+  float p2, p4;       // longitudinal: dF/kT = dq (p2 + p4 (2 (|m|^2 - me2) + dq))
+  float me2h, me2l;   // m_e^2 as a float-float pair (0 at and above Tc)
+  float sigma;        // length-move width (Eq. 13, capped)
+  float zee;          // V Ms0 / kT  (1/T)
+  float k1, k2;       // V K1(T) / kT, V K2(T) / kT
+  float ex, ey, ez;   // easy axis
+  float Bx, By, Bz;   // applied field (T)
+  float Ms0;          // A/m (uniform chains)
+  float gscale;       // bond scale across grains
+};
+
+// Per-chain mutable state, device resident (plain data; part of checkpoints).
+struct ChainState {
+  unsigned long long win_acc;    // accepted moves in the current window
+  unsigned long long win_att;    // attempted moves in the current window
+  unsigned long long last_acc;   // of the last completed window
+  unsigned long long last_att;
+  float theta_deg;
+  float omc;                     // 1 - cos(theta)
+  double sum_m[3];               // snapshot accumulators
+  double sum_len, sum_len2;
+  unsigned long long nsamples;
+  unsigned long long nsnap;
+  unsigned long long nonfinite;
+};
+
+// FP64 energy coefficients of a uniform chain (J), see k_reduce.cu
+struct EnergyCoef {
+  double cex[3];      // V A0 / h_a^2
+  double cdmi[2];     // V D0 / h_a
+  double c2, c4, me2; // F_l = c2 m^2 + c4 (m^2 - me2)^2
+  double Ms0, K1T, K2T, e[3];
+  double B[3];
+  double V;
+  int cubic;
+};
+
+// ---------------------------------------------------------------------------
+// host-side physics (host_physics.cpp)
+double langevin(double x);
+double langevin_deriv(double x);
+double me_of_T(double T, double Tc);
+double chi_of_T(double T, double Tc, double mu);
+double sigma_of_T(double T, double Tc, double mu, double V, double Ms0, double cap);
+void long_coeffs(double T, double Tc, double mu, double V, double Ms0, double *c2, double *c4);
+double rms_len_eq7(double T, double Tc, double mu, double V, double Ms0);
+void demag_tensor(const double h[3], const double R[3], double out[6]);
+void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double> &out);
+
+// ---------------------------------------------------------------------------
+// launches
+struct Launch {
+  cudaStream_t stream;
+  long long *counter;   // kernel launch counter
+};
+
+struct SweepLaunch {
+  const ChainDev *chains;
+  ChainState *st;
+  const int *blk_chain;
+  const long long *blk_first;
+  int blk_base;                 // first block of this launch in the block tables
+  int nblocks;
+  float4 *m;
+  const float4 *heff;
+  const float4 *tab;
+  const unsigned *sweep_base;
+  unsigned sweep_off;
+  unsigned key0, key1;
+  int color;
+  bool percell;
+  float omc_override;
+  float *dec_dbg;
+  signed char *acc_dbg;
+};
+void launch_sweep_pass(const Launch &L, const SweepLaunch &P);
+void launch_advance(const Launch &L, ChainState *st, int nchains, unsigned by, unsigned *sweep_base,
+                    int adapt_now, int adapt, float tmin, float tmax);
+
+struct DemagLaunch {
+  const ChainDev *chains;
+  const float4 *m;
+  const float4 *tab;
+  const float *ms;
+  void *spec;
+  const void *const *nhat;
+  const void *twiddle;
+  float4 *heff;
+  double *Hd;
+  int Hd_chain;
+  const int *rows_chain;
+  const long long *rows_first;
+  int rows_blocks, rows_threads;
+  size_t rows_smem;
+  const int *cols_chain;
+  const long long *cols_first;
+  int cols_blocks, cols_threads, cols_per_block;
+  size_t cols_smem;
+  cudaEvent_t *ev;              // optional: 4 events recorded around the three kernels
+};
+void launch_demag(const Launch &L, const DemagLaunch &P, bool fp64);
+cudaError_t demag_set_smem_limits();
+
+struct ObsLaunch {
+  const ChainDev *chains;
+  ChainState *st;
+  const int *blk_chain;
+  const long long *blk_first;   // nchains + 1 entries
+  int nblocks, nchains;
+  const float4 *m;
+  double *part;
+  unsigned long long *hist;
+  int bins;
+  float scale;
+  double *out;
+  int accumulate;
+};
+void launch_obs(const Launch &L, const ObsLaunch &P);
+
+void launch_energy(const Launch &L, const ChainDev *chains_d, int c, long long slots,
+                   const float4 *m, const double *etab, const double *Hd, const EnergyCoef &E,
+                   double *part, double *out7);
+void launch_pack(const Launch &L, const ChainDev *chains_d, int c, long long slots, float4 *m,
+                 const float4 *nat, int to_split);
+void launch_init_random(const Launch &L, const ChainDev *chains_d, int c, long long slots, float4 *m,
+                        unsigned key0, unsigned key1, const float *len_nat, float len);
+
+}  // namespace mmc

@@ -1,0 +1,212 @@
+"""Python binding of the MMC library: the C-ABI calls with numpy / torch buffers.
+
+Every step of the method runs in the library's CUDA kernels; this module only
+marshals arguments (problem dicts -> C structs, arrays -> pointers).
+
+A problem ("chain") is a dict with the keys
+  mesh (nx, ny, nz), pbc (3 bools), h (3 cell sizes, m), Ms0, A0, D0, K1, K2,
+  eA (3), Tc, T, mu, B (3, tesla), grain (per-cell ints or None),
+  grain_exch_scale, aniso ('uniaxial' | 'cubic');
+Ms0, K1, eA, Tc and T may be per-cell arrays (natural order i + nx (j + ny k)).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import ChainDesc, Material, Mesh, Obs, Options, check, load
+
+MUB = 9.2740100783e-24
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    check(load().mmc_default_options(C.byref(o)), "mmc_default_options")
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _percell(v, n, width=1):
+    a = np.asarray(v, dtype=np.float64)
+    if a.size == width:
+        return None, a.reshape(width)
+    return np.ascontiguousarray(a.reshape(n * width)), None
+
+
+class MMC:
+    """A batch of MMC chains on one GPU (a plain run is a batch of one)."""
+
+    def __init__(self, chains, options: Options | None = None, stream=None, **opt):
+        L = load()
+        if isinstance(chains, dict):
+            chains = [chains]
+        self.specs = list(chains)
+        self.nchains = len(chains)
+        if options is None:
+            options = default_options(**opt)
+        self.options = options
+        keep = []
+        descs = (ChainDesc * self.nchains)()
+        for k, sp in enumerate(self.specs):
+            d = descs[k]
+            nx, ny, nz = sp["mesh"]
+            n = nx * ny * nz
+            d.mesh = Mesh(nx, ny, nz, (C.c_int * 3)(*[int(bool(p)) for p in sp.get("pbc", (0, 0, 0))]))
+            d.cellsize = (C.c_double * 3)(*sp["h"])
+            mat = Material()
+            cell, val = _percell(sp["Ms0"], n)
+            mat.Ms0 = float(val[0]) if val is not None else float(cell.mean())
+            if cell is not None:
+                keep.append(cell); mat.Ms0_cell = _dptr(cell)
+            mat.A0 = float(sp.get("A0", 0.0))
+            mat.D0 = float(sp.get("D0", 0.0))
+            cell, val = _percell(sp.get("K1", 0.0), n)
+            mat.K1 = float(val[0]) if val is not None else float(cell.mean())
+            if cell is not None:
+                keep.append(cell); mat.K1_cell = _dptr(cell)
+            mat.K2 = float(sp.get("K2", 0.0))
+            cell, val = _percell(sp.get("eA", (0.0, 0.0, 1.0)), n, 3)
+            mat.e_A = (C.c_double * 3)(*(val if val is not None else (0.0, 0.0, 1.0)))
+            if cell is not None:
+                keep.append(cell); mat.e_A_cell = _dptr(cell)
+            cell, val = _percell(sp["Tc"], n)
+            mat.Tc = float(val[0]) if val is not None else float(cell.mean())
+            if cell is not None:
+                keep.append(cell); mat.Tc_cell = _dptr(cell)
+            mat.mu_atom = float(sp.get("mu", MUB))
+            mat.aniso_cubic = 1 if sp.get("aniso", "uniaxial") == "cubic" else 0
+            if sp.get("grain") is not None:
+                g = np.ascontiguousarray(sp["grain"], dtype=np.int32).reshape(n)
+                keep.append(g)
+                mat.grain = g.ctypes.data_as(C.POINTER(C.c_int))
+                mat.grain_exch_scale = float(sp.get("grain_exch_scale", 1.0))
+            d.material = mat
+            cell, val = _percell(sp["T"], n)
+            d.T = float(val[0]) if val is not None else float(cell.max())
+            if cell is not None:
+                keep.append(cell); d.T_cell = _dptr(cell)
+            d.B = (C.c_double * 3)(*sp.get("B", (0.0, 0.0, 0.0)))
+        self._ctx = C.c_void_p()
+        st = None
+        if stream is not None:
+            st = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        check(L.mmc_create(descs, self.nchains, C.byref(options), st, C.byref(self._ctx)), "mmc_create")
+        self.ncell = [int(L.mmc_ncell(self._ctx, k)) for k in range(self.nchains)]
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            load().mmc_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ state
+    def set_field(self, B, chain=-1):
+        b = np.asarray(B, dtype=np.float64).reshape(3)
+        check(load().mmc_set_field(self._ctx, int(chain), _dptr(b)), "mmc_set_field")
+
+    def set_m(self, m, chain=0):
+        """m: numpy float32 (ncell, 4) on the host, or a CUDA torch tensor."""
+        if hasattr(m, "is_cuda") and m.is_cuda:
+            assert m.dtype.is_floating_point and m.numel() == 4 * self.ncell[chain] and m.is_contiguous()
+            check(load().mmc_set_m(self._ctx, int(chain), C.c_void_p(m.data_ptr()), 1), "mmc_set_m")
+            return
+        a = np.ascontiguousarray(m, dtype=np.float32).reshape(-1, 4)
+        assert a.shape[0] == self.ncell[chain]
+        check(load().mmc_set_m(self._ctx, int(chain), a.ctypes.data_as(C.c_void_p), 0), "mmc_set_m")
+
+    def get_m(self, chain=0, out=None):
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            check(load().mmc_get_m(self._ctx, int(chain), C.c_void_p(out.data_ptr()), 1), "mmc_get_m")
+            return out
+        a = np.empty((self.ncell[chain], 4), dtype=np.float32) if out is None else out
+        check(load().mmc_get_m(self._ctx, int(chain), a.ctypes.data_as(C.c_void_p), 0), "mmc_get_m")
+        return a
+
+    def init_random(self, seed, length=0.0):
+        check(load().mmc_init_random(self._ctx, int(seed), float(length)), "mmc_init_random")
+
+    # ------------------------------------------------------------------ MC
+    def sweep(self, n, seed):
+        check(load().mmc_sweep(self._ctx, int(n), int(seed)), "mmc_sweep")
+
+    def sweep_sampled(self, n, seed, every):
+        check(load().mmc_sweep_sampled(self._ctx, int(n), int(seed), int(every)), "mmc_sweep_sampled")
+
+    def demag_update(self):
+        check(load().mmc_demag_update(self._ctx), "mmc_demag_update")
+
+    def pass_debug(self, chain, color, sweep, seed, theta_deg):
+        n = self.ncell[chain]
+        dec = np.zeros(n, dtype=np.float32)
+        acc = np.zeros(n, dtype=np.int8)
+        check(load().mmc_pass_debug(self._ctx, int(chain), int(color), int(sweep), int(seed),
+                                    float(theta_deg), dec.ctypes.data_as(C.c_void_p),
+                                    acc.ctypes.data_as(C.c_void_p)), "mmc_pass_debug")
+        return dec, acc
+
+    # ------------------------------------------------------------------ measurements
+    def observables(self, chain=0, reset=False):
+        bins = self.options.hist_bins
+        hist = np.zeros(bins + 1, dtype=np.int64)
+        o = Obs()
+        o.hist = hist.ctypes.data_as(C.POINTER(C.c_int64))
+        check(load().mmc_observables(self._ctx, int(chain), C.byref(o), int(bool(reset))), "mmc_observables")
+        return {"mean_m": np.array(o.mean_m[:]), "mean_len": o.mean_len, "mean_len2": o.mean_len2,
+                "nsnap": o.nsnap, "nonfinite": o.nonfinite, "acc_rate": o.acc_rate,
+                "theta_deg": o.theta_deg, "sweeps": o.sweeps, "hist": hist}
+
+    def energy(self, chain=0):
+        out = np.zeros(7)
+        check(load().mmc_energy(self._ctx, int(chain), _dptr(out)), "mmc_energy")
+        return out
+
+    def demag_field(self, chain=0):
+        H = np.zeros(3 * self.ncell[chain])
+        check(load().mmc_demag_field(self._ctx, int(chain), _dptr(H)), "mmc_demag_field")
+        return H.reshape(-1, 3)
+
+    def tables(self, chain=0):
+        n = self.ncell[chain]
+        me, chi, sg = np.zeros(n), np.zeros(n), np.zeros(n)
+        check(load().mmc_tables(self._ctx, int(chain), _dptr(me), _dptr(chi), _dptr(sg)), "mmc_tables")
+        return {"me": me, "chi": chi, "sigma": sg}
+
+    def phase_times(self, n, seed):
+        """n iterations eagerly with CUDA events around every kernel: returns
+        {kind: (total ms, launches)} for the six kernel kinds."""
+        ms = np.zeros(6)
+        cnt = np.zeros(6, dtype=np.int64)
+        check(load().mmc_phase_times(self._ctx, int(n), int(seed), _dptr(ms),
+                                     cnt.ctypes.data_as(C.POINTER(C.c_int64))), "mmc_phase_times")
+        kinds = ("demag_rows_fwd", "demag_cols", "demag_rows_inv", "sweep_pass", "observables", "advance")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(kinds)}
+
+    @property
+    def launches(self) -> int:
+        return int(load().mmc_kernel_launches(self._ctx))
+
+    def checkpoint(self) -> bytes:
+        L = load()
+        n = C.c_size_t(0)
+        check(L.mmc_checkpoint(self._ctx, None, C.byref(n)), "mmc_checkpoint")
+        buf = (C.c_char * n.value)()
+        check(L.mmc_checkpoint(self._ctx, buf, C.byref(n)), "mmc_checkpoint")
+        return bytes(buf)
+
+    def restore(self, data: bytes):
+        buf = C.create_string_buffer(data, len(data))
+        check(load().mmc_restore(self._ctx, buf, len(data)), "mmc_restore")
