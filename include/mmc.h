@@ -192,8 +192,9 @@ mmc_status mmc_sweep_sampled(mmc_ctx *ctx, int64_t n, uint64_t seed, int sample_
 mmc_status mmc_demag_update(mmc_ctx *ctx);
 
 /* One sublattice pass of one chain with explicit sweep index and cone angle,
- * leaving the sweep counter and adaptation alone: diagnostic form used by
- * parity checks.  dec (optional HOST, ncell floats) receives the decision value
+ * leaving the sweep counter, the adaptation window and the other chains alone:
+ * diagnostic form used by parity checks.  Accepted moves are written to the
+ * chain's state, as in mmc_sweep.  dec (optional HOST, ncell floats) receives the decision value
  * d = dF/kT - 4 ln(m'/m) + ln u3 (accept iff d < 0) of the cells of that
  * colour, acc (optional HOST, ncell int8) 1/0 for them and -1 for the others. */
 mmc_status mmc_pass_debug(mmc_ctx *ctx, int chain, int color, uint32_t sweep, uint64_t seed,
@@ -221,14 +222,19 @@ mmc_status mmc_demag_field(mmc_ctx *ctx, int chain, double *H);
  * m_e (Eq. 9), chi (Eq. 8, 1/T), sigma (Eq. 13 capped). */
 mmc_status mmc_tables(mmc_ctx *ctx, int chain, double *me, double *chi, double *sigma);
 
-/* Energy and gradient of one chain for a caller-given state (differentiable
- * form): m is a DEVICE array of 3*ncell values (double if fp64 != 0, else
- * float) in natural order; dEdm (DEVICE, same type and size) receives dE/dm_i in
- * J per unit m; E (HOST, 7 doubles) the terms as mmc_energy; dEdp (HOST, 5
- * doubles) dE/d(Ms0, A0, D0, K1, chi) for a uniform material.  The demag field is
- * recomputed from m in the requested precision; nothing is stored between
- * calls. */
-mmc_status mmc_energy_grad(mmc_ctx *ctx, int chain, const void *m, int fp64,
+/* Differentiable form: energy and hand-written gradient of one chain for a
+ * caller-given state (Eqs. 7, 10, 11, 12, 14, 15).  m is a DEVICE array of
+ * 3*ncell values in natural order, double if fp64 != 0 else float.  params
+ * (HOST, optional) = {Ms0, A0, D0, Ku, chi} overrides the chain's material for
+ * this call: Ms0 (A/m), A0 (J/m), D0 (J/m^2), the T = 0 anisotropy constant Ku
+ * (K1(T) = Ku m_e^3) and the longitudinal susceptibility chi (1/T) of Eq. 7;
+ * NULL uses the chain's own values.  E (HOST, 7 doubles) receives the terms as
+ * mmc_energy; dEdm (DEVICE, optional, same type and size as m) dE/dm_i in J per
+ * unit m; dEdp (HOST, optional, 5 doubles) dE/d{Ms0, A0, D0, Ku, chi}.  The
+ * demag field is recomputed from m by the FFT convolution in the requested
+ * precision on every call; nothing is kept between calls.  Chains with per-cell
+ * material or temperature return MMC_ERR_UNSUPPORTED. */
+mmc_status mmc_energy_grad(mmc_ctx *ctx, int chain, const void *m, int fp64, const double params[5],
                            double E[7], void *dEdm, double dEdp[5]);
 
 /* Per-kernel timing: runs n MMC iterations eagerly (as mmc_sweep, without

@@ -76,24 +76,54 @@ static void draw4(uint32_t cell, uint32_t sweep, uint32_t chain, uint32_t tag,
 /* ========================================================================== */
 /* Thermodynamics (Sec. II, Eqs. 7-9, 13).                                     */
 
-/* Langevin function B(x) = coth(x) - 1/x (Eq. 8); series near 0. */
+/* Coefficients a_n of coth x - 1/x = sum_{n>=1} a_n x^{2n-1}: a_n = (-1)^{n+1}
+ * 2 zeta(2n) / pi^{2n} (the Bernoulli-number series of coth).  zeta(2n) is
+ * summed directly for n >= 5 (the tail is below 1e-17 relative). */
+#define LANG_TERMS 13
+static double lang_coef[LANG_TERMS];
+static int lang_ready = 0;
+
+static void lang_init(void)
+{
+    if (lang_ready) return;
+    const double pi2 = PI * PI;
+    double z[LANG_TERMS];
+    z[0] = pi2 / 6.0;
+    z[1] = pi2 * pi2 / 90.0;
+    z[2] = pi2 * pi2 * pi2 / 945.0;
+    z[3] = pi2 * pi2 * pi2 * pi2 / 9450.0;
+    for (int n = 5; n <= LANG_TERMS; ++n) {
+        double sum = 0.0;
+        for (int k = 400; k >= 1; --k) sum += pow((double)k, -2.0 * n);
+        z[n - 1] = sum;
+    }
+    for (int n = 1; n <= LANG_TERMS; ++n)
+        lang_coef[n - 1] = ((n % 2) ? 2.0 : -2.0) * z[n - 1] / pow(PI, 2.0 * n);
+    lang_ready = 1;
+}
+
+/* Langevin function B(x) = coth(x) - 1/x (Eq. 8); the series below |x| = 0.5,
+ * where the difference of the two terms would cancel. */
 double orc_langevin(double x)
 {
-    double ax = fabs(x);
-    if (ax < 1e-3) {
-        double x2 = x * x;
-        return x * (1.0 / 3.0 - x2 / 45.0 + 2.0 * x2 * x2 / 945.0);
+    if (fabs(x) < 0.5) {
+        lang_init();
+        double x2 = x * x, acc = 0.0;
+        for (int n = LANG_TERMS; n >= 1; --n) acc = acc * x2 + lang_coef[n - 1];
+        return x * acc;
     }
     return 1.0 / tanh(x) - 1.0 / x;
 }
 
-/* B'(x) = 1/x^2 - 1/sinh^2(x); series near 0. */
+/* B'(x) = 1/x^2 - 1/sinh^2(x); the differentiated series below |x| = 0.5. */
 double orc_langevin_d(double x)
 {
     double ax = fabs(x);
-    if (ax < 1e-3) {
-        double x2 = x * x;
-        return 1.0 / 3.0 - x2 / 15.0 + 2.0 * x2 * x2 / 189.0;
+    if (ax < 0.5) {
+        lang_init();
+        double x2 = x * x, acc = 0.0;
+        for (int n = LANG_TERMS; n >= 1; --n) acc = acc * x2 + (2.0 * n - 1.0) * lang_coef[n - 1];
+        return acc;
     }
     if (ax > 40.0) return 1.0 / (x * x);
     double s = sinh(x);

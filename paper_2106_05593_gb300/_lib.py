@@ -114,7 +114,7 @@ def load():
     L.mmc_tables.restype = st
     L.mmc_tables.argtypes = [vp, C.c_int, dp, dp, dp]
     L.mmc_energy_grad.restype = st
-    L.mmc_energy_grad.argtypes = [vp, C.c_int, vp, C.c_int, dp, vp, dp]
+    L.mmc_energy_grad.argtypes = [vp, C.c_int, vp, C.c_int, dp, dp, vp, dp]
     L.mmc_phase_times.restype = st
     L.mmc_phase_times.argtypes = [vp, C.c_int64, C.c_uint64, dp, C.POINTER(C.c_int64)]
     L.mmc_kernel_launches.restype = C.c_int64

@@ -90,6 +90,7 @@ struct DemagPlan {
   int cols_blocks = 0, cols_threads = 0, cols_cc = 1;
   size_t cols_smem = 0;
   void *spec = nullptr;
+  bool il2d = false;
   bool ready = false;
 };
 
@@ -136,7 +137,8 @@ struct mmc_ctx {
   unsigned long long *d_hist_acc = nullptr, *d_hist_cur = nullptr;
   double *d_obs_out = nullptr;
   DemagPlan batch_plan;
-  std::vector<DemagPlan> single64;      // per chain, built lazily
+  std::vector<DemagPlan> single[2];     // per chain and precision (0 FP32, 1 FP64), built lazily
+  double *d_g8 = nullptr;
   double *d_Hd = nullptr, *d_eout = nullptr, *d_etab = nullptr;
   float4 *d_nat = nullptr;
   float *d_dec = nullptr;
@@ -281,6 +283,7 @@ void build_chain(ChainHost &H, ChainDev &D, const mmc_chain_desc &d, const mmc_o
   D.Bx = (float)d.B[0]; D.By = (float)d.B[1]; D.Bz = (float)d.B[2];
   D.gscale = (float)(mt.grain ? mt.grain_exch_scale : 1.0);
   D.Ms0 = (float)mt.Ms0;
+  D.Ms0d = mt.Ms0;
   double e[3] = {mt.e_A[0], mt.e_A[1], mt.e_A[2]};
   double en = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
   if (!(en > 0)) { e[0] = 0; e[1] = 0; e[2] = 1; en = 1; }
@@ -394,44 +397,64 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
   } else {
     P.d_ch = c->d_ch;
   }
-  // rows kernels
-  const int Gmax = std::max(maxPx / 8, 1);
-  int T = std::min(512, std::max(64, 3 * Gmax));
-  T = (T + 31) / 32 * 32;
-  if (T < Gmax) T = Gmax;
-  std::vector<int> rc;
-  std::vector<long long> rf;
-  size_t rsmem = 0;
-  for (size_t t = 0; t < table.size(); ++t) {
-    const ChainDev &D = table[t];
-    const int G = std::max(D.Px / 8, 1);
-    const int np = std::max(1, std::min(8, T / (3 * G)));
-    const int pairs = (D.nrows + 1) / 2;
-    const int nb = (pairs + np - 1) / np;
-    rf.push_back((long long)rc.size());
-    for (int b = 0; b < nb; ++b) rc.push_back((int)t);
-    rsmem = std::max(rsmem, (size_t)3 * np * D.Px * csz);
+  // 2D chains use the interleaved radix-16 kernels: E elements per block,
+  // 3 sequences per row pair (np = E / (3 Px)) or 3 components per column
+  // (CC = E / (3 Py))
+  const int E = il_elements(fp64);
+  bool il = true;
+  for (const ChainDev &D : table)
+    if (D.Pz != 1 || 3 * D.Px > E || 3 * D.Py > E) il = false;
+  std::vector<int> rc, colc;
+  std::vector<long long> rf, colf;
+  size_t rsmem = 0, csmem = 0;
+  int T = 384, Tc = 384, cc = 1;
+  if (il) {
+    for (size_t t = 0; t < table.size(); ++t) {
+      const ChainDev &D = table[t];
+      const int np = E / (3 * D.Px);
+      const int nb = ((D.nrows + 1) / 2 + np - 1) / np;
+      rf.push_back((long long)rc.size());
+      for (int b = 0; b < nb; ++b) rc.push_back((int)t);
+      const int CC = E / (3 * D.Py);
+      const int nc = (D.Px / 2 + 1 + CC - 1) / CC;
+      colf.push_back((long long)colc.size());
+      for (int b = 0; b < nc; ++b) colc.push_back((int)t);
+    }
+    rsmem = csmem = (size_t)E * csz;
+  } else {
+    const int Gmax = std::max(maxPx / 8, 1);
+    T = std::min(512, std::max(64, 3 * Gmax));
+    T = (T + 31) / 32 * 32;
+    if (T < Gmax) T = Gmax;
+    for (size_t t = 0; t < table.size(); ++t) {
+      const ChainDev &D = table[t];
+      const int G = std::max(D.Px / 8, 1);
+      const int np = std::max(1, std::min(8, T / (3 * G)));
+      const int pairs = (D.nrows + 1) / 2;
+      const int nb = (pairs + np - 1) / np;
+      rf.push_back((long long)rc.size());
+      for (int b = 0; b < nb; ++b) rc.push_back((int)t);
+      rsmem = std::max(rsmem, (size_t)3 * np * D.Px * csz);
+    }
+    cc = 8;
+    while (cc > 1 && (size_t)3 * cc * maxPyPz * csz > 100 * 1024) cc >>= 1;
+    csmem = (size_t)3 * cc * maxPyPz * csz;
+    if (csmem > 200 * 1024) return fail(MMC_ERR_UNSUPPORTED, "column FFT plane too large for shared memory");
+    int Gy = 1;
+    for (size_t t = 0; t < table.size(); ++t) {
+      const ChainDev &D = table[t];
+      Gy = std::max(Gy, std::max(D.Py / 8, std::max(D.Pz / 8, 1)));
+      const int nb = (D.Px / 2 + 1 + cc - 1) / cc;
+      colf.push_back((long long)colc.size());
+      for (int b = 0; b < nb; ++b) colc.push_back((int)t);
+    }
+    Tc = std::min(512, std::max(128, 3 * cc * Gy));
+    Tc = (Tc + 31) / 32 * 32;
+    if (Tc < Gy) Tc = Gy;
   }
   rf.push_back((long long)rc.size());
-  // cols kernel
-  int cc = 8;
-  while (cc > 1 && (size_t)3 * cc * maxPyPz * csz > 100 * 1024) cc >>= 1;
-  const size_t csmem = (size_t)3 * cc * maxPyPz * csz;
-  if (csmem > 200 * 1024) return fail(MMC_ERR_UNSUPPORTED, "column FFT plane too large for shared memory");
-  std::vector<int> colc;
-  std::vector<long long> colf;
-  int Gy = 1;
-  for (size_t t = 0; t < table.size(); ++t) {
-    const ChainDev &D = table[t];
-    Gy = std::max(Gy, std::max(D.Py / 8, std::max(D.Pz / 8, 1)));
-    const int nb = (D.Px / 2 + 1 + cc - 1) / cc;
-    colf.push_back((long long)colc.size());
-    for (int b = 0; b < nb; ++b) colc.push_back((int)t);
-  }
   colf.push_back((long long)colc.size());
-  int Tc = std::min(512, std::max(128, 3 * cc * Gy));
-  Tc = (Tc + 31) / 32 * 32;
-  if (Tc < Gy) Tc = Gy;
+  P.il2d = il;
   MMC_TRY(upload(c, &P.rows_chain, rc));
   MMC_TRY(upload(c, &P.rows_first, rf));
   MMC_TRY(upload(c, &P.cols_chain, colc));
@@ -473,13 +496,17 @@ DemagLaunch make_demag_launch(mmc_ctx *c, const DemagPlan &P, float4 *heff, doub
   D.cols_per_block = P.cols_cc;
   D.cols_smem = P.cols_smem;
   D.ev = nullptr;
+  D.m_nat = nullptr;
+  D.Ms_override = 0.0;
+  D.il2d = P.il2d;
   return D;
 }
 
-mmc_status single_plan(mmc_ctx *c, int chain, DemagPlan **out) {
-  if ((int)c->single64.size() < c->nchains) c->single64.resize(c->nchains);
-  DemagPlan &P = c->single64[chain];
-  if (!P.ready) MMC_TRY(build_demag_plan(c, P, std::vector<int>{chain}, true, true));
+mmc_status single_plan(mmc_ctx *c, int chain, bool fp64, DemagPlan **out) {
+  std::vector<DemagPlan> &v = c->single[fp64 ? 1 : 0];
+  if ((int)v.size() < c->nchains) v.resize(c->nchains);
+  DemagPlan &P = v[chain];
+  if (!P.ready) MMC_TRY(build_demag_plan(c, P, std::vector<int>{chain}, fp64, true));
   *out = &P;
   return MMC_OK;
 }
@@ -1059,7 +1086,7 @@ mmc_status mmc_observables(mmc_ctx *c, int chain, mmc_obs *out, int reset) {
 
 static mmc_status demag64_chain(mmc_ctx *c, int chain) {
   DemagPlan *P = nullptr;
-  MMC_TRY(single_plan(c, chain, &P));
+  MMC_TRY(single_plan(c, chain, true, &P));
   Launch L = c->L();
   launch_demag(L, make_demag_launch(c, *P, nullptr, c->d_Hd, 0), true);
   return check_launch();
@@ -1112,11 +1139,86 @@ mmc_status mmc_tables(mmc_ctx *c, int chain, double *me, double *chi, double *si
   return MMC_OK;
 }
 
-mmc_status mmc_energy_grad(mmc_ctx *c, int chain, const void *m, int fp64, double E[7], void *dEdm,
-                           double dEdp[5]) {
-  (void)m; (void)fp64; (void)E; (void)dEdm; (void)dEdp;
+mmc_status mmc_energy_grad(mmc_ctx *c, int chain, const void *m, int fp64, const double params[5],
+                           double E[7], void *dEdm, double dEdp[5]) {
   MMC_TRY(check_chain(c, chain));
-  return fail(MMC_ERR_UNSUPPORTED, "energy gradient not available in this build");
+  if (!m || !E) return fail(MMC_ERR_ARG, "null m or E");
+  const ChainHost &H = c->hc[chain];
+  if (H.percell) return fail(MMC_ERR_UNSUPPORTED, "energy gradient of a chain with per-cell material");
+  const bool f64 = fp64 != 0;
+  double Ms0 = H.Ms0, A0 = H.ecoef.cex[0] * H.h[0] * H.h[0] / H.V, D0 = H.ecoef.cdmi[0] * H.h[0] / H.V;
+  double Ku = H.K1, chi = H.chi[0];
+  if (params) {
+    Ms0 = params[0]; A0 = params[1]; D0 = params[2]; Ku = params[3]; chi = params[4];
+    if (!(Ms0 > 0) || !(chi > 0)) return fail(MMC_ERR_ARG, "params: Ms0 and chi must be > 0");
+  }
+  GradCoef G;
+  std::memset(&G, 0, sizeof(G));
+  for (int a = 0; a < 3; ++a) {
+    G.vh2[a] = H.V / (H.h[a] * H.h[a]);
+    G.cex[a] = A0 * G.vh2[a];
+  }
+  for (int a = 0; a < 2; ++a) {
+    G.vh[a] = H.V / H.h[a];
+    G.cdmi[a] = D0 * G.vh[a];
+  }
+  const double me = H.me[0];
+  const int l1 = H.cubic ? 10 : 3, l2 = H.cubic ? 21 : 10;
+  G.Kscale = std::pow(me, l1);
+  G.K1T = Ku * G.Kscale;
+  G.K2T = H.K2 * std::pow(me, l2);
+  for (int a = 0; a < 3; ++a) { G.e[a] = H.ecoef.e[a]; G.B[a] = H.ecoef.B[a]; }
+  G.V = H.V;
+  G.Ms0 = Ms0;
+  G.cubic = H.cubic;
+  G.anis = (Ku != 0.0 || H.K2 != 0.0) ? 1 : 0;
+  G.dmi = 1;
+  // longitudinal coefficients from Eq. 7 with the given chi
+  {
+    const double T = H.T, Tc = H.Tc;
+    const double Tg = std::fabs(T - Tc) < 1e-3 ? (T < Tc ? Tc - 1e-3 : Tc + 1e-3) : T;
+    if (Tg < Tc) {
+      G.c2 = 0.0;
+      G.c4 = H.V * Ms0 / (8.0 * chi * me * me);
+      G.me2 = me * me;
+    } else {
+      G.c2 = H.V * Ms0 / (2.0 * chi);
+      G.c4 = G.c2 * 3.0 * Tc / (10.0 * (Tg - Tc));
+      G.me2 = 0.0;
+    }
+  }
+  const double *Hd = nullptr;
+  if (c->any_demag) {
+    DemagPlan *P = nullptr;
+    MMC_TRY(single_plan(c, chain, f64, &P));
+    DemagLaunch D = make_demag_launch(c, *P, nullptr, c->d_Hd, 0);
+    D.m_nat = m;
+    D.Ms_override = Ms0;
+    launch_demag(c->L(), D, f64);
+    Hd = c->d_Hd;
+  }
+  if (!c->d_g8) MMC_TRY(dalloc_t(c, &c->d_g8, 8));
+  launch_energy_grad(c->L(), c->d_ch, chain, H.ncell, m, f64, Hd, G, dEdm, c->d_part, c->d_g8);
+  MMC_TRY(check_launch());
+  double o[8];
+  CUDA_TRY(cudaMemcpyAsync(o, c->d_g8, sizeof(o), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  // o = {ex_unit, dmi_unit, an, an1_unit, zee, long, demag}
+  E[1] = A0 * o[0];
+  E[2] = D0 * o[1];
+  E[3] = o[2];
+  E[4] = o[4];
+  E[5] = o[5];
+  E[6] = o[6];
+  E[0] = E[1] + E[2] + E[3] + E[4] + E[5] + E[6];
+  if (dEdp) {
+    dEdp[0] = (E[5] + E[4] + 2.0 * E[6]) / Ms0;
+    dEdp[1] = o[0];
+    dEdp[2] = o[1];
+    dEdp[3] = o[3];
+    dEdp[4] = -E[5] / chi;
+  }
+  return MMC_OK;
 }
 
 mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[6], int64_t count[6]) {

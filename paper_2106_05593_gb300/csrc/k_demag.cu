@@ -17,6 +17,7 @@
 // The FFTs are the shared-memory Stockham transforms of fft.cuh; R = float or
 // double selects the arithmetic of the whole convolution.
 #include "fft.cuh"
+#include "fft_il.cuh"
 #include "mmc_internal.h"
 
 namespace mmc {
@@ -36,6 +37,8 @@ struct DemagArgs {
   float4 *heff;
   double *Hd;
   int Hd_chain;
+  const R *m_nat;     // optional natural-order input (3 per cell) instead of the split state
+  R Ms_override;      // > 0: uniform Ms0 used with m_nat
 };
 
 __device__ __forceinline__ int pairs_per_block(int Px) {
@@ -44,16 +47,19 @@ __device__ __forceinline__ int pairs_per_block(int Px) {
   return np < 1 ? 1 : (np > 8 ? 8 : np);
 }
 
-// M = Ms0 m of cell (x, row r) from the split layout
-__device__ __forceinline__ float3 load_M(const ChainDev &ch, const float4 *m, const float *ms,
-                                         int r, int x) {
+// M = Ms0 m of cell (x, row r) from the split layout, formed in the convolution's precision
+template <typename R>
+__device__ __forceinline__ void load_M(const ChainDev &ch, const float4 *m, const float *ms, int r, int x,
+                                       R &Mx, R &My, R &Mz) {
   const int j = r % ch.ny, k = r / ch.ny;
   const int col = (x + j + k) & 1;
   const long long S = (long long)ch.nrows * ch.hx;
   const long long idx = (long long)col * S + (long long)r * ch.hx + (x >> 1);
   const float4 v = m[ch.m_off + idx];
-  const float Ms = ch.ms_off >= 0 ? ms[ch.ms_off + idx] : ch.Ms0;
-  return make_float3(Ms * v.x, Ms * v.y, Ms * v.z);
+  const R Ms = ch.ms_off >= 0 ? (R)ms[ch.ms_off + idx] : (R)ch.Ms0d;
+  Mx = Ms * (R)v.x;
+  My = Ms * (R)v.y;
+  Mz = Ms * (R)v.z;
 }
 
 template <typename R>
@@ -70,15 +76,25 @@ __global__ void k_rows_fwd(DemagArgs<R> A) {
   for (int idx = threadIdx.x; idx < np * Px; idx += blockDim.x) {
     const int qq = idx >> lx, x = idx & (Px - 1);
     const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
-    float3 M0 = make_float3(0.f, 0.f, 0.f), M1 = M0;
+    R M0x = 0, M0y = 0, M0z = 0, M1x = 0, M1y = 0, M1z = 0;
     if (pr < totpairs && x < nx) {
-      M0 = load_M(ch, A.m, A.ms, r0, x);
-      if (r1 < nrows) M1 = load_M(ch, A.m, A.ms, r1, x);
+      if (A.m_nat) {
+        const R Ms = A.Ms_override;
+        const R *v0 = A.m_nat + 3 * ((long long)r0 * nx + x);
+        M0x = Ms * v0[0]; M0y = Ms * v0[1]; M0z = Ms * v0[2];
+        if (r1 < nrows) {
+          const R *v1 = A.m_nat + 3 * ((long long)r1 * nx + x);
+          M1x = Ms * v1[0]; M1y = Ms * v1[1]; M1z = Ms * v1[2];
+        }
+      } else {
+        load_M<R>(ch, A.m, A.ms, r0, x, M0x, M0y, M0z);
+        if (r1 < nrows) load_M<R>(ch, A.m, A.ms, r1, x, M1x, M1y, M1z);
+      }
     }
     C z;
-    z.x = M0.x; z.y = M0.y; buf[(3 * qq + 0) * Px + x] = z;
-    z.x = M1.x; z.y = M1.y; buf[(3 * qq + 1) * Px + x] = z;
-    z.x = M0.z; z.y = M1.z; buf[(3 * qq + 2) * Px + x] = z;
+    z.x = M0x; z.y = M0y; buf[(3 * qq + 0) * Px + x] = z;
+    z.x = M1x; z.y = M1y; buf[(3 * qq + 1) * Px + x] = z;
+    z.x = M0z; z.y = M1z; buf[(3 * qq + 2) * Px + x] = z;
   }
   __syncthreads();
   fft_smem<C>(buf, lx, 3 * np, SeqMap{1, Px, 0, 1}, A.tw, false);
@@ -267,6 +283,219 @@ __global__ void k_rows_inv(DemagArgs<R> A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// 2D fast path (Pz == 1): interleaved radix-16 transforms, E complex elements
+// per block (3 sequences per row pair, or 3 components per column), V per thread.
+
+template <typename R> struct IlCfg;
+template <> struct IlCfg<float> { static constexpr int E = 12288, V = 32; };
+template <> struct IlCfg<double> { static constexpr int E = 6144, V = 16; };
+
+template <typename R>
+__global__ void __launch_bounds__(384) k_rows_fwd2(DemagArgs<R> A) {
+  using C = typename Cx<R>::T;
+  constexpr int E = IlCfg<R>::E, V = IlCfg<R>::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *buf = reinterpret_cast<C *>(smem_raw);
+  const int c = A.blk_chain[blockIdx.x];
+  const ChainDev &ch = A.chains[c];
+  const int Px = ch.Px, lx = ch.lx, nx = ch.nx, nrows = ch.nrows, Sx = ch.Sx;
+  const int np = E / (3 * Px), nseq = 3 * np;
+  const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
+  const int totpairs = (nrows + 1) / 2;
+  for (int idx = threadIdx.x; idx < np * Px; idx += blockDim.x) {
+    const int qq = idx >> lx, x = idx & (Px - 1);
+    const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
+    R M0x = 0, M0y = 0, M0z = 0, M1x = 0, M1y = 0, M1z = 0;
+    if (pr < totpairs && x < nx) {
+      if (A.m_nat) {
+        const R Ms = A.Ms_override;
+        const R *v0 = A.m_nat + 3 * ((long long)r0 * nx + x);
+        M0x = Ms * v0[0]; M0y = Ms * v0[1]; M0z = Ms * v0[2];
+        if (r1 < nrows) {
+          const R *v1 = A.m_nat + 3 * ((long long)r1 * nx + x);
+          M1x = Ms * v1[0]; M1y = Ms * v1[1]; M1z = Ms * v1[2];
+        }
+      } else {
+        load_M<R>(ch, A.m, A.ms, r0, x, M0x, M0y, M0z);
+        if (r1 < nrows) load_M<R>(ch, A.m, A.ms, r1, x, M1x, M1y, M1z);
+      }
+    }
+    C z;
+    C *row = buf + x * nseq + 3 * qq;
+    z.x = M0x; z.y = M0y; row[0] = z;
+    z.x = M1x; z.y = M1y; row[1] = z;
+    z.x = M0z; z.y = M1z; row[2] = z;
+  }
+  __syncthreads();
+  fft_il<C, V, false>(buf, lx, IlMap{nseq, 1, 0}, A.tw);
+  const int half = Px / 2 + 1;
+  const long long plane = (long long)nrows * Sx;
+  C *S = A.S + ch.s_off;
+  for (int idx = threadIdx.x; idx < np * half; idx += blockDim.x) {
+    const int qq = idx / half, kx = idx - qq * half;
+    const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
+    if (pr >= totpairs) continue;
+    const int km = (Px - kx) & (Px - 1);
+#pragma unroll
+    for (int sq = 0; sq < 3; ++sq) {
+      const C Z = buf[kx * nseq + 3 * qq + sq], Zm = buf[km * nseq + 3 * qq + sq];
+      C a, b;
+      a.x = (R)0.5 * (Z.x + Zm.x); a.y = (R)0.5 * (Z.y - Zm.y);
+      b.x = (R)0.5 * (Z.y + Zm.y); b.y = (R)0.5 * (Zm.x - Z.x);
+      if (sq == 0) {
+        S[0 * plane + (long long)r0 * Sx + kx] = a;
+        S[1 * plane + (long long)r0 * Sx + kx] = b;
+      } else if (sq == 1) {
+        if (r1 < nrows) {
+          S[0 * plane + (long long)r1 * Sx + kx] = a;
+          S[1 * plane + (long long)r1 * Sx + kx] = b;
+        }
+      } else {
+        S[2 * plane + (long long)r0 * Sx + kx] = a;
+        if (r1 < nrows) S[2 * plane + (long long)r1 * Sx + kx] = b;
+      }
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(384) k_cols2d(DemagArgs<R> A) {
+  using C = typename Cx<R>::T;
+  constexpr int E = IlCfg<R>::E, V = IlCfg<R>::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *buf = reinterpret_cast<C *>(smem_raw);
+  const int c = A.blk_chain[blockIdx.x];
+  const ChainDev &ch = A.chains[c];
+  const int Px = ch.Px, Py = ch.Py, ly = ch.ly, ny = ch.ny, nrows = ch.nrows, Sx = ch.Sx;
+  const int CC = E / (3 * Py);
+  const int kx0 = (int)(blockIdx.x - A.blk_first[c]) * CC;
+  const int qx = Px / 2 + 1, qy = Py / 2 + 1;
+  const long long plane = (long long)nrows * Sx;
+  C *S = A.S + ch.s_off;
+  // buf[(comp * Py + y) * CC + col]; rows y >= ny are the zero padding
+  for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
+    const int col = idx % CC, rest = idx / CC;
+    const int y = rest % Py, comp = rest / Py;
+    const int kx = kx0 + col;
+    C v;
+    v.x = 0; v.y = 0;
+    if (y < ny && kx < qx) v = S[comp * plane + (long long)y * Sx + kx];
+    buf[idx] = v;
+  }
+  __syncthreads();
+  fft_il<C, V, false>(buf, ly, IlMap{CC, 3, Py * CC}, A.tw);
+  const long long Q = (long long)qx * qy;
+  const R *nh = A.nhat[ch.spec];
+  for (int idx = threadIdx.x; idx < Py * CC; idx += blockDim.x) {
+    const int col = idx % CC, ky = idx / CC;
+    const int kx = kx0 + col;
+    if (kx >= qx) continue;
+    const int kyq = ky <= Py / 2 ? ky : Py - ky;
+    const R sy = ky <= Py / 2 ? (R)1 : (R)-1;
+    const long long qi = (long long)kyq * qx + kx;
+    const R Nxx = nh[qi], Nyy = nh[Q + qi], Nzz = nh[2 * Q + qi], Nxy = sy * nh[3 * Q + qi];
+    const int b0 = ky * CC + col, b1 = (Py + ky) * CC + col, b2 = (2 * Py + ky) * CC + col;
+    const C Mx = buf[b0], My = buf[b1], Mz = buf[b2];
+    C hx_, hy_, hz_;
+    hx_.x = -(Nxx * Mx.x + Nxy * My.x);
+    hx_.y = -(Nxx * Mx.y + Nxy * My.y);
+    hy_.x = -(Nxy * Mx.x + Nyy * My.x);
+    hy_.y = -(Nxy * Mx.y + Nyy * My.y);
+    hz_.x = -(Nzz * Mz.x);
+    hz_.y = -(Nzz * Mz.y);
+    buf[b0] = hx_; buf[b1] = hy_; buf[b2] = hz_;
+  }
+  __syncthreads();
+  fft_il<C, V, true>(buf, ly, IlMap{CC, 3, Py * CC}, A.tw);
+  for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
+    const int col = idx % CC, rest = idx / CC;
+    const int y = rest % Py, comp = rest / Py;
+    const int kx = kx0 + col;
+    if (y < ny && kx < qx) S[comp * plane + (long long)y * Sx + kx] = buf[idx];
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(384) k_rows_inv2(DemagArgs<R> A) {
+  using C = typename Cx<R>::T;
+  constexpr int E = IlCfg<R>::E, V = IlCfg<R>::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *buf = reinterpret_cast<C *>(smem_raw);
+  const int c = A.blk_chain[blockIdx.x];
+  const ChainDev &ch = A.chains[c];
+  const int Px = ch.Px, lx = ch.lx, nx = ch.nx, nrows = ch.nrows, Sx = ch.Sx;
+  const int np = E / (3 * Px), nseq = 3 * np;
+  const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
+  const int totpairs = (nrows + 1) / 2;
+  const int half = Px / 2 + 1;
+  const long long plane = (long long)nrows * Sx;
+  const C *S = A.S + ch.s_off;
+  for (int idx = threadIdx.x; idx < np * half; idx += blockDim.x) {
+    const int qq = idx / half, kx = idx - qq * half;
+    const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
+    C a[3], b[3];
+    for (int t = 0; t < 3; ++t) { a[t].x = 0; a[t].y = 0; b[t] = a[t]; }
+    if (pr < totpairs) {
+      a[0] = S[0 * plane + (long long)r0 * Sx + kx];
+      b[0] = S[1 * plane + (long long)r0 * Sx + kx];
+      a[2] = S[2 * plane + (long long)r0 * Sx + kx];
+      if (r1 < nrows) {
+        a[1] = S[0 * plane + (long long)r1 * Sx + kx];
+        b[1] = S[1 * plane + (long long)r1 * Sx + kx];
+        b[2] = S[2 * plane + (long long)r1 * Sx + kx];
+      }
+    }
+    const bool edge = (kx == 0) || (2 * kx == Px);
+#pragma unroll
+    for (int sq = 0; sq < 3; ++sq) {
+      C zk, zm;
+      if (edge) {
+        zk.x = a[sq].x; zk.y = b[sq].x;
+        buf[kx * nseq + 3 * qq + sq] = zk;
+      } else {
+        zk.x = a[sq].x - b[sq].y; zk.y = a[sq].y + b[sq].x;
+        zm.x = a[sq].x + b[sq].y; zm.y = b[sq].x - a[sq].y;
+        buf[kx * nseq + 3 * qq + sq] = zk;
+        buf[(Px - kx) * nseq + 3 * qq + sq] = zm;
+      }
+    }
+  }
+  __syncthreads();
+  fft_il<C, V, true>(buf, lx, IlMap{nseq, 1, 0}, A.tw);
+  const R scale = (R)1 / ((R)Px * (R)ch.Py * (R)ch.Pz);
+  const long long Sl = (long long)nrows * ch.hx;
+  const bool percell = ch.t_off >= 0;
+  const float mu0f = (float)mu0;
+  for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
+    const int qq = idx / nx, x = idx - qq * nx;
+    const int pr = pair0 + qq;
+    if (pr >= totpairs) continue;
+    const C z0 = buf[x * nseq + 3 * qq], z1 = buf[x * nseq + 3 * qq + 1], z2 = buf[x * nseq + 3 * qq + 2];
+    for (int h = 0; h < 2; ++h) {
+      const int r = 2 * pr + h;
+      if (r >= nrows) break;
+      const R Hx = (h == 0 ? z0.x : z1.x) * scale;
+      const R Hy = (h == 0 ? z0.y : z1.y) * scale;
+      const R Hz = (h == 0 ? z2.x : z2.y) * scale;
+      const int j = r % ch.ny, k = r / ch.ny;
+      const int colr = (x + j + k) & 1;
+      const long long li = (long long)colr * Sl + (long long)r * ch.hx + (x >> 1);
+      if (A.heff) {
+        const float zee = percell ? A.tab[ch.t_off + 2 * Sl + li].x : ch.zee;
+        A.heff[ch.h_off + li] = make_float4(zee * (ch.Bx + mu0f * (float)Hx), zee * (ch.By + mu0f * (float)Hy),
+                                            zee * (ch.Bz + mu0f * (float)Hz), 0.f);
+      }
+      if (A.Hd && c == A.Hd_chain) {
+        const long long nat = x + (long long)nx * r;
+        A.Hd[3 * nat + 0] = (double)Hx;
+        A.Hd[3 * nat + 1] = (double)Hy;
+        A.Hd[3 * nat + 2] = (double)Hz;
+      }
+    }
+  }
+}
+
 template <typename R>
 void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
   using C = typename Cx<R>::T;
@@ -276,6 +505,23 @@ void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
   A.nhat = reinterpret_cast<const R *const *>(P.nhat);
   A.tw = reinterpret_cast<const C *>(P.twiddle);
   A.heff = P.heff; A.Hd = P.Hd; A.Hd_chain = P.Hd_chain;
+  A.m_nat = reinterpret_cast<const R *>(P.m_nat);
+  A.Ms_override = (R)P.Ms_override;
+  if (P.il2d) {
+    const size_t sm = (size_t)IlCfg<R>::E * sizeof(C);
+    A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
+    if (P.ev) cudaEventRecord(P.ev[0], L.stream);
+    k_rows_fwd2<R><<<P.rows_blocks, 384, sm, L.stream>>>(A);
+    if (P.ev) cudaEventRecord(P.ev[1], L.stream);
+    A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
+    k_cols2d<R><<<P.cols_blocks, 384, sm, L.stream>>>(A);
+    if (P.ev) cudaEventRecord(P.ev[2], L.stream);
+    A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
+    k_rows_inv2<R><<<P.rows_blocks, 384, sm, L.stream>>>(A);
+    if (P.ev) cudaEventRecord(P.ev[3], L.stream);
+    *L.counter += 3;
+    return;
+  }
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
   if (P.ev) cudaEventRecord(P.ev[0], L.stream);
   k_rows_fwd<R><<<P.rows_blocks, P.rows_threads, P.rows_smem, L.stream>>>(A);
@@ -307,7 +553,19 @@ cudaError_t demag_set_smem_limits() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_rows_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_rows_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  e = cudaFuncSetAttribute(k_rows_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
+  const int lil = 100 * 1024;
+  const void *fns[6] = {(const void *)k_rows_fwd2<float>, (const void *)k_rows_fwd2<double>,
+                        (const void *)k_cols2d<float>, (const void *)k_cols2d<double>,
+                        (const void *)k_rows_inv2<float>, (const void *)k_rows_inv2<double>};
+  for (const void *f : fns) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lil);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
+
+int il_elements(bool fp64) { return fp64 ? IlCfg<double>::E : IlCfg<float>::E; }
 
 }  // namespace mmc

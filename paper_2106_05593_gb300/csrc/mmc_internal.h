@@ -59,6 +59,7 @@ struct ChainDev {
   float ex, ey, ez;   // easy axis
   float Bx, By, Bz;   // applied field (T)
   float Ms0;          // A/m (uniform chains)
+  double Ms0d;        // the same in FP64 (convolution input of the FP64 path)
   float gscale;       // bond scale across grains
 };
 
@@ -86,6 +87,19 @@ struct EnergyCoef {
   double B[3];
   double V;
   int cubic;
+};
+
+// coefficients of the differentiable energy (J), see k_grad.cu
+struct GradCoef {
+  double cex[3];      // V A0 / h_a^2
+  double cdmi[2];     // V D0 / h_a
+  double vh2[3];      // V / h_a^2   (dE/dA0 per unit bond sum)
+  double vh[2];       // V / h_a     (dE/dD0)
+  double c2, c4, me2; // F_l = c2 m^2 + c4 (m^2 - me2)^2
+  double Ms0, K1T, K2T, Kscale, e[3];
+  double B[3];
+  double V;
+  int cubic, anis, dmi;
 };
 
 // ---------------------------------------------------------------------------
@@ -150,7 +164,11 @@ struct DemagLaunch {
   int cols_blocks, cols_threads, cols_per_block;
   size_t cols_smem;
   cudaEvent_t *ev;              // optional: 4 events recorded around the three kernels
+  const void *m_nat;            // optional natural-order m (float or double, as the plan)
+  double Ms_override;           // uniform Ms0 used with m_nat
+  bool il2d;                    // 2D interleaved radix-16 kernels (all chains Pz == 1)
 };
+int il_elements(bool fp64);     // complex elements per block of the 2D kernels
 void launch_demag(const Launch &L, const DemagLaunch &P, bool fp64);
 cudaError_t demag_set_smem_limits();
 
@@ -173,6 +191,9 @@ void launch_obs(const Launch &L, const ObsLaunch &P);
 void launch_energy(const Launch &L, const ChainDev *chains_d, int c, long long slots,
                    const float4 *m, const double *etab, const double *Hd, const EnergyCoef &E,
                    double *part, double *out7);
+void launch_energy_grad(const Launch &L, const ChainDev *chains_d, int c, long long ncell, const void *m,
+                        bool fp64, const double *Hd, const GradCoef &G, void *dEdm, double *part,
+                        double *out8);
 void launch_pack(const Launch &L, const ChainDev *chains_d, int c, long long slots, float4 *m,
                  const float4 *nat, int to_split);
 void launch_init_random(const Launch &L, const ChainDev *chains_d, int c, long long slots, float4 *m,

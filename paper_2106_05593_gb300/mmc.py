@@ -185,6 +185,27 @@ class MMC:
         check(load().mmc_tables(self._ctx, int(chain), _dptr(me), _dptr(chi), _dptr(sg)), "mmc_tables")
         return {"me": me, "chi": chi, "sigma": sg}
 
+    def energy_grad(self, m, params=None, chain=0, grad=True):
+        """Differentiable form: m is a CUDA torch tensor (ncell, 3), float32 or
+        float64; params = (Ms0, A0, D0, Ku, chi) or None.  Returns (E[7],
+        dE/dm tensor or None, dE/dparams[5])."""
+        import torch
+        assert m.is_cuda and m.is_contiguous() and m.shape == (self.ncell[chain], 3)
+        fp64 = m.dtype == torch.float64
+        assert fp64 or m.dtype == torch.float32
+        E = np.zeros(7)
+        dp = np.zeros(5)
+        pp = None
+        if params is not None:
+            pa = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(5))
+            pp = _dptr(pa)
+        g = torch.empty_like(m) if grad else None
+        torch.cuda.current_stream(m.device).synchronize()
+        check(load().mmc_energy_grad(self._ctx, int(chain), C.c_void_p(m.data_ptr()), int(fp64), pp,
+                                     _dptr(E), C.c_void_p(g.data_ptr()) if grad else None, _dptr(dp)),
+              "mmc_energy_grad")
+        return E, g, dp
+
     def phase_times(self, n, seed):
         """n iterations eagerly with CUDA events around every kernel: returns
         {kind: (total ms, launches)} for the six kernel kinds."""

@@ -32,12 +32,15 @@ def full_spec(mesh, demag=False, pbc=(False, False, False), seed=0):
 
 
 def test_tables_match_oracle(P):
-    for T, Tc in [(300, 870), (800, 870), (869.5, 870), (900, 870), (50, 600), (610, 600)]:
+    for T, Tc in [(300, 870), (800, 870), (869.5, 870), (869.99, 870), (900, 870), (50, 600), (610, 600)]:
         s = W._base((4, 2, 1), (4e-9, 4e-9, 4e-9), T=T, Tc=Tc)
         g = P.MMC(s).tables()
         o = O.Oracle(s).tables()
+        # Eq. 8 divides by 1 - 3 B'(x) Tc / T, which vanishes at Tc: rounding is
+        # amplified by about 1 / |1 - T/Tc| there
+        rel = 1e-12 + 1e-15 / abs(1.0 - T / Tc)
         for k in ("me", "chi", "sigma"):
-            assert g[k][0] == pytest.approx(o[k][0], rel=1e-12, abs=1e-300), (T, Tc, k)
+            assert g[k][0] == pytest.approx(o[k][0], rel=rel, abs=1e-300), (T, Tc, k)
 
 
 CASES = {
@@ -55,9 +58,9 @@ def test_one_pass_matches_oracle(P, name):
     n = int(np.prod(spec["mesh"]))
     m4 = W.random_state(n, 21, 0.75, 0.95)
     g = P.MMC(spec)
-    g.set_m(m4)
     for color in (0, 1):
         for sweep, theta in ((0, 30.0), (17, 5.0), (123456, 120.0)):
+            g.set_m(m4)       # the diagnostic pass updates the state: restart from m4
             dec_g, acc_g = g.pass_debug(0, color, sweep, 11, theta)
             _, acc_o, dec_o, band_o = oracle_pass(spec, m4, color, sweep, 0, 11, theta)
             stats = compare_pass(dec_g, acc_g, dec_o, acc_o, band_o)
@@ -70,10 +73,10 @@ def test_one_pass_with_demag_film(P):
     m4 = W.smooth_state(spec["mesh"], 3, 0.86)
     for fp64 in (0, 1):
         g = P.MMC(spec, demag=1, demag_fp64=fp64)
-        g.set_m(m4)
         o = O.Oracle(spec)
         H = o.demag_field(m4[:, :3].astype(np.float64), "fft")
         for color in (0, 1):
+            g.set_m(m4)
             dec_g, acc_g = g.pass_debug(0, color, 5, 3, 25.0)
             _, acc_o, dec_o, band_o = oracle_pass(spec, m4, color, 5, 0, 3, 25.0, H=H)
             print("film128 fp64=%d" % fp64, color, compare_pass(dec_g, acc_g, dec_o, acc_o, band_o))
@@ -81,6 +84,7 @@ def test_one_pass_with_demag_film(P):
 
 def test_demag_field_fp64(P):
     for mesh, h in (((48, 40, 1), (4e-9, 4e-9, 4e-9)), ((16, 12, 4), (3e-9, 2e-9, 2.5e-9)),
+                    ((256, 192, 1), (4e-9, 4e-9, 4e-9)), ((130, 3, 1), (2e-9, 2e-9, 1e-9)),
                     ((1, 1, 1), (5e-9, 5e-9, 5e-9)), ((7, 1, 1), (2e-9, 3e-9, 4e-9))):
         n = int(np.prod(mesh))
         spec = W._base(mesh, h, demag=True, Ms0=6e5)
@@ -90,7 +94,8 @@ def test_demag_field_fp64(P):
         Hg = g.demag_field(0)
         Ho = O.Oracle(spec).demag_field(m4[:, :3].astype(np.float64), "direct" if n <= 4096 else "fft")
         scale = np.abs(Ho).max()
-        assert np.abs(Hg - Ho).max() < 1e-8 * scale, (mesh, np.abs(Hg - Ho).max() / scale)
+        print("demag fp64", mesh, np.abs(Hg - Ho).max() / scale)
+        assert np.abs(Hg - Ho).max() < 1e-9 * scale, (mesh, np.abs(Hg - Ho).max() / scale)
 
 
 def test_energy_terms(P):
@@ -134,6 +139,7 @@ def test_batch_of_uneven_chains(P):
         g.set_m(states[-1], k)
     for k, sp in enumerate(specs):
         for color in (0, 1):
+            g.set_m(states[k], k)
             dec_g, acc_g = g.pass_debug(k, color, 7, 99, 40.0)
             _, acc_o, dec_o, band_o = oracle_pass(sp, states[k], color, 7, k, 99, 40.0)
             compare_pass(dec_g, acc_g, dec_o, acc_o, band_o)
@@ -145,9 +151,26 @@ def test_granular_per_cell_chain(P):
     n = 48 * 48
     m4 = W.random_state(n, 8, 0.6, 0.9)
     g = P.MMC(spec)
-    g.set_m(m4)
     for color in (0, 1):
+        g.set_m(m4)
         dec_g, acc_g = g.pass_debug(0, color, 2, 5, 30.0)
         _, acc_o, dec_o, band_o = oracle_pass(spec, m4, color, 2, 0, 5, 30.0)
         # per-cell m_e^2 is stored in FP32 (no float-float pair): wider absolute bound
         print("granular", color, compare_pass(dec_g, acc_g, dec_o, acc_o, band_o, absolute=5e-4))
+
+
+def test_pass_updates_exactly_the_accepted_cells(P):
+    spec, _ = CASES["full3d"]
+    n = int(np.prod(spec["mesh"]))
+    m4 = W.random_state(n, 22, 0.75, 0.95)
+    g = P.MMC(spec)
+    g.set_m(m4)
+    dec, acc = g.pass_debug(0, 1, 3, 8, 35.0)
+    m1 = g.get_m()
+    m_o, acc_o, dec_o, band_o = oracle_pass(spec, m4, 1, 3, 0, 8, 35.0)
+    compare_pass(dec, acc, dec_o, acc_o, band_o)
+    moved = np.any(m1[:, :3] != m4[:, :3], axis=1)
+    assert np.array_equal(moved, acc == 1)
+    # accepted vectors equal the oracle's FP64 proposals to FP32 rounding
+    sel = acc == 1
+    assert np.abs(m1[sel, :3] - m_o[sel]).max() < 4e-7
