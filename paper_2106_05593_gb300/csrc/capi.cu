@@ -91,6 +91,7 @@ struct DemagPlan {
   size_t cols_smem = 0;
   void *spec = nullptr;
   bool il2d = false;
+  size_t inv_smem = 0;
   bool ready = false;
 };
 
@@ -416,11 +417,14 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
       rf.push_back((long long)rc.size());
       for (int b = 0; b < nb; ++b) rc.push_back((int)t);
       const int CC = E / (3 * D.Py);
-      const int nc = (D.Px / 2 + 1 + CC - 1) / CC;
+      const int nc = D.Sx / CC;
       colf.push_back((long long)colc.size());
       for (int b = 0; b < nc; ++b) colc.push_back((int)t);
     }
     rsmem = csmem = (size_t)E * csz;
+    int minPx = 1 << 30;
+    for (const ChainDev &D : table) minPx = std::min(minPx, D.Px);
+    P.inv_smem = (size_t)(E + 2 * (E / minPx)) * csz;
   } else {
     const int Gmax = std::max(maxPx / 8, 1);
     T = std::min(512, std::max(64, 3 * Gmax));
@@ -468,6 +472,7 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
   P.cols_smem = csmem;
   P.fp64 = fp64;
   MMC_TRY(dalloc(c, &P.spec, (size_t)spec_elems * csz));
+  CUDA_TRY(cudaMemset(P.spec, 0, (size_t)spec_elems * csz));   // padding columns stay defined
   P.ready = true;
   return MMC_OK;
 }
@@ -499,6 +504,7 @@ DemagLaunch make_demag_launch(mmc_ctx *c, const DemagPlan &P, float4 *heff, doub
   D.m_nat = nullptr;
   D.Ms_override = 0.0;
   D.il2d = P.il2d;
+  D.inv_smem = P.inv_smem;
   return D;
 }
 
@@ -740,7 +746,12 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
       D.Py = pad_len(D.ny, true);
       D.Pz = pad_len(D.nz, D.nz > 1);
       D.lx = ilog2(D.Px); D.ly = ilog2(D.Py); D.lz = ilog2(D.Pz);
-      D.Sx = (D.Px / 2 + 1 + 7) / 8 * 8;
+      // spectrum row stride: a multiple of 8 and of the column-group width
+      // 4096 / Py of the tiled 2D layout
+      {
+        const int g = std::max(8, D.Pz == 1 ? 4096 / D.Py : 8);
+        D.Sx = (D.Px / 2 + 1 + g - 1) / g * g;
+      }
       D.s_off = soff;
       soff += 3LL * D.nrows * D.Sx;
       int found = -1;

@@ -118,19 +118,38 @@ __device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C 
   __syncthreads();
 }
 
-// Full transform (forward or unnormalized inverse).  blockDim.x * V must cover
-// ngroups * nseq * N elements.
+// Compile-time pass schedule for N = 2^LOGN: radix 16 while possible, then the
+// remaining factor; the passes are straight-line code so every pass's register
+// arrays have their own short lifetime.
+template <typename C, int V, bool INV, int N, int P>
+__device__ __forceinline__ void fft_passes(C *buf, IlMap mp, const C *__restrict__ tw, int twshift) {
+  if constexpr (P < N) {
+    constexpr int REM = N / P;
+    constexpr int R = REM >= 16 ? 16 : REM;
+    il_pass<C, R, V, INV>(buf, N, P, mp, tw, twshift);
+    fft_passes<C, V, INV, N, P * R>(buf, mp, tw, twshift);
+  }
+}
+
+// Full transform (forward or unnormalized inverse), 2 <= N <= 4096.
+// blockDim.x * V must cover ngroups * nseq * N elements.
 template <typename C, int V, bool INV>
-__device__ void fft_il(C *buf, int logN, IlMap mp, const C *__restrict__ tw) {
-  const int N = 1 << logN;
+__device__ __forceinline__ void fft_il(C *buf, int logN, IlMap mp, const C *__restrict__ tw) {
   const int twshift = 12 - logN;
-  int p = 1;
-  while (p < N) {
-    const int rem = N / p;
-    if (rem >= 16) { il_pass<C, 16, V, INV>(buf, N, p, mp, tw, twshift); p *= 16; }
-    else if (rem == 8) { il_pass<C, 8, V, INV>(buf, N, p, mp, tw, twshift); p *= 8; }
-    else if (rem == 4) { il_pass<C, 4, V, INV>(buf, N, p, mp, tw, twshift); p *= 4; }
-    else { il_pass<C, 2, V, INV>(buf, N, p, mp, tw, twshift); p *= 2; }
+  switch (logN) {
+    case 1: fft_passes<C, V, INV, 2, 1>(buf, mp, tw, twshift); break;
+    case 2: fft_passes<C, V, INV, 4, 1>(buf, mp, tw, twshift); break;
+    case 3: fft_passes<C, V, INV, 8, 1>(buf, mp, tw, twshift); break;
+    case 4: fft_passes<C, V, INV, 16, 1>(buf, mp, tw, twshift); break;
+    case 5: fft_passes<C, V, INV, 32, 1>(buf, mp, tw, twshift); break;
+    case 6: fft_passes<C, V, INV, 64, 1>(buf, mp, tw, twshift); break;
+    case 7: fft_passes<C, V, INV, 128, 1>(buf, mp, tw, twshift); break;
+    case 8: fft_passes<C, V, INV, 256, 1>(buf, mp, tw, twshift); break;
+    case 9: fft_passes<C, V, INV, 512, 1>(buf, mp, tw, twshift); break;
+    case 10: fft_passes<C, V, INV, 1024, 1>(buf, mp, tw, twshift); break;
+    case 11: fft_passes<C, V, INV, 2048, 1>(buf, mp, tw, twshift); break;
+    case 12: fft_passes<C, V, INV, 4096, 1>(buf, mp, tw, twshift); break;
+    default: break;
   }
 }
 

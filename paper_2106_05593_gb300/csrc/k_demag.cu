@@ -285,24 +285,33 @@ __global__ void k_rows_inv(DemagArgs<R> A) {
 
 // ---------------------------------------------------------------------------
 // 2D fast path (Pz == 1): interleaved radix-16 transforms, E complex elements
-// per block (3 sequences per row pair, or 3 components per column), V per thread.
+// per block, V per thread (E / V threads).  The spectrum buffer is tiled by
+// column groups of CC = E / (3 Py) columns: element (comp, y, kx) at
+// ((comp * NG + kx / CC) * ny + y) * CC + kx % CC, NG = Sx / CC, so a row kernel
+// block (2 E / (3 Px) consecutive rows) writes runs of rows * CC elements and a
+// column kernel block reads and writes contiguous ny * CC runs.
 
 template <typename R> struct IlCfg;
-template <> struct IlCfg<float> { static constexpr int E = 12288, V = 32; };
+template <> struct IlCfg<float> { static constexpr int E = 12288, V = 16; };
 template <> struct IlCfg<double> { static constexpr int E = 6144, V = 16; };
 
+__device__ __forceinline__ long long tiled(int comp, int y, int kx, int ny, int NG, int CC) {
+  return ((long long)(comp * NG + kx / CC) * ny + y) * CC + (kx % CC);
+}
+
 template <typename R>
-__global__ void __launch_bounds__(384) k_rows_fwd2(DemagArgs<R> A) {
+__global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_rows_fwd2(DemagArgs<R> A) {
   using C = typename Cx<R>::T;
   constexpr int E = IlCfg<R>::E, V = IlCfg<R>::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
-  const int Px = ch.Px, lx = ch.lx, nx = ch.nx, nrows = ch.nrows, Sx = ch.Sx;
+  const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
   const int np = E / (3 * Px), nseq = 3 * np;
+  const int CC = E / (3 * ch.Py), NG = Sx / CC;
   const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
-  const int totpairs = (nrows + 1) / 2;
+  const int totpairs = (ny + 1) / 2;
   for (int idx = threadIdx.x; idx < np * Px; idx += blockDim.x) {
     const int qq = idx >> lx, x = idx & (Px - 1);
     const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
@@ -312,13 +321,13 @@ __global__ void __launch_bounds__(384) k_rows_fwd2(DemagArgs<R> A) {
         const R Ms = A.Ms_override;
         const R *v0 = A.m_nat + 3 * ((long long)r0 * nx + x);
         M0x = Ms * v0[0]; M0y = Ms * v0[1]; M0z = Ms * v0[2];
-        if (r1 < nrows) {
+        if (r1 < ny) {
           const R *v1 = A.m_nat + 3 * ((long long)r1 * nx + x);
           M1x = Ms * v1[0]; M1y = Ms * v1[1]; M1z = Ms * v1[2];
         }
       } else {
         load_M<R>(ch, A.m, A.ms, r0, x, M0x, M0y, M0z);
-        if (r1 < nrows) load_M<R>(ch, A.m, A.ms, r1, x, M1x, M1y, M1z);
+        if (r1 < ny) load_M<R>(ch, A.m, A.ms, r1, x, M1x, M1y, M1z);
       }
     }
     C z;
@@ -329,58 +338,53 @@ __global__ void __launch_bounds__(384) k_rows_fwd2(DemagArgs<R> A) {
   }
   __syncthreads();
   fft_il<C, V, false>(buf, lx, IlMap{nseq, 1, 0}, A.tw);
+  // half spectra (kx <= Px/2) of the six real rows of each pair, written in
+  // tiled order: c fastest, then the block's rows, then column group, then comp
   const int half = Px / 2 + 1;
-  const long long plane = (long long)nrows * Sx;
+  const int nrb = 2 * np;
+  const int ngu = (half + CC - 1) / CC;
   C *S = A.S + ch.s_off;
-  for (int idx = threadIdx.x; idx < np * half; idx += blockDim.x) {
-    const int qq = idx / half, kx = idx - qq * half;
-    const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
-    if (pr >= totpairs) continue;
+  const int tot = 3 * ngu * nrb * CC;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int cc = idx % CC, rest = idx / CC;
+    const int rr = rest % nrb, rest2 = rest / nrb;
+    const int g = rest2 % ngu, comp = rest2 / ngu;
+    const int kx = g * CC + cc;
+    const int r = 2 * pair0 + rr;
+    if (kx >= half || r >= ny) continue;
+    const int qq = rr >> 1, h = rr & 1;
+    const int sq = comp == 2 ? 2 : h;
+    const bool take_b = comp == 1 || (comp == 2 && h == 1);
     const int km = (Px - kx) & (Px - 1);
-#pragma unroll
-    for (int sq = 0; sq < 3; ++sq) {
-      const C Z = buf[kx * nseq + 3 * qq + sq], Zm = buf[km * nseq + 3 * qq + sq];
-      C a, b;
-      a.x = (R)0.5 * (Z.x + Zm.x); a.y = (R)0.5 * (Z.y - Zm.y);
-      b.x = (R)0.5 * (Z.y + Zm.y); b.y = (R)0.5 * (Zm.x - Z.x);
-      if (sq == 0) {
-        S[0 * plane + (long long)r0 * Sx + kx] = a;
-        S[1 * plane + (long long)r0 * Sx + kx] = b;
-      } else if (sq == 1) {
-        if (r1 < nrows) {
-          S[0 * plane + (long long)r1 * Sx + kx] = a;
-          S[1 * plane + (long long)r1 * Sx + kx] = b;
-        }
-      } else {
-        S[2 * plane + (long long)r0 * Sx + kx] = a;
-        if (r1 < nrows) S[2 * plane + (long long)r1 * Sx + kx] = b;
-      }
-    }
+    const C Z = buf[kx * nseq + 3 * qq + sq], Zm = buf[km * nseq + 3 * qq + sq];
+    C o;
+    if (!take_b) { o.x = (R)0.5 * (Z.x + Zm.x); o.y = (R)0.5 * (Z.y - Zm.y); }
+    else { o.x = (R)0.5 * (Z.y + Zm.y); o.y = (R)0.5 * (Zm.x - Z.x); }
+    S[tiled(comp, r, kx, ny, NG, CC)] = o;
   }
 }
 
 template <typename R>
-__global__ void __launch_bounds__(384) k_cols2d(DemagArgs<R> A) {
+__global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_cols2d(DemagArgs<R> A) {
   using C = typename Cx<R>::T;
   constexpr int E = IlCfg<R>::E, V = IlCfg<R>::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
-  const int Px = ch.Px, Py = ch.Py, ly = ch.ly, ny = ch.ny, nrows = ch.nrows, Sx = ch.Sx;
-  const int CC = E / (3 * Py);
-  const int kx0 = (int)(blockIdx.x - A.blk_first[c]) * CC;
+  const int Px = ch.Px, Py = ch.Py, ly = ch.ly, ny = ch.ny, Sx = ch.Sx;
+  const int CC = E / (3 * Py), NG = Sx / CC;
+  const int g = (int)(blockIdx.x - A.blk_first[c]);
+  const int kx0 = g * CC;
   const int qx = Px / 2 + 1, qy = Py / 2 + 1;
-  const long long plane = (long long)nrows * Sx;
-  C *S = A.S + ch.s_off;
-  // buf[(comp * Py + y) * CC + col]; rows y >= ny are the zero padding
+  const C *S = A.S + ch.s_off;
+  // buf[(comp * Py + y) * CC + cc]; rows y >= ny are the zero padding
   for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
-    const int col = idx % CC, rest = idx / CC;
+    const int cc = idx % CC, rest = idx / CC;
     const int y = rest % Py, comp = rest / Py;
-    const int kx = kx0 + col;
     C v;
     v.x = 0; v.y = 0;
-    if (y < ny && kx < qx) v = S[comp * plane + (long long)y * Sx + kx];
+    if (y < ny) v = S[((long long)(comp * NG + g) * ny + y) * CC + cc];
     buf[idx] = v;
   }
   __syncthreads();
@@ -388,14 +392,14 @@ __global__ void __launch_bounds__(384) k_cols2d(DemagArgs<R> A) {
   const long long Q = (long long)qx * qy;
   const R *nh = A.nhat[ch.spec];
   for (int idx = threadIdx.x; idx < Py * CC; idx += blockDim.x) {
-    const int col = idx % CC, ky = idx / CC;
-    const int kx = kx0 + col;
+    const int cc = idx % CC, ky = idx / CC;
+    const int kx = kx0 + cc;
     if (kx >= qx) continue;
     const int kyq = ky <= Py / 2 ? ky : Py - ky;
     const R sy = ky <= Py / 2 ? (R)1 : (R)-1;
     const long long qi = (long long)kyq * qx + kx;
     const R Nxx = nh[qi], Nyy = nh[Q + qi], Nzz = nh[2 * Q + qi], Nxy = sy * nh[3 * Q + qi];
-    const int b0 = ky * CC + col, b1 = (Py + ky) * CC + col, b2 = (2 * Py + ky) * CC + col;
+    const int b0 = ky * CC + cc, b1 = (Py + ky) * CC + cc, b2 = (2 * Py + ky) * CC + cc;
     const C Mx = buf[b0], My = buf[b1], Mz = buf[b2];
     C hx_, hy_, hz_;
     hx_.x = -(Nxx * Mx.x + Nxy * My.x);
@@ -408,65 +412,78 @@ __global__ void __launch_bounds__(384) k_cols2d(DemagArgs<R> A) {
   }
   __syncthreads();
   fft_il<C, V, true>(buf, ly, IlMap{CC, 3, Py * CC}, A.tw);
+  C *So = A.S + ch.s_off;
   for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
-    const int col = idx % CC, rest = idx / CC;
+    const int cc = idx % CC, rest = idx / CC;
     const int y = rest % Py, comp = rest / Py;
-    const int kx = kx0 + col;
-    if (y < ny && kx < qx) S[comp * plane + (long long)y * Sx + kx] = buf[idx];
+    if (y < ny) So[((long long)(comp * NG + g) * ny + y) * CC + cc] = buf[idx];
   }
 }
 
 template <typename R>
-__global__ void __launch_bounds__(384) k_rows_inv2(DemagArgs<R> A) {
+__global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_rows_inv2(DemagArgs<R> A) {
   using C = typename Cx<R>::T;
   constexpr int E = IlCfg<R>::E, V = IlCfg<R>::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
+  C *side = buf + E;                        // B[0] and B[Px/2] of each sequence
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
-  const int Px = ch.Px, lx = ch.lx, nx = ch.nx, nrows = ch.nrows, Sx = ch.Sx;
+  const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
   const int np = E / (3 * Px), nseq = 3 * np;
+  const int CC = E / (3 * ch.Py), NG = Sx / CC;
   const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
-  const int totpairs = (nrows + 1) / 2;
   const int half = Px / 2 + 1;
-  const long long plane = (long long)nrows * Sx;
+  const int nrb = 2 * np;
+  const int ngu = (half + CC - 1) / CC;
   const C *S = A.S + ch.s_off;
-  for (int idx = threadIdx.x; idx < np * half; idx += blockDim.x) {
-    const int qq = idx / half, kx = idx - qq * half;
-    const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
-    C a[3], b[3];
-    for (int t = 0; t < 3; ++t) { a[t].x = 0; a[t].y = 0; b[t] = a[t]; }
-    if (pr < totpairs) {
-      a[0] = S[0 * plane + (long long)r0 * Sx + kx];
-      b[0] = S[1 * plane + (long long)r0 * Sx + kx];
-      a[2] = S[2 * plane + (long long)r0 * Sx + kx];
-      if (r1 < nrows) {
-        a[1] = S[0 * plane + (long long)r1 * Sx + kx];
-        b[1] = S[1 * plane + (long long)r1 * Sx + kx];
-        b[2] = S[2 * plane + (long long)r1 * Sx + kx];
-      }
-    }
-    const bool edge = (kx == 0) || (2 * kx == Px);
-#pragma unroll
-    for (int sq = 0; sq < 3; ++sq) {
+  // stage: sequence s = a + i b; a[k] at position k, b[k] at position Px - k
+  // (b[0], b[Px/2] in side[])
+  const int tot = 3 * ngu * nrb * CC;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int cc = idx % CC, rest = idx / CC;
+    const int rr = rest % nrb, rest2 = rest / nrb;
+    const int g = rest2 % ngu, comp = rest2 / ngu;
+    const int kx = g * CC + cc;
+    if (kx >= half) continue;
+    const int r = 2 * pair0 + rr;
+    const int qq = rr >> 1, h = rr & 1;
+    const int sq = comp == 2 ? 2 : h;
+    const bool is_b = comp == 1 || (comp == 2 && h == 1);
+    C v;
+    v.x = 0; v.y = 0;
+    if (r < ny) v = S[tiled(comp, r, kx, ny, NG, CC)];
+    const int s = 3 * qq + sq;
+    if (!is_b) buf[kx * nseq + s] = v;
+    else if (kx == 0) side[2 * s] = v;
+    else if (2 * kx == Px) side[2 * s + 1] = v;
+    else buf[(Px - kx) * nseq + s] = v;
+  }
+  __syncthreads();
+  // z[k] = a[k] + i b[k], z[Px-k] = conj(a[k]) + i conj(b[k]); real parts only at k = 0, Px/2
+  for (int idx = threadIdx.x; idx < nseq * half; idx += blockDim.x) {
+    const int s = idx % nseq, kx = idx / nseq;
+    if (kx == 0 || 2 * kx == Px) {
+      const C a = buf[kx * nseq + s], b = side[2 * s + (kx == 0 ? 0 : 1)];
+      C z;
+      z.x = a.x; z.y = b.x;
+      buf[kx * nseq + s] = z;
+    } else {
+      const C a = buf[kx * nseq + s], b = buf[(Px - kx) * nseq + s];
       C zk, zm;
-      if (edge) {
-        zk.x = a[sq].x; zk.y = b[sq].x;
-        buf[kx * nseq + 3 * qq + sq] = zk;
-      } else {
-        zk.x = a[sq].x - b[sq].y; zk.y = a[sq].y + b[sq].x;
-        zm.x = a[sq].x + b[sq].y; zm.y = b[sq].x - a[sq].y;
-        buf[kx * nseq + 3 * qq + sq] = zk;
-        buf[(Px - kx) * nseq + 3 * qq + sq] = zm;
-      }
+      zk.x = a.x - b.y; zk.y = a.y + b.x;
+      zm.x = a.x + b.y; zm.y = b.x - a.y;
+      buf[kx * nseq + s] = zk;
+      buf[(Px - kx) * nseq + s] = zm;
     }
   }
   __syncthreads();
   fft_il<C, V, true>(buf, lx, IlMap{nseq, 1, 0}, A.tw);
   const R scale = (R)1 / ((R)Px * (R)ch.Py * (R)ch.Pz);
-  const long long Sl = (long long)nrows * ch.hx;
+  const long long Sl = (long long)ny * ch.hx;
   const bool percell = ch.t_off >= 0;
   const float mu0f = (float)mu0;
+  const int totpairs = (ny + 1) / 2;
   for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
     const int qq = idx / nx, x = idx - qq * nx;
     const int pr = pair0 + qq;
@@ -474,12 +491,11 @@ __global__ void __launch_bounds__(384) k_rows_inv2(DemagArgs<R> A) {
     const C z0 = buf[x * nseq + 3 * qq], z1 = buf[x * nseq + 3 * qq + 1], z2 = buf[x * nseq + 3 * qq + 2];
     for (int h = 0; h < 2; ++h) {
       const int r = 2 * pr + h;
-      if (r >= nrows) break;
+      if (r >= ny) break;
       const R Hx = (h == 0 ? z0.x : z1.x) * scale;
       const R Hy = (h == 0 ? z0.y : z1.y) * scale;
       const R Hz = (h == 0 ? z2.x : z2.y) * scale;
-      const int j = r % ch.ny, k = r / ch.ny;
-      const int colr = (x + j + k) & 1;
+      const int colr = (x + r) & 1;
       const long long li = (long long)colr * Sl + (long long)r * ch.hx + (x >> 1);
       if (A.heff) {
         const float zee = percell ? A.tab[ch.t_off + 2 * Sl + li].x : ch.zee;
@@ -508,16 +524,18 @@ void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
   A.m_nat = reinterpret_cast<const R *>(P.m_nat);
   A.Ms_override = (R)P.Ms_override;
   if (P.il2d) {
+    constexpr int T = IlCfg<R>::E / IlCfg<R>::V;
     const size_t sm = (size_t)IlCfg<R>::E * sizeof(C);
+    const size_t sm_inv = P.inv_smem;
     A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
     if (P.ev) cudaEventRecord(P.ev[0], L.stream);
-    k_rows_fwd2<R><<<P.rows_blocks, 384, sm, L.stream>>>(A);
+    k_rows_fwd2<R><<<P.rows_blocks, T, sm, L.stream>>>(A);
     if (P.ev) cudaEventRecord(P.ev[1], L.stream);
     A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
-    k_cols2d<R><<<P.cols_blocks, 384, sm, L.stream>>>(A);
+    k_cols2d<R><<<P.cols_blocks, T, sm, L.stream>>>(A);
     if (P.ev) cudaEventRecord(P.ev[2], L.stream);
     A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
-    k_rows_inv2<R><<<P.rows_blocks, 384, sm, L.stream>>>(A);
+    k_rows_inv2<R><<<P.rows_blocks, T, sm_inv, L.stream>>>(A);
     if (P.ev) cudaEventRecord(P.ev[3], L.stream);
     *L.counter += 3;
     return;
@@ -555,7 +573,7 @@ cudaError_t demag_set_smem_limits() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_rows_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e != cudaSuccess) return e;
-  const int lil = 100 * 1024;
+  const int lil = 200 * 1024;
   const void *fns[6] = {(const void *)k_rows_fwd2<float>, (const void *)k_rows_fwd2<double>,
                         (const void *)k_cols2d<float>, (const void *)k_cols2d<double>,
                         (const void *)k_rows_inv2<float>, (const void *)k_rows_inv2<double>};

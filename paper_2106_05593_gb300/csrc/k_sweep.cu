@@ -58,13 +58,16 @@ __global__ void __launch_bounds__(kSweepBlock) k_sweep_pass(SweepArgs A) {
   const int c = A.blk_chain[blk];
   const ChainDev &ch = A.chains[c];
   const int nx = ch.nx, ny = ch.ny, nz = ch.nz, hx = ch.hx, nrows = ch.nrows;
-  const long long S = (long long)nrows * hx;
-  const long long q = (long long)(blk - A.blk_first[c]) * kSweepBlock + threadIdx.x;
+  // a chain has fewer than 2^31 cells: 32-bit slot arithmetic
+  const unsigned S32 = (unsigned)nrows * (unsigned)hx;
+  const long long S = (long long)S32;
+  const unsigned q32 = (unsigned)(blk - (int)A.blk_first[c]) * (unsigned)kSweepBlock + threadIdx.x;
+  const long long q = (long long)q32;
   const int color = A.color;
-  bool valid = q < S;
-  const int row = valid ? (int)(q / hx) : 0;
-  const int s = (int)(q - (long long)row * hx);
-  const int j = row % ny, k = row / ny;
+  bool valid = q32 < S32;
+  const int row = valid ? (int)(q32 / (unsigned)hx) : 0;
+  const int s = (int)(q32 - (unsigned)row * (unsigned)hx);
+  const int k = (int)((unsigned)row / (unsigned)ny), j = row - k * ny;
   const int p = (j + k + color) & 1;
   const int i = 2 * s + p;
   valid = valid && (i < nx);
@@ -136,7 +139,7 @@ __global__ void __launch_bounds__(kSweepBlock) k_sweep_pass(SweepArgs A) {
     }
 
     // random numbers
-    const unsigned cell = (unsigned)(i + (long long)nx * row);
+    const unsigned cell = (unsigned)i + (unsigned)nx * (unsigned)row;
     const unsigned sweep = *A.sweep_base + A.sweep_off;
     const uint4 r = philox4x32_10(make_uint4(cell, sweep, (unsigned)ch.chain, 0u),
                                   make_uint2(A.key0, A.key1));
@@ -220,7 +223,11 @@ __global__ void __launch_bounds__(kSweepBlock) k_sweep_pass(SweepArgs A) {
     }
 
     const float dF = fex + flin + flong + fan;
-    const float dec = dF - 4.f * log1pf(tt) + logf(u3);
+    const float dl = dF - 4.f * log1pf(tt);
+    // ln u3 < 0: a non-positive dl accepts whatever u3 is, so its log is skipped
+    float dec;
+    if (DEBUG || dl > 0.f) dec = dl + logf(u3);
+    else dec = dl;
     accepted = dec < 0.f;
     if (accepted) mc[q] = make_float4(mpx, mpy, mpz, a.w);
     if (DEBUG) {

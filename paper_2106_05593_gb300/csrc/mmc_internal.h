@@ -167,6 +167,7 @@ struct DemagLaunch {
   const void *m_nat;            // optional natural-order m (float or double, as the plan)
   double Ms_override;           // uniform Ms0 used with m_nat
   bool il2d;                    // 2D interleaved radix-16 kernels (all chains Pz == 1)
+  size_t inv_smem;              // shared memory of the 2D inverse row kernel
 };
 int il_elements(bool fp64);     // complex elements per block of the 2D kernels
 void launch_demag(const Launch &L, const DemagLaunch &P, bool fp64);
