@@ -260,6 +260,31 @@ int64_t mmc_ncell(const mmc_ctx *ctx, int chain);
 mmc_status mmc_checkpoint(mmc_ctx *ctx, void *buf, size_t *len);
 mmc_status mmc_restore(mmc_ctx *ctx, const void *buf, size_t len);
 
+/* Observables of a caller-owned state, with no device allocation by the
+ * library.  The paper has no counterpart: this is a service entry point for
+ * callers that cannot allocate device memory themselves or through a library
+ * call -- code recording a CUDA graph (an allocation breaks the capture),
+ * frameworks whose caching allocator owns all device memory, and latency-
+ * critical loops that cannot pay the implicit synchronization of cudaMalloc.
+ * It computes the same quantities as mmc_observables (current state):
+ *   m    DEVICE, n float4 (mx, my, mz, unused) cells, any order;
+ *   out  DEVICE, 8 doubles: <mx>, <my>, <mz>, <|m|>, <|m|^2> over the finite
+ *        cells, the number of non-finite cells, the number of finite cells, 0;
+ *   hist DEVICE, hist_bins + 1 counters of |m| on [0, hist_max) (last =
+ *        overflow), cleared by the call.
+ * Work is queued on cuda_stream (a cudaStream_t, or NULL for the legacy
+ * stream); the call does not synchronize.  Scratch for the per-block partial
+ * sums is a fixed 128 KiB __device__ array inside the library, so n is limited
+ * to 2,097,152 cells (MMC_ERR_ARG beyond that, with nothing launched).  The
+ * first call on each device looks up that array's device address with the
+ * device current; make that first call before any stream capture.  All calls
+ * on a device share the array: calls whose kernels may overlap on the GPU
+ * (different streams without ordering) race and give wrong results.  Every
+ * call overwrites the partials it reads, so no clearing is needed between
+ * calls. */
+mmc_status mmc_observables_noalloc(const float *m, int64_t n, int hist_bins, double hist_max,
+                                   double *out, unsigned long long *hist, void *cuda_stream);
+
 const char *mmc_status_str(mmc_status s);
 const char *mmc_last_error(void);
 

@@ -21,7 +21,7 @@ EXPORTS = [
     "mmc_set_m", "mmc_get_m", "mmc_init_random", "mmc_sweep", "mmc_sweep_sampled",
     "mmc_demag_update", "mmc_pass_debug", "mmc_observables", "mmc_energy", "mmc_demag_field",
     "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell",
-    "mmc_checkpoint", "mmc_restore", "mmc_status_str", "mmc_last_error",
+    "mmc_checkpoint", "mmc_restore", "mmc_observables_noalloc", "mmc_status_str", "mmc_last_error",
 ]
 
 
@@ -127,6 +127,8 @@ def load():
     L.mmc_checkpoint.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
     L.mmc_restore.restype = st
     L.mmc_restore.argtypes = [vp, vp, C.c_size_t]
+    L.mmc_observables_noalloc.restype = st
+    L.mmc_observables_noalloc.argtypes = [vp, C.c_int64, C.c_int, C.c_double, vp, vp, vp]
     L.mmc_status_str.restype = C.c_char_p
     L.mmc_status_str.argtypes = [st]
     L.mmc_last_error.restype = C.c_char_p

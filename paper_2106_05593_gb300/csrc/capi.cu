@@ -22,6 +22,12 @@ mmc_status fail(mmc_status s, const std::string &msg) {
   return s;
 }
 
+}  // namespace
+
+void mmc::set_last_error(const char *msg) { g_err = msg; }
+
+namespace {
+
 #define CUDA_TRY(expr)                                                                         \
   do {                                                                                         \
     cudaError_t e_ = (expr);                                                                   \

@@ -102,6 +102,9 @@ struct GradCoef {
   int cubic, anis, dmi;
 };
 
+// message returned by mmc_last_error() on the calling thread
+void set_last_error(const char *msg);
+
 // ---------------------------------------------------------------------------
 // host-side physics (host_physics.cpp)
 double langevin(double x);
