@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-demag", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the cuFFT demag timing and the one-chain-per-launch comparison")
     return ap.parse_args()
 
 
@@ -289,6 +291,40 @@ def run_ours(args):
                   "frac": sweep_bytes / (sweep_ms / sweep_cnt * 1e-3) / 1e9 / peak, "unit": "GB/s",
                   "avg_launch_ms": sweep_ms / sweep_cnt}
 
+    # comparisons: demag update through cuFFT, and the same chains one per context
+    compare = None
+    if not args.no_compare:
+        compare = {}
+        if demag:
+            kinds = ("demag_rows_fwd", "demag_cols", "demag_rows_inv")
+            own = sum(phases[k][0] for k in kinds) / max(phases["demag_cols"][1], 1)
+            cf = MMC(specs, demag=1, demag_cufft=1, demag_fp64=int(args.fp64_demag), stream=stream)
+            cf.init_random(seed)
+            ph = cf.phase_times(20, seed)
+            cfm = sum(ph[k][0] for k in kinds) / max(ph["demag_cols"][1], 1)
+            compare["demag_update_ms"] = {"own": own, "cufft": cfm}
+            del cf
+        if len(specs) > 1:
+            plain = [MMC([sp], demag=int(demag), demag_fp64=int(args.fp64_demag), stream=stream) for sp in specs]
+            for k, p1 in enumerate(plain):
+                p1.set_m(g.get_m(k))
+                p1.sweep(SWEEPS_PER_STEP, seed)
+            torch.cuda.synchronize()
+            steps_p = max(1, min(args.steps, 3))
+            p0 = torch.cuda.Event(enable_timing=True)
+            p1e = torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            for _ in range(steps_p):
+                for p1 in plain:
+                    p1.sweep(SWEEPS_PER_STEP, seed)
+            p1e.record(stream)
+            torch.cuda.synchronize()
+            pms = p0.elapsed_time(p1e)
+            compare["plain_one_chain_per_launch"] = {
+                "value": cells_per_step * steps_p / (pms * 1e-3), "unit": UNIT, "steps": steps_p,
+                "batched_over_plain": value / world / (cells_per_step * steps_p / (pms * 1e-3))}
+            del plain
+
     # end to end through the public API: state from pinned host memory, observables back
     e2e = None
     if args.e2e_steps > 0:
@@ -333,7 +369,7 @@ def run_ours(args):
                        "sweeps_per_step": SWEEPS_PER_STEP, "demag": "once per iteration" if demag else "off",
                        "l2": "working set larger than L2" if args.workload in ("chiral512", "granular", "probe8192")
                        else "working set L2-resident (no flush)", "graphs": True},
-            "roofline": roofline, "roofline_sweep_pass": sweep_roof,
+            "roofline": roofline, "roofline_sweep_pass": sweep_roof, "compare": compare,
             "phases_ms": {k: round(v[0] / max(v[1], 1), 5) for k, v in phases.items()},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "kernel_source": src,

@@ -90,7 +90,8 @@ typedef struct {
     int demag;                /* 1: include the demag interaction (Eq. 14)          [0] */
     int demag_per_pass;       /* 1: recompute H_d before each sublattice pass       [0] */
     int demag_fp64;           /* 1: FP64 FFT convolution; 0: FP32 (own kernels)     [0] */
-    int demag_cufft;          /* 1: cuFFT transforms instead of the own FFT kernels [0] */
+    int demag_cufft;          /* 1: cuFFT R2C/C2R transforms (comparison path) for the
+                                 sweep's demag field instead of the own kernels [0] */
     int adapt;                /* 1: adapt the cone angle every 100 sweeps (Sec. II) [1] */
     double theta0_deg;        /* initial cone half-angle                           [30] */
     double sigma_cap;         /* cap of Eq. 13                                   [0.03] */

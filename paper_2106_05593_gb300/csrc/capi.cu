@@ -144,6 +144,7 @@ struct mmc_ctx {
   unsigned long long *d_hist_acc = nullptr, *d_hist_cur = nullptr;
   double *d_obs_out = nullptr;
   DemagPlan batch_plan;
+  std::vector<CufftGroup> cf;           // cuFFT comparison path (demag_cufft)
   std::vector<DemagPlan> single[2];     // per chain and precision (0 FP32, 1 FP64), built lazily
   double *d_g8 = nullptr;
   double *d_Hd = nullptr, *d_eout = nullptr, *d_etab = nullptr;
@@ -286,6 +287,8 @@ void build_chain(ChainHost &H, ChainDev &D, const mmc_chain_desc &d, const mmc_o
   D.pbc = (d.mesh.periodic[0] ? 1 : 0) | (d.mesh.periodic[1] ? 2 : 0) | (d.mesh.periodic[2] ? 4 : 0);
   D.chain = idx;
   D.ncell = H.ncell;
+  divmagic((unsigned)hx, D.hx_m, D.hx_l);
+  divmagic((unsigned)ny, D.ny_m, D.ny_l);
   D.h_off = -1; D.t_off = -1; D.ms_off = -1;
   D.Bx = (float)d.B[0]; D.By = (float)d.B[1]; D.Bz = (float)d.B[2];
   D.gscale = (float)(mt.grain ? mt.grain_exch_scale : 1.0);
@@ -581,6 +584,21 @@ struct PhaseTimer {
 
 void issue_demag(mmc_ctx *c, PhaseTimer *pt = nullptr) {
   Launch L = c->L();
+  if (!c->cf.empty()) {
+    const void *const *nh = c->opt.demag_fp64 ? (const void *const *)c->d_nhat64 : (const void *const *)c->d_nhat32;
+    for (auto &G : c->cf) {
+      cudaEvent_t ev[4];
+      cudaEvent_t *evp = nullptr;
+      if (pt) {
+        int idx[4];
+        for (int k = 0; k < 4; ++k) { idx[k] = (int)pt->used; ev[k] = pt->next(); }
+        for (int k = 0; k < 3; ++k) pt->marks.push_back({k, {idx[k], idx[k + 1]}});
+        evp = ev;
+      }
+      launch_cufft_group(L, G, c->d_ch, c->d_m, c->d_ms, c->d_tab, c->d_heff, nullptr, -1, nh, evp);
+    }
+    return;
+  }
   DemagLaunch D = make_demag_launch(c, c->batch_plan, c->d_heff, nullptr, -1);
   cudaEvent_t ev[4];
   if (pt) {
@@ -690,6 +708,7 @@ void mmc_destroy(mmc_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto &g : c->cf) destroy_cufft_plans(g);
   for (void *p : c->allocs) cudaFree(p);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -706,7 +725,6 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
   if (!(o.hist_max > 0)) return fail(MMC_ERR_ARG, "hist_max must be > 0");
   if (!(o.sigma_cap > 0 && o.sigma_cap < 1)) return fail(MMC_ERR_ARG, "sigma_cap must be in (0, 1)");
   if (!(o.theta0_deg >= 1 && o.theta0_deg <= 180)) return fail(MMC_ERR_ARG, "theta0_deg must be in [1, 180]");
-  if (o.demag_cufft) return fail(MMC_ERR_UNSUPPORTED, "cuFFT demag path not available in this build");
   for (int i = 0; i < nchains; ++i) MMC_TRY(validate(chains[i], o, i));
 
   mmc_ctx *c = new mmc_ctx();
@@ -903,6 +921,37 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     std::vector<int> all(nchains);
     for (int i = 0; i < nchains; ++i) all[i] = i;
     MMC_TRY_OR(build_demag_plan(c, c->batch_plan, all, o.demag_fp64 != 0, false));
+  }
+  if (o.demag && o.demag_cufft) {
+    // one batched cuFFT plan pair per padded size
+    for (int i = 0; i < nchains; ++i) {
+      const ChainDev &D = c->ch[i];
+      CufftGroup *G = nullptr;
+      for (auto &g : c->cf)
+        if (g.Px == D.Px && g.Py == D.Py && g.Pz == D.Pz) G = &g;
+      if (!G) {
+        c->cf.emplace_back();
+        G = &c->cf.back();
+        G->Px = D.Px; G->Py = D.Py; G->Pz = D.Pz;
+        G->fp64 = o.demag_fp64 != 0;
+      }
+      G->nchain += 1;
+    }
+    for (auto &G : c->cf) {
+      std::vector<int> slots;
+      for (int i = 0; i < nchains; ++i)
+        if (c->ch[i].Px == G.Px && c->ch[i].Py == G.Py && c->ch[i].Pz == G.Pz) slots.push_back(i);
+      MMC_TRY_OR(upload(c, &G.chain_of, slots));
+      const size_t rs = G.fp64 ? 8 : 4;
+      const long long P = (long long)G.Px * G.Py * G.Pz;
+      const long long H = (long long)(G.Px / 2 + 1) * G.Py * G.Pz;
+      MMC_TRY_OR(dalloc(c, &G.real, (size_t)G.nchain * 3 * P * rs));
+      MMC_TRY_OR(dalloc(c, &G.cplx, (size_t)G.nchain * 3 * H * 2 * rs));
+      if (make_cufft_plans(G) != cudaSuccess) {
+        mmc_destroy(c);
+        return fail(MMC_ERR_CUDA, "cufftPlanMany failed");
+      }
+    }
   }
   CUDA_TRY_OR(cudaDeviceSynchronize());
   *out = c;

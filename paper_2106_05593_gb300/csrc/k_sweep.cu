@@ -53,7 +53,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 }
 
 template <bool PERCELL, bool DEBUG>
-__global__ void __launch_bounds__(kSweepBlock) k_sweep_pass(SweepArgs A) {
+__global__ void __launch_bounds__(kSweepBlock, 4) k_sweep_pass(SweepArgs A) {
   const int blk = A.blk_base + (int)blockIdx.x;
   const int c = A.blk_chain[blk];
   const ChainDev &ch = A.chains[c];
@@ -65,9 +65,9 @@ __global__ void __launch_bounds__(kSweepBlock) k_sweep_pass(SweepArgs A) {
   const long long q = (long long)q32;
   const int color = A.color;
   bool valid = q32 < S32;
-  const int row = valid ? (int)(q32 / (unsigned)hx) : 0;
+  const int row = valid ? (int)divq(q32, ch.hx_m, ch.hx_l) : 0;
   const int s = (int)(q32 - (unsigned)row * (unsigned)hx);
-  const int k = (int)((unsigned)row / (unsigned)ny), j = row - k * ny;
+  const int k = (int)divq((unsigned)row, ch.ny_m, ch.ny_l), j = row - k * ny;
   const int p = (j + k + color) & 1;
   const int i = 2 * s + p;
   valid = valid && (i < nx);
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kSweepBlock) k_sweep_pass(SweepArgs A) {
 
     // orthonormal basis about n (Duff et al., JCGT 6(1), 2017)
     const float sg = n2 >= 0.f ? 1.f : -1.f;
-    const float aa = -1.f / (sg + n2);
+    const float aa = -__frcp_rn(sg + n2);
     const float bb = n0 * n1 * aa;
     const float e1x = 1.f + sg * n0 * n0 * aa, e1y = sg * bb, e1z = -sg * n0;
     const float e2x = bb, e2y = sg + n1 * n1 * aa, e2z = -n1;
@@ -188,11 +188,20 @@ __global__ void __launch_bounds__(kSweepBlock) k_sweep_pass(SweepArgs A) {
     const float wd[6] = {wx, wx, wy, wy, wz, wz};
     float fex = 0.f;
 #pragma unroll
-    for (int b = 0; b < 6; ++b) {
+    for (int b = 0; b < 4; ++b) {
       const float vx = (mpx - nb[b].x) + (a.x - nb[b].x);
       const float vy = (mpy - nb[b].y) + (a.y - nb[b].y);
       const float vz = (mpz - nb[b].z) + (a.z - nb[b].z);
       fex = fmaf(wd[b] * w[b], dmx * vx + dmy * vy + dmz * vz, fex);
+    }
+    if (nz > 1) {
+#pragma unroll
+      for (int b = 4; b < 6; ++b) {
+        const float vx = (mpx - nb[b].x) + (a.x - nb[b].x);
+        const float vy = (mpy - nb[b].y) + (a.y - nb[b].y);
+        const float vz = (mpz - nb[b].z) + (a.z - nb[b].z);
+        fex = fmaf(wd[b] * w[b], dmx * vx + dmy * vy + dmz * vz, fex);
+      }
     }
     // interfacial DMI: linear in m_i
     float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -223,7 +232,13 @@ __global__ void __launch_bounds__(kSweepBlock) k_sweep_pass(SweepArgs A) {
     }
 
     const float dF = fex + flin + flong + fan;
-    const float dl = dF - 4.f * log1pf(tt);
+    // ln(1 + t): Taylor series through t^7 when |t| <= 0.05 (error below t^8 / 8)
+    float lg;
+    if (fabsf(tt) <= 0.05f)
+      lg = tt * (1.f - tt * (0.5f - tt * (1.f / 3.f - tt * (0.25f - tt * (0.2f - tt * (1.f / 6.f - tt * (1.f / 7.f)))))));
+    else
+      lg = log1pf(tt);
+    const float dl = dF - 4.f * lg;
     // ln u3 < 0: a non-positive dl accepts whatever u3 is, so its log is skipped
     float dec;
     if (DEBUG || dl > 0.f) dec = dl + logf(u3);

@@ -49,6 +49,8 @@ struct ChainDev {
   int Px, Py, Pz;     // padded FFT sizes
   int lx, ly, lz;     // log2 of the padded sizes
   int Sx;             // row stride (complex elements) of the spectrum buffer
+  unsigned hx_m, ny_m;   // division by hx and ny: multiply-shift constants
+  int hx_l, ny_l;        // (Granlund & Montgomery's round-up method, l = ceil(log2 d))
   float wx, wy, wz;   // exchange bond weights V A0 / (h^2 kT)
   float cdx, cdy;     // DMI weights V D0 / (h kT)
   float p2, p4;       // longitudinal: dF/kT = dq (p2 + p4 (2 (|m|^2 - me2) + dq))
@@ -101,6 +103,22 @@ struct GradCoef {
   double V;
   int cubic, anis, dmi;
 };
+
+// q / d for 32-bit unsigned q with precomputed (m, l) of d (l = 0 means d = 1)
+__host__ __device__ inline void divmagic(unsigned d, unsigned &m, int &l) {
+  if (d <= 1) { m = 0; l = 0; return; }
+  l = 0;
+  while ((1u << l) < d && l < 31) ++l;
+  if ((1ull << l) < d) l = 32;
+  m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned divq(unsigned q, unsigned m, int l) {
+  if (l == 0) return q;
+  const unsigned t = __umulhi(m, q);
+  return (t + ((q - t) >> 1)) >> (l - 1);
+}
+#endif
 
 // message returned by mmc_last_error() on the calling thread
 void set_last_error(const char *msg);
@@ -175,6 +193,23 @@ struct DemagLaunch {
 int il_elements(bool fp64);     // complex elements per block of the 2D kernels
 void launch_demag(const Launch &L, const DemagLaunch &P, bool fp64);
 cudaError_t demag_set_smem_limits();
+
+// cuFFT comparison path (k_cufft.cu): chains of one padded size
+struct CufftGroup {
+  int Px = 1, Py = 1, Pz = 1;
+  bool fp64 = false;
+  int nchain = 0;
+  int *chain_of = nullptr;     // device: chain index per slot
+  void *real = nullptr;        // [slot][comp][Pz][Py][Px]
+  void *cplx = nullptr;        // [slot][comp][Pz][Py][Px/2+1]
+  int fwd = 0, inv = 0;        // cufftHandle
+  bool planned = false;
+};
+cudaError_t make_cufft_plans(CufftGroup &G);
+void destroy_cufft_plans(CufftGroup &G);
+cudaError_t launch_cufft_group(const Launch &L, const CufftGroup &G, const ChainDev *chains_d,
+                               const float4 *m, const float *ms, const float4 *tab, float4 *heff,
+                               double *Hd, int Hd_slot, const void *const *nhat, cudaEvent_t *ev);
 
 struct ObsLaunch {
   const ChainDev *chains;

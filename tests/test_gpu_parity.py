@@ -71,15 +71,16 @@ def test_one_pass_with_demag_film(P):
     spec = W.film256(128, B_mT=20.0)
     n = 128 * 128
     m4 = W.smooth_state(spec["mesh"], 3, 0.86)
-    for fp64 in (0, 1):
-        g = P.MMC(spec, demag=1, demag_fp64=fp64)
+    for fp64, cufft in ((0, 0), (1, 0), (0, 1), (1, 1)):
+        g = P.MMC(spec, demag=1, demag_fp64=fp64, demag_cufft=cufft)
         o = O.Oracle(spec)
         H = o.demag_field(m4[:, :3].astype(np.float64), "fft")
         for color in (0, 1):
             g.set_m(m4)
             dec_g, acc_g = g.pass_debug(0, color, 5, 3, 25.0)
             _, acc_o, dec_o, band_o = oracle_pass(spec, m4, color, 5, 0, 3, 25.0, H=H)
-            print("film128 fp64=%d" % fp64, color, compare_pass(dec_g, acc_g, dec_o, acc_o, band_o))
+            print("film128 fp64=%d cufft=%d" % (fp64, cufft), color,
+                  compare_pass(dec_g, acc_g, dec_o, acc_o, band_o))
 
 
 def test_demag_field_fp64(P):
