@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--fp64-demag", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the cuFFT demag timing and the one-chain-per-launch comparison")
+    ap.add_argument("--chains", type=int, default=0, help="use only the first N chains of the workload")
+    ap.add_argument("--profile-run", type=int, default=0,
+                    help="profiling case: run N iterations eagerly (no graphs, no timing) and exit")
     return ap.parse_args()
 
 
@@ -231,8 +234,18 @@ def run_ours(args):
     from paper_2106_05593_gb300 import MMC, build
     build.build()
     specs, demag, desc = workload(args.workload)
+    if args.chains > 0:
+        specs = specs[:args.chains]
+        desc += f" (first {len(specs)} chains)"
     percell = args.workload == "granular"
     stream = torch.cuda.Stream()
+    if args.profile_run > 0:
+        gp = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), use_graphs=0, stream=stream)
+        gp.init_random(1 + rank)
+        gp.sweep(args.profile_run, 1 + rank)
+        torch.cuda.synchronize()
+        print("profile run ok", gp.launches, flush=True)
+        return
     g = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), stream=stream)
     seed = 1 + rank
     g.init_random(seed)

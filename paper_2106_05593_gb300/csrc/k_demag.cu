@@ -312,6 +312,7 @@ __global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_rows_fwd2(DemagAr
   const int CC = E / (3 * ch.Py), NG = Sx / CC;
   const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
   const int totpairs = (ny + 1) / 2;
+#pragma unroll 4
   for (int idx = threadIdx.x; idx < np * Px; idx += blockDim.x) {
     const int qq = idx >> lx, x = idx & (Px - 1);
     const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
@@ -379,6 +380,7 @@ __global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_cols2d(DemagArgs<
   const int qx = Px / 2 + 1, qy = Py / 2 + 1;
   const C *S = A.S + ch.s_off;
   // buf[(comp * Py + y) * CC + cc]; rows y >= ny are the zero padding
+#pragma unroll 8
   for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
     const int cc = idx % CC, rest = idx / CC;
     const int y = rest % Py, comp = rest / Py;
@@ -440,6 +442,7 @@ __global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_rows_inv2(DemagAr
   // stage: sequence s = a + i b; a[k] at position k, b[k] at position Px - k
   // (b[0], b[Px/2] in side[])
   const int tot = 3 * ngu * nrb * CC;
+#pragma unroll 4
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     const int cc = idx % CC, rest = idx / CC;
     const int rr = rest % nrb, rest2 = rest / nrb;
