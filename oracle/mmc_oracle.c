@@ -888,14 +888,13 @@ int64_t orc_pass(orc_ctx *c, double *m, const double *H, int color, uint32_t swe
     return nacc;
 }
 
-/* App. B: serial MMC, exact demag energy change (frozen field plus the self
- * term) and the field updated after every accepted move. */
+/* App. B: serial MMC, cells in index order, the demag field updated after
+ * every accepted move so that every move's Eq. 14 term uses the field of the
+ * current state (plus the self term when demag_self is set). */
 int64_t orc_serial_sweep(orc_ctx *c, double *m, double *H, uint32_t sweep, uint32_t chain,
                          uint64_t seed, double theta_deg)
 {
     double cos_tc = cos(theta_deg * PI / 180.0);
-    int saved = c->p.demag_self;
-    c->p.demag_self = 1;
     const orc_problem *p = &c->p;
     int64_t nacc = 0;
     for (int q = 0; q < c->n; ++q) {
@@ -915,7 +914,6 @@ int64_t orc_serial_sweep(orc_ctx *c, double *m, double *H, uint32_t sweep, uint3
             }
         }
     }
-    c->p.demag_self = saved;
     return nacc;
 }
 
@@ -973,8 +971,10 @@ int64_t orc_run(orc_ctx *c, double *m, int64_t n, orc_run_state *st, orc_obs *ob
     int method = c->n <= 1024 ? 0 : 1;
     for (int64_t s = 0; s < n; ++s) {
         int64_t acc = 0;
-        if (st->demag_mode == 3 && H) {
-            orc_demag_field(c, m, H, method);
+        if (st->demag_mode == 3) {
+            /* App. B serial form: cells in index order; without demag it is the
+               serial Metropolis sweep */
+            if (H) orc_demag_field(c, m, H, method);
             acc = orc_serial_sweep(c, m, H, st->sweep, st->chain, st->seed, st->theta_deg);
         } else {
             if (H) orc_demag_field(c, m, H, method);

@@ -127,7 +127,8 @@ int64_t orc_pass(orc_ctx *c, double *m, const double *H, int color, uint32_t swe
                  int8_t *acc, double *dec, double *band);
 
 /* serial pass in index order with the demag field updated after every accepted move
- * (App. B); H is updated in place. */
+ * (App. B): Eq. 14 against the current field, plus the self term when the
+ * problem's demag_self is set; H is updated in place. */
 int64_t orc_serial_sweep(orc_ctx *c, double *m, double *H, uint32_t sweep,
                          uint32_t chain, uint64_t seed, double theta_deg);
 
@@ -139,7 +140,7 @@ typedef struct {
     double theta_deg;           /* cone half-angle */
     int64_t win_acc, win_att;   /* acceptance window counters */
     int adapt;                  /* adapt the cone angle every 100 sweeps */
-    int demag_mode;             /* 0 off, 1 once per sweep, 2 before each pass, 3 serial exact */
+    int demag_mode;             /* 0 off, 1 once per sweep, 2 before each pass, 3 serial (App. B) */
 } orc_run_state;
 
 /* n full sweeps; obs (may be NULL) accumulates a snapshot every obs_every sweeps */

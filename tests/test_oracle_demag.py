@@ -118,3 +118,22 @@ def test_fft_convolution_equals_direct_sum(mesh, h):
     Hd = o.demag_field(m, "direct")
     Hf = o.demag_field(m, "fft")
     assert np.abs(Hd - Hf).max() < 1e-12 * np.abs(Hd).max()
+
+
+@pytest.mark.parametrize("mesh,h", [((9, 7, 1), (4e-9, 4e-9, 4e-9)),
+                                    ((5, 4, 3), (5e-9, 3e-9, 2e-9))])
+def test_serial_sweep_keeps_the_field_exact(mesh, h):
+    """App. B serial form: after a sweep in which the field was updated after
+    every accepted move, the field equals the direct sum over the final state
+    (a wrong sign, axis flip or offset direction in the update breaks this)."""
+    n = mesh[0] * mesh[1] * mesh[2]
+    rng = np.random.default_rng(4)
+    s = W._base(mesh, h, demag=True, Ms0=rng.uniform(4e5, 9e5, n), T=600.0)
+    o = O.Oracle(s)
+    m = 0.8 * rng.standard_normal((n, 3)) / math.sqrt(3)
+    H0 = o.demag_field(m, "direct")
+    m1, H1, nacc = o.serial_sweep(m, H0, 0, 0, 17, 60.0)
+    assert nacc > n // 4
+    H_ref = o.demag_field(m1, "direct")
+    assert np.abs(H1 - H_ref).max() < 1e-12 * np.abs(H_ref).max()
+

@@ -206,3 +206,28 @@ def test_pass_touches_only_its_sublattice_and_ignores_same_colour_cells():
     others = ~black
     others[r] = False
     assert np.array_equal(dec[others], dec2[others])
+
+
+def test_serial_form_without_demag_is_the_index_order_sweep():
+    """App. B serial form with demag off: one iteration visits the cells one at a
+    time in index order, each decided against the current neighbours.  A
+    sublattice pass decides every cell of its colour from the current state, so
+    applying the pass of each cell's colour in index order and keeping only that
+    cell's result must reproduce the walk exactly."""
+    import workloads as W
+    spec = W.permalloy32(4)
+    o = O.Oracle(spec)
+    rng = np.random.default_rng(3)
+    m = rng.standard_normal((16, 3))
+    m *= 0.85 / np.linalg.norm(m, axis=1, keepdims=True)
+    st = O.new_state(seed=9, chain=0, theta_deg=40.0, adapt=False, demag_mode=3)
+    ms, _, _ = o.run(m.copy(), 1, st)
+    # the same walk by hand: a pass of colour c changes only cells of colour c and
+    # decides each from the current neighbours, so applying the pass of the cell's
+    # colour and keeping only that cell's result reproduces one step of the walk
+    cur = m.copy()
+    for q in range(16):
+        i, j = q % 4, q // 4
+        m1, acc, _, _ = o.sweep_pass(cur, None, (i + j) & 1, 0, 0, 9, 40.0)
+        cur[q] = m1[q]
+    assert np.array_equal(ms, cur)
