@@ -98,6 +98,12 @@ typedef struct {
     int hist_bins;            /* |m| histogram bins on [0, hist_max)              [200] */
     double hist_max;          /*                                                    [1] */
     int use_graphs;           /* 1: capture 100-sweep blocks in CUDA graphs         [1] */
+    int demag_self;           /* serial form (mmc_sweep_serial) only: add the demag
+                                 self term (mu0 V / 2) Ms0^2 dm.N(0).dm to Eq. 14,
+                                 making its demag energy change exact           [0] */
+    int fft_variant;          /* FP32 2D demag kernels: 0 time both on the batch at
+                                 the first update and keep the faster, 1 radix-16
+                                 passes, 2 radix-32 passes                          [0] */
 } mmc_options;
 
 /* One chain of a batch. T_cell (optional, HOST) gives a per-cell temperature;
@@ -192,6 +198,24 @@ mmc_status mmc_sweep_sampled(mmc_ctx *ctx, int64_t n, uint64_t seed, int sample_
 /* Recompute the demag field of every chain from the current state (Eq. 14). */
 mmc_status mmc_demag_update(mmc_ctx *ctx);
 
+/* n MMC iterations of the serial form of the method (App. B) on every chain:
+ * the cells are visited one at a time in index order i + nx (j + ny k); a move's
+ * demag energy change is exact, the frozen-field term of Eq. 14 plus the self
+ * term (mu0 V / 2) Ms0^2 dm . N(0) . dm, and after every accepted move the demag
+ * field of the whole chain is updated by -N(r - q) . dM_q (Newell tensor N), so
+ * every move sees the field of the current state.  The field is recomputed by
+ * the FFT convolution at the start of every iteration (in the precision of
+ * mmc_options.demag_fp64; later updates in FP32).  Philox counters, moves,
+ * acceptance rule (Eq. 5), sweep counter and cone adaptation are those of
+ * mmc_sweep, so the same seed gives the same random numbers per cell and
+ * iteration in both forms.  Without demag this is the serial index-order
+ * Metropolis sweep.  One thread block per chain, O(N^2) work per iteration:
+ * meant for small chains (the comparison of App. B).  Chains whose moments,
+ * field and tensor fit in 200 KB (48 B per cell in 2D, 56 B in 3D, about
+ * 4,200 cells in 2D) run from shared memory, larger ones from global memory.
+ * demag_per_pass has no meaning here; options.use_graphs is not used. */
+mmc_status mmc_sweep_serial(mmc_ctx *ctx, int64_t n, uint64_t seed);
+
 /* One sublattice pass of one chain with explicit sweep index and cone angle,
  * leaving the sweep counter, the adaptation window and the other chains alone:
  * diagnostic form used by parity checks.  Accepted moves are written to the
@@ -245,6 +269,16 @@ mmc_status mmc_energy_grad(mmc_ctx *ctx, int chain, const void *m, int fp64, con
  * rows inverse, 3 sublattice pass, 4 observables, 5 window/adaptation step.
  * Both arrays have 6 entries (HOST). */
 mmc_status mmc_phase_times(mmc_ctx *ctx, int64_t n, uint64_t seed, double ms[6], int64_t count[6]);
+
+/* FFT variant of the batch's FP32 2D demag kernels (1 radix 16, 2 radix 32;
+ * 0 when the batch does not use them) and, when mmc_options.fft_variant was 0,
+ * the per-update times in ms that the create-time timing measured for the two
+ * variants (else zeros).  The variants compute the same convolution with FP32
+ * rounding in a different order, so the demag field, and through it the chain,
+ * can differ between them at rounding level; set the variant explicitly where
+ * runs must repeat bit for bit across contexts.  (HOST outputs.)  Not a paper
+ * quantity: a tuning record of this implementation. */
+mmc_status mmc_fft_tuning(const mmc_ctx *ctx, int *variant, double ms[2]);
 
 /* Number of kernels the library launched since create (all kinds). */
 int64_t mmc_kernel_launches(const mmc_ctx *ctx);

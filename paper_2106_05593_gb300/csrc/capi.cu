@@ -97,6 +97,7 @@ struct DemagPlan {
   size_t cols_smem = 0;
   void *spec = nullptr;
   bool il2d = false;
+  int fft_variant = 1;
   size_t inv_smem = 0;
   bool ready = false;
 };
@@ -145,7 +146,15 @@ struct mmc_ctx {
   double *d_obs_out = nullptr;
   DemagPlan batch_plan;
   std::vector<CufftGroup> cf;           // cuFFT comparison path (demag_cufft)
+  int tuned_variant = 0;                // FFT variant picked at create (0: not tuned)
+  double tune_ms[2] = {0.0, 0.0};       // per-update time of the two variants when tuned
   std::vector<DemagPlan> single[2];     // per chain and precision (0 FP32, 1 FP64), built lazily
+  // serial exact-demag sweep: real-space tensors per set, proposals scratch
+  bool serial_ready = false;
+  float **d_oct = nullptr;
+  int4 *d_oct_dim = nullptr;
+  float4 *d_prop = nullptr;
+  size_t serial_smem = 0;
   double *d_g8 = nullptr;
   double *d_Hd = nullptr, *d_eout = nullptr, *d_etab = nullptr;
   float4 *d_nat = nullptr;
@@ -230,6 +239,11 @@ void parallel_for(long long n, F fn) {
   for (auto &x : th) x.join();
 }
 
+bool has_percell(const mmc_chain_desc &d) {
+  const mmc_material &mt = d.material;
+  return mt.Ms0_cell || mt.K1_cell || mt.e_A_cell || mt.Tc_cell || d.T_cell;
+}
+
 mmc_status validate(const mmc_chain_desc &d, const mmc_options &o, int idx) {
   const std::string w = "chain " + std::to_string(idx) + ": ";
   const mmc_mesh &m = d.mesh;
@@ -267,8 +281,11 @@ mmc_status validate(const mmc_chain_desc &d, const mmc_options &o, int idx) {
   return MMC_OK;
 }
 
-// tables of one chain (host)
-void build_chain(ChainHost &H, ChainDev &D, const mmc_chain_desc &d, const mmc_options &o, int idx) {
+// tables of one chain (host); a batch in which any chain has per-cell inputs
+// gives every chain per-cell tables (force_percell), since one sweep launch
+// reads all chains of the batch the same way
+void build_chain(ChainHost &H, ChainDev &D, const mmc_chain_desc &d, const mmc_options &o, int idx,
+                 bool force_percell) {
   const mmc_material &mt = d.material;
   H.mesh = d.mesh;
   for (int a = 0; a < 3; ++a) H.h[a] = d.cellsize[a];
@@ -276,7 +293,7 @@ void build_chain(ChainHost &H, ChainDev &D, const mmc_chain_desc &d, const mmc_o
   H.T = d.T; H.Tc = mt.Tc; H.Ms0 = mt.Ms0; H.K1 = mt.K1; H.K2 = mt.K2;
   H.mu = mt.mu_atom > 0 ? mt.mu_atom : muB;
   H.cubic = mt.aniso_cubic;
-  H.percell = mt.Ms0_cell || mt.K1_cell || mt.e_A_cell || mt.Tc_cell || d.T_cell;
+  H.percell = has_percell(d) || force_percell;
   const int nx = d.mesh.nx, ny = d.mesh.ny, nz = d.mesh.nz;
   H.ncell = 1LL * nx * ny * nz;
   const int hx = (nx + 1) / 2;
@@ -289,6 +306,7 @@ void build_chain(ChainHost &H, ChainDev &D, const mmc_chain_desc &d, const mmc_o
   D.ncell = H.ncell;
   divmagic((unsigned)hx, D.hx_m, D.hx_l);
   divmagic((unsigned)ny, D.ny_m, D.ny_l);
+  divmagic((unsigned)nx, D.nx_m, D.nx_l);
   D.h_off = -1; D.t_off = -1; D.ms_off = -1;
   D.Bx = (float)d.B[0]; D.By = (float)d.B[1]; D.Bz = (float)d.B[2];
   D.gscale = (float)(mt.grain ? mt.grain_exch_scale : 1.0);
@@ -430,10 +448,13 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
       colf.push_back((long long)colc.size());
       for (int b = 0; b < nc; ++b) colc.push_back((int)t);
     }
-    rsmem = csmem = (size_t)E * csz;
+    // data block, then the block's twiddle table (Px entries for the row kernels,
+    // Py for the column kernel); the inverse row kernel keeps a side array between
     int minPx = 1 << 30;
     for (const ChainDev &D : table) minPx = std::min(minPx, D.Px);
-    P.inv_smem = (size_t)(E + 2 * (E / minPx)) * csz;
+    rsmem = (size_t)(E + maxPx) * csz;
+    csmem = (size_t)(E + maxPyPz) * csz;
+    P.inv_smem = (size_t)(E + 2 * (E / minPx) + maxPx) * csz;
   } else {
     const int Gmax = std::max(maxPx / 8, 1);
     T = std::min(512, std::max(64, 3 * Gmax));
@@ -480,6 +501,8 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
   P.cols_cc = cc;
   P.cols_smem = csmem;
   P.fp64 = fp64;
+  P.fft_variant = c->opt.fft_variant == 1 || c->opt.fft_variant == 2 ? c->opt.fft_variant
+                  : (c->tuned_variant ? c->tuned_variant : 1);
   MMC_TRY(dalloc(c, &P.spec, (size_t)spec_elems * csz));
   CUDA_TRY(cudaMemset(P.spec, 0, (size_t)spec_elems * csz));   // padding columns stay defined
   P.ready = true;
@@ -513,6 +536,7 @@ DemagLaunch make_demag_launch(mmc_ctx *c, const DemagPlan &P, float4 *heff, doub
   D.m_nat = nullptr;
   D.Ms_override = 0.0;
   D.il2d = P.il2d;
+  D.fft_variant = P.fft_variant;
   D.inv_smem = P.inv_smem;
   return D;
 }
@@ -686,6 +710,62 @@ mmc_status sweep_impl(mmc_ctx *c, int64_t n, uint64_t seed, int sample_every) {
   return MMC_OK;
 }
 
+mmc_status serial_prepare(mmc_ctx *c) {
+  if (c->serial_ready) return MMC_OK;
+  if (c->any_demag) {
+    std::vector<float *> ptrs;
+    std::vector<int4> dims;
+    for (auto &ss : c->specs) {
+      const int ox = std::max(ss.Px / 2, 1), oy = std::max(ss.Py / 2, 1), oz = std::max(ss.Pz / 2, 1);
+      std::vector<double> oct;
+      demag_octant(ss.h, ox, oy, oz, oct);
+      const size_t n = (size_t)ox * oy * oz;
+      std::vector<float> soa(6 * n);
+      for (size_t q = 0; q < n; ++q)
+        for (int k = 0; k < 6; ++k) soa[k * n + q] = (float)oct[6 * q + k];
+      float *d = nullptr;
+      MMC_TRY(upload(c, &d, soa));
+      ptrs.push_back(d);
+      dims.push_back(make_int4(ox, oy, oz, 0));
+    }
+    MMC_TRY(upload(c, &c->d_oct, ptrs));
+    MMC_TRY(upload(c, &c->d_oct_dim, dims));
+  }
+  MMC_TRY(dalloc_t(c, &c->d_prop, (size_t)c->m_total));
+  // shared memory: the largest need among the chains that fit in 200 KB
+  size_t need = 0;
+  for (const ChainDev &D : c->ch) {
+    const size_t b = serial_smem_need(D);
+    if (b <= 200 * 1024) need = std::max(need, b);
+  }
+  c->serial_smem = need;
+  if (need > 0) CUDA_TRY(serial_set_smem_limit(need));
+  c->serial_ready = true;
+  return MMC_OK;
+}
+
+SerialLaunch serial_launch(mmc_ctx *c, unsigned off, unsigned key0, unsigned key1) {
+  SerialLaunch P;
+  P.chains = c->d_ch;
+  P.st = c->d_st;
+  P.m = c->d_m;
+  P.heff = c->d_heff;
+  P.tab = c->d_tab;
+  P.ms = c->d_ms;
+  P.oct = (const float *const *)c->d_oct;
+  P.oct_dim = c->d_oct_dim;
+  P.prop = c->d_prop;
+  P.sweep_base = c->d_sweep_base;
+  P.sweep_off = off;
+  P.key0 = key0;
+  P.key1 = key1;
+  P.nchains = c->nchains;
+  P.percell = c->any_percell;
+  P.self = c->opt.demag_self != 0;
+  P.smem = c->serial_smem;
+  return P;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -701,6 +781,8 @@ mmc_status mmc_default_options(mmc_options *o) {
   o->hist_bins = 200;
   o->hist_max = 1.0;
   o->use_graphs = 1;
+  o->demag_self = 0;
+  o->fft_variant = 0;
   return MMC_OK;
 }
 
@@ -726,6 +808,15 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
   if (!(o.sigma_cap > 0 && o.sigma_cap < 1)) return fail(MMC_ERR_ARG, "sigma_cap must be in (0, 1)");
   if (!(o.theta0_deg >= 1 && o.theta0_deg <= 180)) return fail(MMC_ERR_ARG, "theta0_deg must be in [1, 180]");
   for (int i = 0; i < nchains; ++i) MMC_TRY(validate(chains[i], o, i));
+  {
+    bool any_pc = false, any_cubic = false;
+    for (int i = 0; i < nchains; ++i) {
+      any_pc |= has_percell(chains[i]);
+      any_cubic |= chains[i].material.aniso_cubic != 0;
+    }
+    if (any_pc && any_cubic)
+      return fail(MMC_ERR_UNSUPPORTED, "cubic anisotropy in a batch with per-cell material or temperature");
+  }
 
   mmc_ctx *c = new mmc_ctx();
   c->nchains = nchains;
@@ -743,8 +834,10 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
   CUDA_TRY_OR(demag_set_smem_limits());
   c->hc.resize(nchains);
   c->ch.resize(nchains);
+  bool batch_percell = false;
+  for (int i = 0; i < nchains; ++i) batch_percell |= has_percell(chains[i]);
   for (int i = 0; i < nchains; ++i) {
-    build_chain(c->hc[i], c->ch[i], chains[i], o, i);
+    build_chain(c->hc[i], c->ch[i], chains[i], o, i, batch_percell);
     c->any_demag |= (o.demag != 0);
     c->any_percell |= c->hc[i].percell;
     c->max_ncell = std::max(c->max_ncell, c->hc[i].ncell);
@@ -773,7 +866,7 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
       // spectrum row stride: a multiple of 8 and of the column-group width
       // 4096 / Py of the tiled 2D layout
       {
-        const int g = std::max(8, D.Pz == 1 ? 4096 / D.Py : 8);
+        const int g = std::max(8, D.Pz == 1 ? il_elements(false) / 3 / D.Py : 8);
         D.Sx = (D.Px / 2 + 1 + g - 1) / g * g;
       }
       D.s_off = soff;
@@ -922,6 +1015,30 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     for (int i = 0; i < nchains; ++i) all[i] = i;
     MMC_TRY_OR(build_demag_plan(c, c->batch_plan, all, o.demag_fp64 != 0, false));
   }
+  if (o.demag && !o.demag_cufft && !o.demag_fp64 && c->batch_plan.il2d && o.fft_variant == 0) {
+    // time both FP32 variants on this batch (a few updates each) and keep the faster
+    float best = 1e30f;
+    int pick = 1;
+    cudaEvent_t e0, e1;
+    CUDA_TRY_OR(cudaEventCreate(&e0));
+    CUDA_TRY_OR(cudaEventCreate(&e1));
+    for (int v = 1; v <= 2; ++v) {
+      c->batch_plan.fft_variant = v;
+      issue_demag(c);
+      CUDA_TRY_OR(cudaEventRecord(e0, c->stream));
+      for (int r = 0; r < 5; ++r) issue_demag(c);
+      CUDA_TRY_OR(cudaEventRecord(e1, c->stream));
+      CUDA_TRY_OR(cudaEventSynchronize(e1));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      c->tune_ms[v - 1] = ms / 5.0;
+      if (ms < best) { best = ms; pick = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->batch_plan.fft_variant = pick;
+    c->tuned_variant = pick;
+  }
   if (o.demag && o.demag_cufft) {
     // one batched cuFFT plan pair per padded size
     for (int i = 0; i < nchains; ++i) {
@@ -1069,6 +1186,27 @@ mmc_status mmc_sweep(mmc_ctx *c, int64_t n, uint64_t seed) {
 mmc_status mmc_sweep_sampled(mmc_ctx *c, int64_t n, uint64_t seed, int sample_every) {
   if (sample_every < 1) return fail(MMC_ERR_ARG, "sample_every must be >= 1");
   MMC_TRY(sweep_impl(c, n, seed, sample_every));
+  return MMC_OK;
+}
+
+mmc_status mmc_sweep_serial(mmc_ctx *c, int64_t n, uint64_t seed) {
+  if (!c) return fail(MMC_ERR_ARG, "null context");
+  if (n < 0) return fail(MMC_ERR_ARG, "negative sweep count");
+  MMC_TRY(serial_prepare(c));
+  const unsigned key0 = (unsigned)(seed & 0xffffffffu), key1 = (unsigned)(seed >> 32);
+  Launch L = c->L();
+  while (n > 0) {
+    const int k = (int)std::min<int64_t>(n, 100 - (int64_t)(c->host_sweep % 100));
+    for (int off = 0; off < k; ++off) {
+      if (c->any_demag) issue_demag(c);
+      launch_serial_sweep(L, serial_launch(c, (unsigned)off, key0, key1));
+    }
+    const int adapt_now = ((c->host_sweep + k) % 100 == 0) ? 1 : 0;
+    launch_advance(L, c->d_st, c->nchains, (unsigned)k, c->d_sweep_base, adapt_now, c->opt.adapt, 1.f, 180.f);
+    MMC_TRY(check_launch());
+    c->host_sweep += (uint64_t)k;
+    n -= k;
+  }
   return MMC_OK;
 }
 
@@ -1316,6 +1454,14 @@ mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[6], i
 }
 
 int64_t mmc_kernel_launches(const mmc_ctx *c) { return c ? c->launches : 0; }
+
+mmc_status mmc_fft_tuning(const mmc_ctx *c, int *variant, double ms[2]) {
+  if (!c || !variant || !ms) return fail(MMC_ERR_ARG, "null argument");
+  *variant = c->batch_plan.ready && c->batch_plan.il2d ? c->batch_plan.fft_variant : 0;
+  ms[0] = c->tune_ms[0];
+  ms[1] = c->tune_ms[1];
+  return MMC_OK;
+}
 int mmc_nchains(const mmc_ctx *c) { return c ? c->nchains : 0; }
 int64_t mmc_ncell(const mmc_ctx *c, int chain) {
   if (!c || chain < 0 || chain >= c->nchains) return 0;

@@ -8,7 +8,8 @@
 // every thread loads V complex values (V / R butterflies) into registers,
 // all threads synchronize, then twiddle, transform and store them; a sequence of
 // length N takes ceil(log16 N) passes.  The inverse pass is conj(F(conj(x))).
-// Twiddles come from the FP64-built table tw[t] = exp(-2 pi i t / 4096).
+// Twiddles come from the FP64-built table tw[t] = exp(-2 pi i t / 4096), or
+// from a block-local copy of the N entries a transform of length N uses.
 #pragma once
 
 #include "fft.cuh"
@@ -54,24 +55,62 @@ template <typename C> __device__ __forceinline__ void dft16(C *x) {
   }
 }
 
+// W32^m = exp(-2 pi i m / 32), m = 0..21 (the twiddles n2 k1 of a 4 x 8 split),
+// cos and -sin of 2 pi m / 32 rounded to double; m is a compile-time constant
+// after unrolling, so the selection folds away
+template <typename C> __device__ __forceinline__ C cmul_w32(C a, int m) {
+  using R = decltype(a.x);
+  const double tc[22] = {1.0, 0.9807852804032304, 0.9238795325112867, 0.8314696123025452, 0.7071067811865476, 0.5555702330196023, 0.38268343236508984, 0.19509032201612833, 0.0, -0.1950903220161282, -0.3826834323650897, -0.555570233019602, -0.7071067811865475, -0.8314696123025453, -0.9238795325112867, -0.9807852804032304, -1.0, -0.9807852804032304, -0.9238795325112868, -0.8314696123025455, -0.7071067811865477, -0.5555702330196022};
+  const double ts[22] = {0.0, -0.19509032201612825, -0.3826834323650898, -0.5555702330196022, -0.7071067811865475, -0.8314696123025452, -0.9238795325112867, -0.9807852804032304, -1.0, -0.9807852804032304, -0.9238795325112867, -0.8314696123025455, -0.7071067811865476, -0.5555702330196022, -0.3826834323650899, -0.1950903220161286, 0.0, 0.19509032201612836, 0.38268343236508967, 0.555570233019602, 0.7071067811865475, 0.8314696123025452};
+  const R c = (R)tc[m], s = (R)ts[m];
+  C r;
+  r.x = a.x * c - a.y * s;
+  r.y = a.x * s + a.y * c;
+  return r;
+}
+
+// forward 32-point DFT in registers: 4 x 8 Cooley-Tukey (n = 8 n1 + n2, k = k1 + 4 k2)
+template <typename C> __device__ __forceinline__ void dft32(C *x) {
+  C a[32];
+#pragma unroll
+  for (int n2 = 0; n2 < 8; ++n2) {
+    C t[4] = {x[n2], x[8 + n2], x[16 + n2], x[24 + n2]};
+    dft4(t);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) a[4 * n2 + k1] = (n2 * k1) ? cmul_w32(t[k1], n2 * k1) : t[k1];
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C t[8] = {a[k1], a[4 + k1], a[8 + k1], a[12 + k1], a[16 + k1], a[20 + k1], a[24 + k1], a[28 + k1]};
+    dft8(t);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) x[k1 + 4 * k2] = t[k2];
+  }
+}
+
 template <typename C, int R> __device__ __forceinline__ void dft_r(C *u) {
-  if (R == 16) dft16(u);
+  if (R == 32) dft32(u);
+  else if (R == 16) dft16(u);
   else if (R == 8) dft8(u);
   else if (R == 4) dft4(u);
   else if (R == 2) dft2(u[0], u[1]);
 }
 
 struct IlMap {
-  int nseq, ngroups, gstride;
+  int lnseq;        // log2 of the interleaved sequences per group (a power of two)
+  int ngroups, gstride;
 };
 
 // one radix-R Stockham pass over all interleaved sequences (p = product of the
-// radices already done); V values per thread
-template <typename C, int R, int V, bool INV>
+// radices already done); V values per thread.  ZIN (first pass only): the upper
+// half of every sequence is known to be zero and is not read.  HALFOUT (last
+// pass only): only the lower half of every output sequence is stored.
+template <typename C, int R, int V, bool INV, bool ZIN, bool HALFOUT>
 __device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C *__restrict__ tw, int twshift) {
   constexpr int NB = V / R;
-  const int nbf = N / R;
-  const int total = mp.ngroups * nbf * mp.nseq;
+  const int nbf = N / R;              // compile-time: N and R are template constants
+  const int nseq = 1 << mp.lnseq;
+  const int total = mp.ngroups * (nbf << mp.lnseq);
   C v[V];
   int addr[NB], kk[NB];
   bool on[NB];
@@ -79,8 +118,8 @@ __device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C 
   for (int i = 0; i < NB; ++i) {
     const int bf = threadIdx.x + i * blockDim.x;
     on[i] = bf < total;
-    const int s = bf % mp.nseq;
-    const int rest = bf / mp.nseq;
+    const int s = bf & (nseq - 1);
+    const int rest = bf >> mp.lnseq;
     const int b = rest % nbf;
     const int g = rest / nbf;
     kk[i] = b & (p - 1);
@@ -88,13 +127,18 @@ __device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C 
     if (on[i]) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        C t = buf[addr[i] + (b + r * nbf) * mp.nseq];
+        C t;
+        if (ZIN && 2 * r >= R) {          // element b + r N / R >= N / 2
+          t.x = 0; t.y = 0;
+        } else {
+          t = buf[addr[i] + ((b + r * nbf) << mp.lnseq)];
+        }
         if (INV) t.y = -t.y;
         v[i * R + r] = t;
       }
     }
     // output position of element r: (b - k) R + k + r p
-    addr[i] += ((b - kk[i]) * R + kk[i]) * mp.nseq;
+    addr[i] += ((b - kk[i]) * R + kk[i]) << mp.lnseq;
   }
   __syncthreads();
 #pragma unroll
@@ -105,50 +149,56 @@ __device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C 
     if (k != 0) {
       const int step = (k * (N / (p * R))) << twshift;
 #pragma unroll
-      for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw[(r * step) & 4095]);
+      for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw[r * step]);   // r step < N << twshift
     }
     dft_r<C, R>(u);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+      if (HALFOUT && 2 * r >= R) continue;   // last pass: output k + r N / R >= N / 2
       C t = u[r];
       if (INV) t.y = -t.y;
-      buf[addr[i] + r * p * mp.nseq] = t;
+      buf[addr[i] + ((r * p) << mp.lnseq)] = t;
     }
   }
   __syncthreads();
 }
 
-// Compile-time pass schedule for N = 2^LOGN: radix 16 while possible, then the
-// remaining factor; the passes are straight-line code so every pass's register
+// Compile-time pass schedule for N = 2^LOGN: radix 32 (V >= 32) or 16 while
+// possible, then the remaining factor; the passes are straight-line code so every pass's register
 // arrays have their own short lifetime.
-template <typename C, int V, bool INV, int N, int P>
+template <typename C, int V, bool INV, int N, int P, bool ZIN, bool HALFOUT>
 __device__ __forceinline__ void fft_passes(C *buf, IlMap mp, const C *__restrict__ tw, int twshift) {
   if constexpr (P < N) {
     constexpr int REM = N / P;
-    constexpr int R = REM >= 16 ? 16 : REM;
-    il_pass<C, R, V, INV>(buf, N, P, mp, tw, twshift);
-    fft_passes<C, V, INV, N, P * R>(buf, mp, tw, twshift);
+    constexpr int RMAX = V >= 32 ? 32 : 16;      // radix 32 when a thread holds 32 values
+    constexpr int R = REM >= RMAX ? RMAX : REM;
+    il_pass<C, R, V, INV, ZIN && P == 1, HALFOUT && P * R == N>(buf, N, P, mp, tw, twshift);
+    fft_passes<C, V, INV, N, P * R, ZIN, HALFOUT>(buf, mp, tw, twshift);
   }
 }
 
 // Full transform (forward or unnormalized inverse), 2 <= N <= 4096.
-// blockDim.x * V must cover ngroups * nseq * N elements.
-template <typename C, int V, bool INV>
-__device__ __forceinline__ void fft_il(C *buf, int logN, IlMap mp, const C *__restrict__ tw) {
-  const int twshift = 12 - logN;
+// blockDim.x * V must cover ngroups * nseq * N elements.  tw is either the
+// 4096-entry table exp(-2 pi i t / 4096) (local = false) or a table of the N
+// entries exp(-2 pi i t / N) (local = true, typically staged in shared memory).
+// ZIN: the upper half of every input sequence is zero (zero padding) and is
+// never read; HALFOUT: only the lower half of every output is written back.
+template <typename C, int V, bool INV, bool ZIN = false, bool HALFOUT = false>
+__device__ __forceinline__ void fft_il(C *buf, int logN, IlMap mp, const C *__restrict__ tw, bool local) {
+  const int twshift = local ? 0 : 12 - logN;
   switch (logN) {
-    case 1: fft_passes<C, V, INV, 2, 1>(buf, mp, tw, twshift); break;
-    case 2: fft_passes<C, V, INV, 4, 1>(buf, mp, tw, twshift); break;
-    case 3: fft_passes<C, V, INV, 8, 1>(buf, mp, tw, twshift); break;
-    case 4: fft_passes<C, V, INV, 16, 1>(buf, mp, tw, twshift); break;
-    case 5: fft_passes<C, V, INV, 32, 1>(buf, mp, tw, twshift); break;
-    case 6: fft_passes<C, V, INV, 64, 1>(buf, mp, tw, twshift); break;
-    case 7: fft_passes<C, V, INV, 128, 1>(buf, mp, tw, twshift); break;
-    case 8: fft_passes<C, V, INV, 256, 1>(buf, mp, tw, twshift); break;
-    case 9: fft_passes<C, V, INV, 512, 1>(buf, mp, tw, twshift); break;
-    case 10: fft_passes<C, V, INV, 1024, 1>(buf, mp, tw, twshift); break;
-    case 11: fft_passes<C, V, INV, 2048, 1>(buf, mp, tw, twshift); break;
-    case 12: fft_passes<C, V, INV, 4096, 1>(buf, mp, tw, twshift); break;
+    case 1: fft_passes<C, V, INV, 2, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 2: fft_passes<C, V, INV, 4, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 3: fft_passes<C, V, INV, 8, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 4: fft_passes<C, V, INV, 16, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 5: fft_passes<C, V, INV, 32, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 6: fft_passes<C, V, INV, 64, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 7: fft_passes<C, V, INV, 128, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 8: fft_passes<C, V, INV, 256, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 9: fft_passes<C, V, INV, 512, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 10: fft_passes<C, V, INV, 1024, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 11: fft_passes<C, V, INV, 2048, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 12: fft_passes<C, V, INV, 4096, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
     default: break;
   }
 }

@@ -308,6 +308,26 @@ static void fft_inplace(std::complex<double> *a, int n, long long s) {
   }
 }
 
+// the six tensor components (xx yy zz xy xz yz) at offsets (x, y, z) h with
+// 0 <= x < ox, 0 <= y < oy, 0 <= z < oz, interleaved: oct[6 (x + ox (y + oy z)) + c];
+// the other octants follow by symmetry (xy odd in x and y, xz in x and z, yz in y and z)
+void demag_octant(const double h[3], int ox, int oy, int oz, std::vector<double> &oct) {
+  oct.assign((size_t)6 * ox * oy * oz, 0.0);
+  TensorRules rules(h);
+  const int nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  const long long total = 1LL * ox * oy * oz;
+  for (int t = 0; t < nth; ++t)
+    th.emplace_back([&, t]() {
+      for (long long q = t; q < total; q += nth) {
+        const int x = (int)(q % ox), y = (int)((q / ox) % oy), z = (int)(q / (1LL * ox * oy));
+        const double R[3] = {x * h[0], y * h[1], z * h[2]};
+        tensor_with(h, R, rules, &oct[6 * q]);
+      }
+    });
+  for (auto &x : th) x.join();
+}
+
 void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double> &out) {
   const int ncomp = Pz > 1 ? 6 : 4;
   const int qx = Px / 2 + 1, qy = Py / 2 + 1, qz = Pz / 2 + 1;
@@ -319,22 +339,8 @@ void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double
   // offsets -P/2 never reach a mesh cell when n <= P/2 and are left at zero,
   // which keeps every spectrum real)
   const int ox = std::max(Px / 2, 1), oy = std::max(Py / 2, 1), oz = std::max(Pz / 2, 1);
-  std::vector<double> oct((size_t)6 * ox * oy * oz);
-  TensorRules rules(h);
-  {
-    const int nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-    std::vector<std::thread> th;
-    const long long total = 1LL * ox * oy * oz;
-    for (int t = 0; t < nth; ++t)
-      th.emplace_back([&, t]() {
-        for (long long q = t; q < total; q += nth) {
-          const int x = (int)(q % ox), y = (int)((q / ox) % oy), z = (int)(q / (1LL * ox * oy));
-          const double R[3] = {x * h[0], y * h[1], z * h[2]};
-          tensor_with(h, R, rules, &oct[6 * q]);
-        }
-      });
-    for (auto &x : th) x.join();
-  }
+  std::vector<double> oct;
+  demag_octant(h, ox, oy, oz, oct);
   static const int comp_map[6] = {0, 1, 2, 3, 4, 5};  // xx yy zz xy xz yz
   std::vector<std::complex<double>> a((size_t)P);
   for (int c = 0; c < ncomp; ++c) {

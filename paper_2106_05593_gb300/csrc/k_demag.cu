@@ -51,7 +51,7 @@ __device__ __forceinline__ int pairs_per_block(int Px) {
 template <typename R>
 __device__ __forceinline__ void load_M(const ChainDev &ch, const float4 *m, const float *ms, int r, int x,
                                        R &Mx, R &My, R &Mz) {
-  const int j = r % ch.ny, k = r / ch.ny;
+  const int k = (int)divq((unsigned)r, ch.ny_m, ch.ny_l), j = r - k * ch.ny;
   const int col = (x + j + k) & 1;
   const long long S = (long long)ch.nrows * ch.hx;
   const long long idx = (long long)col * S + (long long)r * ch.hx + (x >> 1);
@@ -254,7 +254,7 @@ __global__ void k_rows_inv(DemagArgs<R> A) {
   const bool percell = ch.t_off >= 0;
   const double mu0d = mu0;
   for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
-    const int qq = idx / nx, x = idx - qq * nx;
+    const int qq = (int)divq((unsigned)idx, ch.nx_m, ch.nx_l), x = idx - qq * nx;
     const int pr = pair0 + qq;
     if (pr >= totpairs) continue;
     const C z0 = buf[(3 * qq + 0) * Px + x], z1 = buf[(3 * qq + 1) * Px + x], z2 = buf[(3 * qq + 2) * Px + x];
@@ -291,30 +291,44 @@ __global__ void k_rows_inv(DemagArgs<R> A) {
 // block (2 E / (3 Px) consecutive rows) writes runs of rows * CC elements and a
 // column kernel block reads and writes contiguous ny * CC runs.
 
-template <typename R> struct IlCfg;
-template <> struct IlCfg<float> { static constexpr int E = 12288, V = 16; };
-template <> struct IlCfg<double> { static constexpr int E = 6144, V = 16; };
+// kernel configurations: E elements per block, V values per thread (E / V
+// threads), MINB blocks per SM for the register budget.  Two FP32 variants
+// (radix 16 with 384 threads, radix 32 with 192 threads) are timed against each
+// other on the actual batch; FP64 uses radix 16.
+struct CfgF16 { using R = float; static constexpr int E = 12288, V = 16, MINB = 1; };
+struct CfgF32 { using R = float; static constexpr int E = 12288, V = 32, MINB = 1; };
+struct CfgD16 { using R = double; static constexpr int E = 6144, V = 16, MINB = 1; };
 
-__device__ __forceinline__ long long tiled(int comp, int y, int kx, int ny, int NG, int CC) {
-  return ((long long)(comp * NG + kx / CC) * ny + y) * CC + (kx % CC);
+// index of (comp, y, kx) in the column-tiled spectrum layout [comp][kx / CC][y][CC], CC = 2^lcc
+__device__ __forceinline__ long long tiled(int comp, int y, int kx, int ny, int NG, int lcc) {
+  return ((long long)(comp * NG + (kx >> lcc)) * ny + y) * (1 << lcc) + (kx & ((1 << lcc) - 1));
 }
 
-template <typename R>
-__global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_rows_fwd2(DemagArgs<R> A) {
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+
+template <typename CFG>
+__global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagArgs<typename CFG::R> A) {
+  using R = typename CFG::R;
   using C = typename Cx<R>::T;
-  constexpr int E = IlCfg<R>::E, V = IlCfg<R>::V;
+  constexpr int E = CFG::E, V = CFG::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
-  const int np = E / (3 * Px), nseq = 3 * np;
-  const int CC = E / (3 * ch.Py), NG = Sx / CC;
+  // 3 groups (x+iy of the even row, x+iy of the odd row, z_even + i z_odd) of np
+  // interleaved sequences: element (g, x, qq) at g * Px * np + x * np + qq
+  constexpr int LE3 = ilog2c(E / 3);         // E / 3 is a power of two
+  const int lnp = LE3 - lx, np = 1 << lnp, gs = Px * np;
+  const int lcc = LE3 - ch.ly, CC = 1 << lcc, NG = Sx >> lcc;
   const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
   const int totpairs = (ny + 1) / 2;
+  C *tws = buf + E;                          // twiddles exp(-2 pi i j / Px), j < Px
+  for (int j = threadIdx.x; j < Px; j += blockDim.x) tws[j] = A.tw[j << (12 - lx)];
+  // the upper half x >= Px/2 is zero padding the first FFT pass never reads
 #pragma unroll 4
-  for (int idx = threadIdx.x; idx < np * Px; idx += blockDim.x) {
-    const int qq = idx >> lx, x = idx & (Px - 1);
+  for (int idx = threadIdx.x; idx < np * (Px >> 1); idx += blockDim.x) {
+    const int qq = idx >> (lx - 1), x = idx & ((Px >> 1) - 1);
     const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
     R M0x = 0, M0y = 0, M0z = 0, M1x = 0, M1y = 0, M1z = 0;
     if (pr < totpairs && x < nx) {
@@ -332,24 +346,23 @@ __global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_rows_fwd2(DemagAr
       }
     }
     C z;
-    C *row = buf + x * nseq + 3 * qq;
-    z.x = M0x; z.y = M0y; row[0] = z;
-    z.x = M1x; z.y = M1y; row[1] = z;
-    z.x = M0z; z.y = M1z; row[2] = z;
+    C *el = buf + x * np + qq;
+    z.x = M0x; z.y = M0y; el[0] = z;
+    z.x = M1x; z.y = M1y; el[gs] = z;
+    z.x = M0z; z.y = M1z; el[2 * gs] = z;
   }
   __syncthreads();
-  fft_il<C, V, false>(buf, lx, IlMap{nseq, 1, 0}, A.tw);
+  fft_il<C, V, false, true, false>(buf, lx, IlMap{lnp, 3, gs}, tws, true);
   // half spectra (kx <= Px/2) of the six real rows of each pair, written in
   // tiled order: c fastest, then the block's rows, then column group, then comp
   const int half = Px / 2 + 1;
-  const int nrb = 2 * np;
+  const int nrb = 2 * np, lnrb = lnp + 1;
   const int ngu = (half + CC - 1) / CC;
   C *S = A.S + ch.s_off;
   const int tot = 3 * ngu * nrb * CC;
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int cc = idx % CC, rest = idx / CC;
-    const int rr = rest % nrb, rest2 = rest / nrb;
-    const int g = rest2 % ngu, comp = rest2 / ngu;
+    const int cc = idx & (CC - 1), rr = (idx >> lcc) & (nrb - 1), o = idx >> (lcc + lnrb);
+    const int comp = (o >= ngu) + (o >= 2 * ngu), g = o - comp * ngu;
     const int kx = g * CC + cc;
     const int r = 2 * pair0 + rr;
     if (kx >= half || r >= ny) continue;
@@ -357,44 +370,48 @@ __global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_rows_fwd2(DemagAr
     const int sq = comp == 2 ? 2 : h;
     const bool take_b = comp == 1 || (comp == 2 && h == 1);
     const int km = (Px - kx) & (Px - 1);
-    const C Z = buf[kx * nseq + 3 * qq + sq], Zm = buf[km * nseq + 3 * qq + sq];
-    C o;
-    if (!take_b) { o.x = (R)0.5 * (Z.x + Zm.x); o.y = (R)0.5 * (Z.y - Zm.y); }
-    else { o.x = (R)0.5 * (Z.y + Zm.y); o.y = (R)0.5 * (Zm.x - Z.x); }
-    S[tiled(comp, r, kx, ny, NG, CC)] = o;
+    const C Z = buf[sq * gs + kx * np + qq], Zm = buf[sq * gs + km * np + qq];
+    C o2;
+    if (!take_b) { o2.x = (R)0.5 * (Z.x + Zm.x); o2.y = (R)0.5 * (Z.y - Zm.y); }
+    else { o2.x = (R)0.5 * (Z.y + Zm.y); o2.y = (R)0.5 * (Zm.x - Z.x); }
+    S[tiled(comp, r, kx, ny, NG, lcc)] = o2;
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_cols2d(DemagArgs<R> A) {
+template <typename CFG>
+__global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs<typename CFG::R> A) {
+  using R = typename CFG::R;
   using C = typename Cx<R>::T;
-  constexpr int E = IlCfg<R>::E, V = IlCfg<R>::V;
+  constexpr int E = CFG::E, V = CFG::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, Py = ch.Py, ly = ch.ly, ny = ch.ny, Sx = ch.Sx;
-  const int CC = E / (3 * Py), NG = Sx / CC;
+  constexpr int LE3 = ilog2c(E / 3);         // E / 3 is a power of two
+  const int lcc = LE3 - ly, CC = 1 << lcc, NG = Sx >> lcc;
   const int g = (int)(blockIdx.x - A.blk_first[c]);
   const int kx0 = g * CC;
   const int qx = Px / 2 + 1, qy = Py / 2 + 1;
   const C *S = A.S + ch.s_off;
-  // buf[(comp * Py + y) * CC + cc]; rows y >= ny are the zero padding
+  C *tws = buf + E;                          // twiddles exp(-2 pi i j / Py), j < Py
+  for (int j = threadIdx.x; j < Py; j += blockDim.x) tws[j] = A.tw[j << (12 - ly)];
+  // buf[(comp * Py + y) * CC + cc]; rows y >= ny are the zero padding, and the
+  // upper half y >= Py/2 is never read by the first FFT pass
 #pragma unroll 8
-  for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
-    const int cc = idx % CC, rest = idx / CC;
-    const int y = rest % Py, comp = rest / Py;
+  for (int idx = threadIdx.x; idx < E / 2; idx += blockDim.x) {
+    const int cc = idx & (CC - 1), y = (idx >> lcc) & ((Py >> 1) - 1), comp = idx >> (LE3 - 1);
     C v;
     v.x = 0; v.y = 0;
     if (y < ny) v = S[((long long)(comp * NG + g) * ny + y) * CC + cc];
-    buf[idx] = v;
+    buf[(comp * Py + y) * CC + cc] = v;
   }
   __syncthreads();
-  fft_il<C, V, false>(buf, ly, IlMap{CC, 3, Py * CC}, A.tw);
+  fft_il<C, V, false, true, false>(buf, ly, IlMap{lcc, 3, Py * CC}, tws, true);
   const long long Q = (long long)qx * qy;
   const R *nh = A.nhat[ch.spec];
   for (int idx = threadIdx.x; idx < Py * CC; idx += blockDim.x) {
-    const int cc = idx % CC, ky = idx / CC;
+    const int cc = idx & (CC - 1), ky = idx >> lcc;
     const int kx = kx0 + cc;
     if (kx >= qx) continue;
     const int kyq = ky <= Py / 2 ? ky : Py - ky;
@@ -413,40 +430,42 @@ __global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_cols2d(DemagArgs<
     buf[b0] = hx_; buf[b1] = hy_; buf[b2] = hz_;
   }
   __syncthreads();
-  fft_il<C, V, true>(buf, ly, IlMap{CC, 3, Py * CC}, A.tw);
+  fft_il<C, V, true, false, true>(buf, ly, IlMap{lcc, 3, Py * CC}, tws, true);
   C *So = A.S + ch.s_off;
   for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
-    const int cc = idx % CC, rest = idx / CC;
-    const int y = rest % Py, comp = rest / Py;
+    const int cc = idx & (CC - 1), y = (idx >> lcc) & (Py - 1), comp = idx >> LE3;
     if (y < ny) So[((long long)(comp * NG + g) * ny + y) * CC + cc] = buf[idx];
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_rows_inv2(DemagArgs<R> A) {
+template <typename CFG>
+__global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_inv2(DemagArgs<typename CFG::R> A) {
+  using R = typename CFG::R;
   using C = typename Cx<R>::T;
-  constexpr int E = IlCfg<R>::E, V = IlCfg<R>::V;
+  constexpr int E = CFG::E, V = CFG::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
   C *side = buf + E;                        // B[0] and B[Px/2] of each sequence
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
-  const int np = E / (3 * Px), nseq = 3 * np;
-  const int CC = E / (3 * ch.Py), NG = Sx / CC;
+  constexpr int LE3 = ilog2c(E / 3);         // E / 3 is a power of two
+  const int lnp = LE3 - lx, np = 1 << lnp, gs = Px * np, nseq = 3 * np;
+  const int lcc = LE3 - ch.ly, CC = 1 << lcc, NG = Sx >> lcc;
   const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
   const int half = Px / 2 + 1;
-  const int nrb = 2 * np;
+  const int nrb = 2 * np, lnrb = lnp + 1;
   const int ngu = (half + CC - 1) / CC;
   const C *S = A.S + ch.s_off;
+  C *tws = side + 2 * nseq;                  // twiddles exp(-2 pi i j / Px), j < Px
+  for (int j = threadIdx.x; j < Px; j += blockDim.x) tws[j] = A.tw[j << (12 - lx)];
   // stage: sequence s = a + i b; a[k] at position k, b[k] at position Px - k
   // (b[0], b[Px/2] in side[])
   const int tot = 3 * ngu * nrb * CC;
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int cc = idx % CC, rest = idx / CC;
-    const int rr = rest % nrb, rest2 = rest / nrb;
-    const int g = rest2 % ngu, comp = rest2 / ngu;
+    const int cc = idx & (CC - 1), rr = (idx >> lcc) & (nrb - 1), o = idx >> (lcc + lnrb);
+    const int comp = (o >= ngu) + (o >= 2 * ngu), g = o - comp * ngu;
     const int kx = g * CC + cc;
     if (kx >= half) continue;
     const int r = 2 * pair0 + rr;
@@ -455,43 +474,45 @@ __global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_rows_inv2(DemagAr
     const bool is_b = comp == 1 || (comp == 2 && h == 1);
     C v;
     v.x = 0; v.y = 0;
-    if (r < ny) v = S[tiled(comp, r, kx, ny, NG, CC)];
-    const int s = 3 * qq + sq;
-    if (!is_b) buf[kx * nseq + s] = v;
+    if (r < ny) v = S[tiled(comp, r, kx, ny, NG, lcc)];
+    const int s = sq * np + qq;                 // side-array index of the sequence
+    C *seq = buf + sq * gs + qq;
+    if (!is_b) seq[kx * np] = v;
     else if (kx == 0) side[2 * s] = v;
     else if (2 * kx == Px) side[2 * s + 1] = v;
-    else buf[(Px - kx) * nseq + s] = v;
+    else seq[(Px - kx) * np] = v;
   }
   __syncthreads();
   // z[k] = a[k] + i b[k], z[Px-k] = conj(a[k]) + i conj(b[k]); real parts only at k = 0, Px/2
   for (int idx = threadIdx.x; idx < nseq * half; idx += blockDim.x) {
-    const int s = idx % nseq, kx = idx / nseq;
+    const int kx = (idx >> lnp) / 3, s = idx - kx * nseq;
+    C *seq = buf + (s >> lnp) * gs + (s & (np - 1));
     if (kx == 0 || 2 * kx == Px) {
-      const C a = buf[kx * nseq + s], b = side[2 * s + (kx == 0 ? 0 : 1)];
+      const C a = seq[kx * np], b = side[2 * s + (kx == 0 ? 0 : 1)];
       C z;
       z.x = a.x; z.y = b.x;
-      buf[kx * nseq + s] = z;
+      seq[kx * np] = z;
     } else {
-      const C a = buf[kx * nseq + s], b = buf[(Px - kx) * nseq + s];
+      const C a = seq[kx * np], b = seq[(Px - kx) * np];
       C zk, zm;
       zk.x = a.x - b.y; zk.y = a.y + b.x;
       zm.x = a.x + b.y; zm.y = b.x - a.y;
-      buf[kx * nseq + s] = zk;
-      buf[(Px - kx) * nseq + s] = zm;
+      seq[kx * np] = zk;
+      seq[(Px - kx) * np] = zm;
     }
   }
   __syncthreads();
-  fft_il<C, V, true>(buf, lx, IlMap{nseq, 1, 0}, A.tw);
+  fft_il<C, V, true, false, true>(buf, lx, IlMap{lnp, 3, gs}, tws, true);
   const R scale = (R)1 / ((R)Px * (R)ch.Py * (R)ch.Pz);
   const long long Sl = (long long)ny * ch.hx;
   const bool percell = ch.t_off >= 0;
   const float mu0f = (float)mu0;
   const int totpairs = (ny + 1) / 2;
   for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
-    const int qq = idx / nx, x = idx - qq * nx;
+    const int qq = (int)divq((unsigned)idx, ch.nx_m, ch.nx_l), x = idx - qq * nx;
     const int pr = pair0 + qq;
     if (pr >= totpairs) continue;
-    const C z0 = buf[x * nseq + 3 * qq], z1 = buf[x * nseq + 3 * qq + 1], z2 = buf[x * nseq + 3 * qq + 2];
+    const C z0 = buf[x * np + qq], z1 = buf[gs + x * np + qq], z2 = buf[2 * gs + x * np + qq];
     for (int h = 0; h < 2; ++h) {
       const int r = 2 * pr + h;
       if (r >= ny) break;
@@ -515,6 +536,23 @@ __global__ void __launch_bounds__(IlCfg<R>::E / IlCfg<R>::V) k_rows_inv2(DemagAr
   }
 }
 
+template <typename CFG>
+void launch_il(const Launch &L, const DemagLaunch &P, DemagArgs<typename CFG::R> A) {
+  using C = typename Cx<typename CFG::R>::T;
+  constexpr int T = CFG::E / CFG::V;
+  A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
+  if (P.ev) cudaEventRecord(P.ev[0], L.stream);
+  k_rows_fwd2<CFG><<<P.rows_blocks, T, P.rows_smem, L.stream>>>(A);
+  if (P.ev) cudaEventRecord(P.ev[1], L.stream);
+  A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
+  k_cols2d<CFG><<<P.cols_blocks, T, P.cols_smem, L.stream>>>(A);
+  if (P.ev) cudaEventRecord(P.ev[2], L.stream);
+  A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
+  k_rows_inv2<CFG><<<P.rows_blocks, T, P.inv_smem, L.stream>>>(A);
+  if (P.ev) cudaEventRecord(P.ev[3], L.stream);
+  *L.counter += 3;
+}
+
 template <typename R>
 void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
   using C = typename Cx<R>::T;
@@ -527,20 +565,9 @@ void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
   A.m_nat = reinterpret_cast<const R *>(P.m_nat);
   A.Ms_override = (R)P.Ms_override;
   if (P.il2d) {
-    constexpr int T = IlCfg<R>::E / IlCfg<R>::V;
-    const size_t sm = (size_t)IlCfg<R>::E * sizeof(C);
-    const size_t sm_inv = P.inv_smem;
-    A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
-    if (P.ev) cudaEventRecord(P.ev[0], L.stream);
-    k_rows_fwd2<R><<<P.rows_blocks, T, sm, L.stream>>>(A);
-    if (P.ev) cudaEventRecord(P.ev[1], L.stream);
-    A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
-    k_cols2d<R><<<P.cols_blocks, T, sm, L.stream>>>(A);
-    if (P.ev) cudaEventRecord(P.ev[2], L.stream);
-    A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
-    k_rows_inv2<R><<<P.rows_blocks, T, sm_inv, L.stream>>>(A);
-    if (P.ev) cudaEventRecord(P.ev[3], L.stream);
-    *L.counter += 3;
+    if constexpr (sizeof(R) == 8) launch_il<CfgD16>(L, P, A);
+    else if (P.fft_variant == 2) launch_il<CfgF32>(L, P, A);
+    else launch_il<CfgF16>(L, P, A);
     return;
   }
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
@@ -577,9 +604,11 @@ cudaError_t demag_set_smem_limits() {
   e = cudaFuncSetAttribute(k_rows_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e != cudaSuccess) return e;
   const int lil = 200 * 1024;
-  const void *fns[6] = {(const void *)k_rows_fwd2<float>, (const void *)k_rows_fwd2<double>,
-                        (const void *)k_cols2d<float>, (const void *)k_cols2d<double>,
-                        (const void *)k_rows_inv2<float>, (const void *)k_rows_inv2<double>};
+  const void *fns[9] = {(const void *)k_rows_fwd2<CfgF16>, (const void *)k_rows_fwd2<CfgF32>,
+                        (const void *)k_rows_fwd2<CfgD16>, (const void *)k_cols2d<CfgF16>,
+                        (const void *)k_cols2d<CfgF32>, (const void *)k_cols2d<CfgD16>,
+                        (const void *)k_rows_inv2<CfgF16>, (const void *)k_rows_inv2<CfgF32>,
+                        (const void *)k_rows_inv2<CfgD16>};
   for (const void *f : fns) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lil);
     if (e != cudaSuccess) return e;
@@ -587,6 +616,6 @@ cudaError_t demag_set_smem_limits() {
   return cudaSuccess;
 }
 
-int il_elements(bool fp64) { return fp64 ? IlCfg<double>::E : IlCfg<float>::E; }
+int il_elements(bool fp64) { return fp64 ? CfgD16::E : CfgF16::E; }
 
 }  // namespace mmc

@@ -49,8 +49,8 @@ struct ChainDev {
   int Px, Py, Pz;     // padded FFT sizes
   int lx, ly, lz;     // log2 of the padded sizes
   int Sx;             // row stride (complex elements) of the spectrum buffer
-  unsigned hx_m, ny_m;   // division by hx and ny: multiply-shift constants
-  int hx_l, ny_l;        // (Granlund & Montgomery's round-up method, l = ceil(log2 d))
+  unsigned hx_m, ny_m, nx_m;   // division by hx, ny and nx: multiply-shift constants
+  int hx_l, ny_l, nx_l;        // (Granlund & Montgomery's round-up method, l = ceil(log2 d))
   float wx, wy, wz;   // exchange bond weights V A0 / (h^2 kT)
   float cdx, cdy;     // DMI weights V D0 / (h kT)
   float p2, p4;       // longitudinal: dF/kT = dq (p2 + p4 (2 (|m|^2 - me2) + dq))
@@ -134,6 +134,7 @@ void long_coeffs(double T, double Tc, double mu, double V, double Ms0, double *c
 double rms_len_eq7(double T, double Tc, double mu, double V, double Ms0);
 void demag_tensor(const double h[3], const double R[3], double out[6]);
 void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double> &out);
+void demag_octant(const double h[3], int ox, int oy, int oz, std::vector<double> &oct);
 
 // ---------------------------------------------------------------------------
 // launches
@@ -165,6 +166,29 @@ void launch_sweep_pass(const Launch &L, const SweepLaunch &P);
 void launch_advance(const Launch &L, ChainState *st, int nchains, unsigned by, unsigned *sweep_base,
                     int adapt_now, int adapt, float tmin, float tmax);
 
+// serial exact-demag sweep (k_serial.cu)
+struct SerialLaunch {
+  const ChainDev *chains;
+  ChainState *st;
+  float4 *m;
+  float4 *heff;
+  const float4 *tab;
+  const float *ms;
+  const float *const *oct;      // per tensor set: real-space tensor [6][oz][oy][ox]
+  const int4 *oct_dim;
+  float4 *prop;                 // scratch with the layout of m
+  const unsigned *sweep_base;
+  unsigned sweep_off;
+  unsigned key0, key1;
+  int nchains;
+  bool percell;
+  bool self;                    // add the demag self term to every move
+  size_t smem;                  // dynamic shared memory per block (chains needing more run from global memory)
+};
+void launch_serial_sweep(const Launch &L, const SerialLaunch &P);
+size_t serial_smem_need(const ChainDev &ch);
+cudaError_t serial_set_smem_limit(size_t bytes);
+
 struct DemagLaunch {
   const ChainDev *chains;
   const float4 *m;
@@ -187,7 +211,8 @@ struct DemagLaunch {
   cudaEvent_t *ev;              // optional: 4 events recorded around the three kernels
   const void *m_nat;            // optional natural-order m (float or double, as the plan)
   double Ms_override;           // uniform Ms0 used with m_nat
-  bool il2d;                    // 2D interleaved radix-16 kernels (all chains Pz == 1)
+  bool il2d;                    // 2D interleaved kernels (all chains Pz == 1)
+  int fft_variant;              // FP32 2D kernels: 1 radix 16 (384 threads), 2 radix 32 (192 threads)
   size_t inv_smem;              // shared memory of the 2D inverse row kernel
 };
 int il_elements(bool fp64);     // complex elements per block of the 2D kernels

@@ -143,6 +143,11 @@ class MMC:
     def sweep(self, n, seed):
         check(load().mmc_sweep(self._ctx, int(n), int(seed)), "mmc_sweep")
 
+    def sweep_serial(self, n, seed):
+        """n iterations of the serial exact-demag form (App. B): cells in index
+        order, demag field updated after every accepted move."""
+        check(load().mmc_sweep_serial(self._ctx, int(n), int(seed)), "mmc_sweep_serial")
+
     def sweep_sampled(self, n, seed, every):
         check(load().mmc_sweep_sampled(self._ctx, int(n), int(seed), int(every)), "mmc_sweep_sampled")
 
@@ -215,6 +220,13 @@ class MMC:
                                      cnt.ctypes.data_as(C.POINTER(C.c_int64))), "mmc_phase_times")
         kinds = ("demag_rows_fwd", "demag_cols", "demag_rows_inv", "sweep_pass", "observables", "advance")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(kinds)}
+
+    def fft_tuning(self):
+        """(variant, (ms radix-16, ms radix-32)) of the FP32 2D demag kernels."""
+        v = C.c_int(0)
+        ms = np.zeros(2)
+        check(load().mmc_fft_tuning(self._ctx, C.byref(v), _dptr(ms)), "mmc_fft_tuning")
+        return int(v.value), (float(ms[0]), float(ms[1]))
 
     @property
     def launches(self) -> int:

@@ -91,21 +91,10 @@ def granular_chain(n, seed, h=5e-9, grain_spacing=8e-9, Ms0=1e6, Ku=3e5, Tc=700.
     sy = rng.uniform(0, L, nseeds)
     xc = (np.arange(n) + 0.5) * h
     X, Y = np.meshgrid(xc, xc, indexing="xy")          # X varies along i (fast)
-    grain = np.empty((n, n), dtype=np.int32)
-    # nearest seed by blocks of rows to bound memory
-    for r0 in range(0, n, 64):
-        xs = X[r0:r0 + 64].reshape(-1, 1)
-        ys = Y[r0:r0 + 64].reshape(-1, 1)
-        best = np.full(xs.shape[0], np.inf)
-        arg = np.zeros(xs.shape[0], dtype=np.int32)
-        for c0 in range(0, nseeds, 2048):
-            d2 = (xs - sx[c0:c0 + 2048]) ** 2 + (ys - sy[c0:c0 + 2048]) ** 2
-            j = np.argmin(d2, axis=1)
-            v = d2[np.arange(d2.shape[0]), j]
-            upd = v < best
-            best[upd] = v[upd]
-            arg[upd] = (j[upd] + c0).astype(np.int32)
-        grain[r0:r0 + 64] = arg.reshape(-1, n)
+    # nearest seed of every cell centre (exact nearest neighbour by k-d tree)
+    from scipy.spatial import cKDTree
+    _, arg = cKDTree(np.stack([sx, sy], axis=1)).query(np.stack([X.reshape(-1), Y.reshape(-1)], axis=1))
+    grain = arg.astype(np.int32).reshape(n, n)
     g_Ms = Ms0 * np.exp(sigma_ln * rng.standard_normal(nseeds))
     g_Ku = Ku * np.exp(sigma_ln * rng.standard_normal(nseeds))
     g_Tc = Tc * np.exp(sigma_ln * rng.standard_normal(nseeds))
