@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-demag", action="store_true")
+    ap.add_argument("--fft-variant", type=int, default=0, choices=(0, 1, 2),
+                    help="FP32 2D demag kernels: 0 timed pick at create, 1 radix 16, 2 radix 32")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the cuFFT demag timing and the one-chain-per-launch comparison")
     ap.add_argument("--chains", type=int, default=0, help="use only the first N chains of the workload")
@@ -267,13 +269,14 @@ def run_ours(args):
     percell = args.workload == "granular"
     stream = torch.cuda.Stream()
     if args.profile_run > 0:
-        gp = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), use_graphs=0, stream=stream)
+        gp = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), use_graphs=0,
+                 fft_variant=args.fft_variant, stream=stream)
         gp.init_random(1 + rank)
         gp.sweep(args.profile_run, 1 + rank)
         torch.cuda.synchronize()
         print("profile run ok", gp.launches, flush=True)
         return
-    g = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), stream=stream)
+    g = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=args.fft_variant, stream=stream)
     seed = 1 + rank
     g.init_random(seed)
     ncell = sum(g.ncell)
@@ -350,7 +353,8 @@ def run_ours(args):
                                       "create_time_ms": {"radix16": tms[0], "radix32": tms[1]}}
             del cf
         if len(specs) > 1:
-            plain = [MMC([sp], demag=int(demag), demag_fp64=int(args.fp64_demag), stream=stream) for sp in specs]
+            plain = [MMC([sp], demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=args.fft_variant,
+                         stream=stream) for sp in specs]
             for k, p1 in enumerate(plain):
                 p1.set_m(g.get_m(k))
                 p1.sweep(SWEEPS_PER_STEP, seed)

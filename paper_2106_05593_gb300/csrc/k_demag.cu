@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_inv2(DemagA
   // stage: sequence s = a + i b; a[k] at position k, b[k] at position Px - k
   // (b[0], b[Px/2] in side[])
   const int tot = 3 * ngu * nrb * CC;
-#pragma unroll 4
+#pragma unroll 16
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     const int cc = idx & (CC - 1), rr = (idx >> lcc) & (nrb - 1), o = idx >> (lcc + lnrb);
     const int comp = (o >= ngu) + (o >= 2 * ngu), g = o - comp * ngu;

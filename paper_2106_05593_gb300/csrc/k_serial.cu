@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kSerialThreads, 1) k_serial_sweep(SerialArgs A
       const float ns = v.dmx * v.dmx * tn[0] + v.dmy * v.dmy * tn[tstride] + v.dmz * v.dmz * tn[2 * tstride];
       loc += 0.5f * (float)mu0 * M.zee * Ms * ns;
     }
-    loc = loc - 4.f * log1p_move(v.tt) + logf(u3);
+    loc = loc - 4.f * log1p_move(v.tt) + __logf(u3);
     pr[t] = make_float4(v.mpx, v.mpy, v.mpz, loc);
   }
   __syncthreads();
@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(kSerialThreads, 1) k_serial_sweep(SerialArgs A
           const float4 P = pr[idx];
           float4 nb[6];
           float w[6];
-          load_neighbours(ch, nx, ny, nz, hx, mm + (long long)(1 - color) * S, a, i, j, k, row, i >> 1, i & 1, nb, w);
+          load_neighbours(ch.pbc, (flags & F_GRAIN) != 0, ch.gscale, nx, ny, nz, hx, mm + (long long)(1 - color) * S, a,
+                          i, j, k, row, i >> 1, i & 1, nb, w);
           float bs = 1.f, zee = ch.zee;
           if (PERCELL) {
             const float4 t1 = A.tab[ch.t_off + 2 * S + idx];

@@ -32,37 +32,40 @@ enum : int {
 // Per-chain constants, device resident.  Energies are in units of kT (of the
 // chain temperature, or of a reference T_ref for per-cell chains, whose table
 // carries bscale = T_ref / T_cell for the bond weights).
-struct ChainDev {
+struct __align__(16) ChainDev {
+  // the sweep kernel reads the first 128 bytes as eight 16-byte vectors
   int nx, ny, nz;
   int hx;             // sublattice slots per row: (nx + 1) / 2
   int nrows;          // ny * nz
   int pbc;            // bit a: axis a periodic
   int flags;
   int chain;          // chain index (Philox counter word 2)
-  long long ncell;
-  long long m_off;    // float4 index of the red array in the m arena; black follows
-  long long h_off;    // float4 index of the red h_eff array (split layout), or -1
-  long long t_off;    // float4 index of the per-cell table (3 x 2 x nrows*hx float4), or -1
-  long long ms_off;   // float index of per-cell Ms0 (split layout), or -1
-  long long s_off;    // complex element index of the spectrum buffer
-  int spec;           // tensor-spectrum set index
-  int Px, Py, Pz;     // padded FFT sizes
-  int lx, ly, lz;     // log2 of the padded sizes
-  int Sx;             // row stride (complex elements) of the spectrum buffer
   unsigned hx_m, ny_m, nx_m;   // division by hx, ny and nx: multiply-shift constants
+  int spec;           // tensor-spectrum set index
   int hx_l, ny_l, nx_l;        // (Granlund & Montgomery's round-up method, l = ceil(log2 d))
+  float gscale;       // bond scale across grains
   float wx, wy, wz;   // exchange bond weights V A0 / (h^2 kT)
-  float cdx, cdy;     // DMI weights V D0 / (h kT)
+  float cdx;          // DMI weights V D0 / (h kT), x bonds
+  float cdy;          // y bonds
   float p2, p4;       // longitudinal: dF/kT = dq (p2 + p4 (2 (|m|^2 - me2) + dq))
-  float me2h, me2l;   // m_e^2 as a float-float pair (0 at and above Tc)
+  float me2h;         // m_e^2 as a float-float pair (0 at and above Tc)
+  float me2l;
   float sigma;        // length-move width (Eq. 13, capped)
   float zee;          // V Ms0 / kT  (1/T)
   float k1, k2;       // V K1(T) / kT, V K2(T) / kT
   float ex, ey, ez;   // easy axis
   float Bx, By, Bz;   // applied field (T)
   float Ms0;          // A/m (uniform chains)
-  double Ms0d;        // the same in FP64 (convolution input of the FP64 path)
-  float gscale;       // bond scale across grains
+  long long m_off;    // float4 index of the red array in the m arena; black follows
+  long long h_off;    // float4 index of the red h_eff array (split layout), or -1
+  long long t_off;    // float4 index of the per-cell table (3 x 2 x nrows*hx float4), or -1
+  long long ms_off;   // float index of per-cell Ms0 (split layout), or -1
+  long long ncell;
+  long long s_off;    // complex element index of the spectrum buffer
+  int Px, Py, Pz;     // padded FFT sizes
+  int Sx;             // row stride (complex elements) of the spectrum buffer
+  int lx, ly, lz;     // log2 of the padded sizes
+  double Ms0d;        // Ms0 in FP64 (convolution input of the FP64 path)
 };
 
 // Per-chain mutable state, device resident (plain data; part of checkpoints).

@@ -18,14 +18,45 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// chain constants a trial needs, loaded from the first 176 bytes of ChainDev
+// as eleven 16-byte vectors (one load instruction each instead of one per field)
+struct ChainK {
+  int nx, ny, nz, hx, nrows, pbc, flags, chain;
+  unsigned hx_m, ny_m;
+  int hx_l, ny_l;
+  float gscale, wx, wy, wz, cdx, cdy, p2, p4, me2h, me2l, sigma, zee, k1, k2, ex, ey, ez, Bx, By, Bz, Ms0;
+  long long m_off, h_off, t_off, ms_off;
+};
+
+__device__ __forceinline__ ChainK load_chain(const ChainDev *cd) {
+  const int4 *iv = reinterpret_cast<const int4 *>(cd);
+  const float4 *fv = reinterpret_cast<const float4 *>(cd);
+  const longlong2 *lv = reinterpret_cast<const longlong2 *>(cd);
+  const int4 a = iv[0], b = iv[1], u = iv[2], l = iv[3];
+  const float4 f0 = fv[4], f1 = fv[5], f2 = fv[6], f3 = fv[7], f4 = fv[8];
+  const longlong2 o0 = lv[9], o1 = lv[10];
+  ChainK K;
+  K.nx = a.x; K.ny = a.y; K.nz = a.z; K.hx = a.w;
+  K.nrows = b.x; K.pbc = b.y; K.flags = b.z; K.chain = b.w;
+  K.hx_m = (unsigned)u.x; K.ny_m = (unsigned)u.y;
+  K.hx_l = l.x; K.ny_l = l.y; K.gscale = __int_as_float(l.w);
+  K.wx = f0.x; K.wy = f0.y; K.wz = f0.z; K.cdx = f0.w;
+  K.cdy = f1.x; K.p2 = f1.y; K.p4 = f1.z; K.me2h = f1.w;
+  K.me2l = f2.x; K.sigma = f2.y; K.zee = f2.z; K.k1 = f2.w;
+  K.k2 = f3.x; K.ex = f3.y; K.ey = f3.z; K.ez = f3.w;
+  K.Bx = f4.x; K.By = f4.y; K.Bz = f4.z; K.Ms0 = f4.w;
+  K.m_off = o0.x; K.h_off = o0.y; K.t_off = o1.x; K.ms_off = o1.y;
+  return K;
+}
+
 // material constants of one cell
 struct CellMat {
   float p2, p4, me2h, me2l, sigma, zee, k1, k2, ex, ey, ez, bs;
 };
 
 // off = colour * S + slot; per-cell tables are 3 float4 arrays of 2 S entries
-template <bool PERCELL>
-__device__ __forceinline__ CellMat cell_material(const ChainDev &ch, const float4 *tab, long long S, long long off) {
+template <bool PERCELL, typename CH>
+__device__ __forceinline__ CellMat cell_material(const CH &ch, const float4 *tab, long long S, long long off) {
   CellMat M;
   if (PERCELL) {
     const float4 *tb = tab + ch.t_off;
@@ -43,10 +74,9 @@ __device__ __forceinline__ CellMat cell_material(const ChainDev &ch, const float
 
 // the six neighbours of cell (i, j, k) of colour `color`, all in the other
 // colour's array mo; absent bonds get weight 0, bonds across grains gscale
-__device__ __forceinline__ void load_neighbours(const ChainDev &ch, int nx, int ny, int nz, int hx, const float4 *mo,
-                                                float4 a, int i, int j, int k, int row, int s, int p, float4 nb[6],
-                                                float w[6]) {
-  const int pbc = ch.pbc;
+__device__ __forceinline__ void load_neighbours(int pbc, bool grain, float gscale, int nx, int ny, int nz, int hx,
+                                                const float4 *mo, float4 a, int i, int j, int k, int row, int s,
+                                                int p, float4 nb[6], float w[6]) {
   const int im = i > 0 ? i - 1 : ((pbc & 1) ? nx - 1 : -1);
   const int ip = i < nx - 1 ? i + 1 : ((pbc & 1) ? 0 : -1);
   const int jm = j > 0 ? j - 1 : ((pbc & 2) ? ny - 1 : -1);
@@ -67,11 +97,10 @@ __device__ __forceinline__ void load_neighbours(const ChainDev &ch, int nx, int 
   w[3] = jp >= 0 ? 1.f : 0.f;
   w[4] = km >= 0 ? 1.f : 0.f;
   w[5] = kp >= 0 ? 1.f : 0.f;
-  if (ch.flags & F_GRAIN) {
-    const float gs = ch.gscale;
+  if (grain) {
 #pragma unroll
     for (int b = 0; b < 6; ++b)
-      if (nb[b].w != a.w) w[b] *= gs;
+      if (nb[b].w != a.w) w[b] *= gscale;
   }
 }
 
@@ -113,14 +142,15 @@ __device__ __forceinline__ Move move_length(float4 a, float me2h, float me2l) {
 __device__ __forceinline__ void move_direction(Move &v, float4 a, float sigma, float omc, float u0, float u1,
                                                float u2) {
   const float sg = v.n2 >= 0.f ? 1.f : -1.f;
-  const float aa = -__frcp_rn(sg + v.n2);
+  const float aa = -__fdividef(1.f, sg + v.n2);     // |sg + n2| >= 1
   const float bb = v.n0 * v.n1 * aa;
   const float e1x = 1.f + sg * v.n0 * v.n0 * aa, e1y = sg * bb, e1z = -sg * v.n0;
   const float e2x = bb, e2y = sg + v.n1 * v.n1 * aa, e2z = -v.n1;
 
   const float t = u0 * omc;
   const float ct = 1.f - t;
-  const float st = sqrtf(t * (2.f - t));
+  const float t2 = t * (2.f - t);                  // > 0: t = u0 (1 - cos theta) in (0, 2)
+  const float st = t2 * rsqrtf(t2);
   float sp, cp;
   sincospif(2.f * u1, &sp, &cp);
   v.dx = ct * v.n0 + st * (cp * e1x + sp * e2x);
