@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-demag", action="store_true")
-    ap.add_argument("--fft-variant", type=int, default=0, choices=(0, 1, 2),
-                    help="FP32 2D demag kernels: 0 timed pick at create, 1 radix 16, 2 radix 32")
+    ap.add_argument("--fft-variant", type=int, default=0, choices=(0, 1, 2, 3),
+                    help="FP32 2D demag kernels: 0 timed pick at create, 1 radix 16, 2 radix 32, "
+                         "3 radix 16 two blocks per SM")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the cuFFT demag timing and the one-chain-per-launch comparison")
     ap.add_argument("--chains", type=int, default=0, help="use only the first N chains of the workload")
@@ -349,8 +350,9 @@ def run_ours(args):
             cfm = sum(ph[k][0] for k in kinds) / 20.0
             compare["demag_update_ms"] = {"own": own, "cufft": cfm}
             v, tms = g.fft_tuning()
-            compare["fft_variant"] = {"picked": {0: None, 1: "radix16", 2: "radix32"}[v],
-                                      "create_time_ms": {"radix16": tms[0], "radix32": tms[1]}}
+            compare["fft_variant"] = {"picked": {0: None, 1: "radix16", 2: "radix32", 3: "radix16x2"}[v],
+                                      "create_time_ms": {"radix16": tms[0], "radix32": tms[1],
+                                                         "radix16x2": tms[2]}}
             del cf
         if len(specs) > 1:
             plain = [MMC([sp], demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=args.fft_variant,

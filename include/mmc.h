@@ -101,9 +101,10 @@ typedef struct {
     int demag_self;           /* serial form (mmc_sweep_serial) only: add the demag
                                  self term (mu0 V / 2) Ms0^2 dm.N(0).dm to Eq. 14,
                                  making its demag energy change exact           [0] */
-    int fft_variant;          /* FP32 2D demag kernels: 0 time both on the batch at
-                                 the first update and keep the faster, 1 radix-16
-                                 passes, 2 radix-32 passes                          [0] */
+    int fft_variant;          /* FP32 2D demag kernels: 0 time the variants on the
+                                 batch at create and keep the fastest, 1 radix 16
+                                 (768 threads), 2 radix 32 (384 threads), 3 radix
+                                 16 (384 threads, two blocks per SM)            [0] */
 } mmc_options;
 
 /* One chain of a batch. T_cell (optional, HOST) gives a per-cell temperature;
@@ -168,8 +169,12 @@ void mmc_destroy(mmc_ctx *ctx);
 mmc_status mmc_set_field(mmc_ctx *ctx, int chain, const double B[3]);
 
 /* Copy m of one chain in/out as float4 per cell in natural order.  src/dst are
- * HOST pointers when is_device == 0, DEVICE pointers otherwise.  mmc_set_m
- * rejects non-finite values (MMC_ERR_NONFINITE) and recomputes H_d. */
+ * HOST pointers when is_device == 0, DEVICE pointers otherwise; the caller's
+ * buffer is no longer used when the call returns.  mmc_set_m rejects non-finite
+ * values (MMC_ERR_NONFINITE, state unchanged; checked on the device).  The demag
+ * field is not recomputed here: every iteration of mmc_sweep / mmc_sweep_serial
+ * computes it first, and mmc_pass_debug refreshes it when the state or the
+ * field changed since the last update (mmc_demag_update forces it). */
 mmc_status mmc_set_m(mmc_ctx *ctx, int chain, const float *src, int is_device);
 mmc_status mmc_get_m(mmc_ctx *ctx, int chain, float *dst, int is_device);
 
@@ -262,6 +267,24 @@ mmc_status mmc_tables(mmc_ctx *ctx, int chain, double *me, double *chi, double *
 mmc_status mmc_energy_grad(mmc_ctx *ctx, int chain, const void *m, int fp64, const double params[5],
                            double E[7], void *dEdm, double dEdp[5]);
 
+/* Zero-temperature steepest descent on one chain, the comparison method of
+ * Sec. III (SDesc): the energy of mmc_energy (exchange, DMI, anisotropy,
+ * Zeeman, demag; the longitudinal term vanishes at |m| = m_e) is minimized over
+ * the directions u_i with every |m_i| held at m_e(T), i.e. with the parameters
+ * rescaled to T and no stochasticity or length distribution.  Steps
+ * u_i <- normalize(u_i - tau g_i), g_i the tangential gradient m_e (G_i - (G_i.u_i) u_i)
+ * of G = dE/dm (FP64, as mmc_energy_grad); tau turns the steepest cell by 0.01 rad
+ * on the first step, then alternates the Barzilai-Borwein sizes s.s/s.y and
+ * s.y/y.y (s, y the changes of u and g; the previous tau is kept when s.y <= 0).
+ * Stops when the largest normalized torque |u_i x h_i| / |h_i|, h = -m_e G, is
+ * below tol (the paper uses 1e-5) or after maxit steps; the chain's state is
+ * replaced by the result.  Outputs (HOST, each may be NULL): steps taken, final
+ * largest torque (compare with tol to see convergence), energy terms E[7] of the
+ * result as mmc_energy.  Uniform chains below Tc only (MMC_ERR_UNSUPPORTED for
+ * per-cell material, MMC_ERR_ARG at or above Tc). */
+mmc_status mmc_minimize(mmc_ctx *ctx, int chain, int64_t maxit, double tol, int64_t *iters, double *torque,
+                        double E[7]);
+
 /* Per-kernel timing: runs n MMC iterations eagerly (as mmc_sweep, without
  * graphs) with CUDA events recorded on the context's stream around every kernel
  * and returns, per kernel kind, the summed duration in ms (ms) and the number
@@ -270,15 +293,17 @@ mmc_status mmc_energy_grad(mmc_ctx *ctx, int chain, const void *m, int fp64, con
  * Both arrays have 6 entries (HOST). */
 mmc_status mmc_phase_times(mmc_ctx *ctx, int64_t n, uint64_t seed, double ms[6], int64_t count[6]);
 
-/* FFT variant of the batch's FP32 2D demag kernels (1 radix 16, 2 radix 32;
- * 0 when the batch does not use them) and, when mmc_options.fft_variant was 0,
- * the per-update times in ms that the create-time timing measured for the two
- * variants (else zeros).  The variants compute the same convolution with FP32
- * rounding in a different order, so the demag field, and through it the chain,
- * can differ between them at rounding level; set the variant explicitly where
- * runs must repeat bit for bit across contexts.  (HOST outputs.)  Not a paper
- * quantity: a tuning record of this implementation. */
-mmc_status mmc_fft_tuning(const mmc_ctx *ctx, int *variant, double ms[2]);
+/* FFT variant of the batch's FP32 2D demag kernels (1 radix 16 with 768-thread
+ * blocks, 2 radix 32 with 384-thread blocks, 3 radix 16 with 384-thread blocks,
+ * two per SM; 0 when the batch does not use them) and, when
+ * mmc_options.fft_variant was 0, the per-update times in ms that the
+ * create-time timing measured for the three variants (0 for a variant that was
+ * not timed).  The variants compute the same convolution with FP32 rounding in
+ * a different order, so the demag field, and through it the chain, can differ
+ * between them at rounding level; set the variant explicitly where runs must
+ * repeat bit for bit across contexts.  (HOST outputs.)  Not a paper quantity: a
+ * tuning record of this implementation. */
+mmc_status mmc_fft_tuning(const mmc_ctx *ctx, int *variant, double ms[3]);
 
 /* Number of kernels the library launched since create (all kinds). */
 int64_t mmc_kernel_launches(const mmc_ctx *ctx);

@@ -117,6 +117,8 @@ def lib():
         L.orc_pass.restype = C.c_int64
         L.orc_pass.argtypes = [C.c_void_p, dp, dp, C.c_int, C.c_uint32, C.c_uint32, C.c_uint64,
                                C.c_double, C.POINTER(C.c_int8), dp, dp]
+        L.orc_sdesc.restype = C.c_int
+        L.orc_sdesc.argtypes = [C.c_void_p, dp, C.c_int, C.c_double, C.POINTER(C.c_int), dp]
         L.orc_serial_sweep.restype = C.c_int64
         L.orc_serial_sweep.argtypes = [C.c_void_p, dp, dp, C.c_uint32, C.c_uint32, C.c_uint64, C.c_double]
         L.orc_run.restype = C.c_int64
@@ -340,6 +342,15 @@ class Oracle:
         nacc = lib().orc_serial_sweep(self._ctx, _dp(mm), _dp(Hh), int(sweep), int(chain),
                                       int(seed), float(theta_deg))
         return mm.reshape(self.n, 3), Hh.reshape(self.n, 3), nacc
+
+    def sdesc(self, m, maxit=20000, tol=1e-5):
+        """Zero-temperature steepest descent (Sec. III SDesc) from m; returns
+        (m_min (n, 3), converged, iterations, final max normalized torque)."""
+        mm = self._m(m).copy()
+        it = C.c_int(0)
+        tq = np.zeros(1)
+        rc = lib().orc_sdesc(self._ctx, _dp(mm), int(maxit), float(tol), C.byref(it), _dp(tq))
+        return mm.reshape(self.n, 3), rc == 0, int(it.value), float(tq[0])
 
     def init_state(self, random=False, direction=(1.0, 0.0, 0.0), length=1.0, chain=0, seed=1):
         m = np.zeros(3 * self.n)

@@ -1095,3 +1095,81 @@ void orc_energy_grad(orc_ctx *c, const double *m, double *g, double dEdp[5], dou
     dEdp[3] = c->K1[0] != 0.0 ? E[3] / c->K1[0] : 0.0;
     dEdp[4] = c->chi[0] != 0.0 ? -E[5] / c->chi[0] : 0.0;
 }
+
+
+/* Sec. III comparison method (SDesc): zero-temperature steepest descent with
+ * the lengths held at m_e(T) of each cell (the temperature enters only through
+ * the rescaled parameters, as in the MMC energy).  With u_i = m_i / m_e,i unit
+ * vectors, the tangential gradient is g_i = m_e,i (G_i - (G_i . u_i) u_i),
+ * G = dE/dm; a step is u_i <- (u_i - tau g_i) / |u_i - tau g_i|.  tau: the first
+ * step turns the cell with the largest gradient by 0.01 rad; afterwards the
+ * Barzilai-Borwein step sizes s.s / s.y (odd steps) and s.y / y.y (even
+ * steps) with s = u - u_prev, y = g - g_prev, keeping the previous tau when
+ * s.y <= 0.  Stops when the largest normalized torque |u_i x h_i| / |h_i|
+ * (h = -m_e G) is below tol. */
+int orc_sdesc(orc_ctx *c, double *m, int maxit, double tol, int *iters, double *torque)
+{
+    const int n = c->n;
+    double *u = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *up = (double *)calloc(3 * (size_t)n, sizeof(double));
+    double *G = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *g = (double *)calloc(3 * (size_t)n, sizeof(double));
+    double *gp = (double *)calloc(3 * (size_t)n, sizeof(double));
+    double *mm = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double dEdp[5], E[7];
+    for (int q = 0; q < n; ++q) {
+        double l = sqrt(m[3 * q] * m[3 * q] + m[3 * q + 1] * m[3 * q + 1] + m[3 * q + 2] * m[3 * q + 2]);
+        for (int a = 0; a < 3; ++a) u[3 * q + a] = l > 0 ? m[3 * q + a] / l : (a == 0 ? 1.0 : 0.0);
+    }
+    double tau = 0.0, tmax = 0.0;
+    int it = 0, done = 0;
+    for (;;) {
+        for (int q = 0; q < n; ++q)
+            for (int a = 0; a < 3; ++a) mm[3 * q + a] = c->me[q] * u[3 * q + a];
+        orc_energy_grad(c, mm, G, dEdp, E);
+        double ss = 0, sy = 0, yy = 0, gmax = 0;
+        tmax = 0.0;
+        for (int q = 0; q < n; ++q) {
+            const double *uq = u + 3 * q, *Gq = G + 3 * q;
+            double me = c->me[q];
+            double d = Gq[0] * uq[0] + Gq[1] * uq[1] + Gq[2] * uq[2];
+            double gn2 = 0, Gn2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                double ga = me * (Gq[a] - d * uq[a]);
+                g[3 * q + a] = ga;
+                gn2 += ga * ga;
+                Gn2 += me * me * Gq[a] * Gq[a];
+                double sa = uq[a] - up[3 * q + a], ya = ga - gp[3 * q + a];
+                ss += sa * sa; sy += sa * ya; yy += ya * ya;
+            }
+            double r = Gn2 > 0 ? sqrt(gn2 / Gn2) : 0.0;   /* |u x h| / |h| */
+            if (r > tmax) tmax = r;
+            if (gn2 > gmax) gmax = gn2;
+        }
+        if (tmax < tol) { done = 1; break; }
+        if (it >= maxit) break;
+        if (it == 0) {
+            tau = gmax > 0 ? 0.01 / sqrt(gmax) : 0.0;
+        } else if (sy > 0) {
+            tau = (it & 1) ? ss / sy : sy / yy;
+        }
+        for (int q = 0; q < n; ++q) {
+            double v[3], l2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                up[3 * q + a] = u[3 * q + a];
+                gp[3 * q + a] = g[3 * q + a];
+                v[a] = u[3 * q + a] - tau * g[3 * q + a];
+                l2 += v[a] * v[a];
+            }
+            double il = 1.0 / sqrt(l2);
+            for (int a = 0; a < 3; ++a) u[3 * q + a] = v[a] * il;
+        }
+        ++it;
+    }
+    for (int q = 0; q < n; ++q)
+        for (int a = 0; a < 3; ++a) m[3 * q + a] = c->me[q] * u[3 * q + a];
+    if (iters) *iters = it;
+    if (torque) *torque = tmax;
+    free(u); free(up); free(G); free(g); free(gp); free(mm);
+    return done ? 0 : 1;
+}

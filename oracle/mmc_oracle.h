@@ -132,6 +132,12 @@ int64_t orc_pass(orc_ctx *c, double *m, const double *H, int color, uint32_t swe
 int64_t orc_serial_sweep(orc_ctx *c, double *m, double *H, uint32_t sweep,
                          uint32_t chain, uint64_t seed, double theta_deg);
 
+/* Sec. III comparison method (SDesc): steepest descent over directions with
+ * |m_i| = m_e(T_i), Barzilai-Borwein steps, until the largest normalized
+ * torque is below tol (or maxit steps).  m in/out (3 n).  Returns 0 when
+ * converged, 1 otherwise. */
+int orc_sdesc(orc_ctx *c, double *m, int maxit, double tol, int *iters, double *torque);
+
 /* Run state carried across orc_run calls. */
 typedef struct {
     uint64_t seed;

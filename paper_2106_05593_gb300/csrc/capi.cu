@@ -84,7 +84,17 @@ struct ChainHost {
   std::vector<float> grain;             // natural order, or empty
 };
 
+// block tables of the 2D interleaved kernels for one block size E
+struct IlTables {
+  bool ok = false;
+  int *rows_chain = nullptr, *cols_chain = nullptr;
+  long long *rows_first = nullptr, *cols_first = nullptr;
+  int rows_blocks = 0, cols_blocks = 0;
+  size_t rows_smem = 0, cols_smem = 0, inv_smem = 0;
+};
+
 struct DemagPlan {
+  IlTables small;                       // FP32 variant 3: E = 6144 (2 blocks per SM)
   bool fp64 = false;
   ChainDev *d_ch = nullptr;             // chain table the plan indexes
   int *rows_chain = nullptr;
@@ -147,7 +157,7 @@ struct mmc_ctx {
   DemagPlan batch_plan;
   std::vector<CufftGroup> cf;           // cuFFT comparison path (demag_cufft)
   int tuned_variant = 0;                // FFT variant picked at create (0: not tuned)
-  double tune_ms[2] = {0.0, 0.0};       // per-update time of the two variants when tuned
+  double tune_ms[3] = {0.0, 0.0, 0.0};  // per-update time of the variants when tuned
   std::vector<DemagPlan> single[2];     // per chain and precision (0 FP32, 1 FP64), built lazily
   // serial exact-demag sweep: real-space tensors per set, proposals scratch
   bool serial_ready = false;
@@ -155,6 +165,9 @@ struct mmc_ctx {
   int4 *d_oct_dim = nullptr;
   float4 *d_prop = nullptr;
   size_t serial_smem = 0;
+  // steepest-descent minimizer scratch (sized for the largest chain, built lazily)
+  double *d_sd = nullptr;       // u, m, u_prev, g_prev, G, g: 6 x 3 max_ncell
+  double *d_sd_part = nullptr, *d_sd_out = nullptr;
   double *d_g8 = nullptr;
   double *d_Hd = nullptr, *d_eout = nullptr, *d_etab = nullptr;
   float4 *d_nat = nullptr;
@@ -163,6 +176,9 @@ struct mmc_ctx {
   long long max_ncell = 0, max_slots = 0;
   long long launches = 0;
   uint64_t host_sweep = 0;
+  bool heff_stale = true;               // state or field changed since the last demag update
+  bool obs_fresh = false;               // current-state observables of all chains are up to date
+  int *d_flag = nullptr;                // device scratch int (input checks)
   std::vector<GraphEntry> graphs;
   std::vector<void *> allocs;
 
@@ -404,6 +420,44 @@ inline long long split_index(const ChainDev &D, int i, int row) {
   return (long long)col * D.nrows * D.hx + (long long)row * D.hx + (i >> 1);
 }
 
+mmc_status build_il_tables(mmc_ctx *c, IlTables &T, const std::vector<ChainDev> &table, int E, bool fp64) {
+  const size_t csz = fp64 ? 16 : 8;
+  int maxPx = 1, maxPy = 1, minPx = 1 << 30;
+  for (const ChainDev &D : table) {
+    if (D.Pz != 1 || 3 * D.Px > E || 3 * D.Py > E) return MMC_OK;   // T.ok stays false
+    maxPx = std::max(maxPx, D.Px);
+    maxPy = std::max(maxPy, D.Py);
+    minPx = std::min(minPx, D.Px);
+  }
+  std::vector<int> rc, colc;
+  std::vector<long long> rf, colf;
+  for (size_t t = 0; t < table.size(); ++t) {
+    const ChainDev &D = table[t];
+    const int np = E / (3 * D.Px);
+    const int nb = ((D.nrows + 1) / 2 + np - 1) / np;
+    rf.push_back((long long)rc.size());
+    for (int b = 0; b < nb; ++b) rc.push_back((int)t);
+    const int CC = E / (3 * D.Py);
+    const int nc = D.Sx / CC;
+    colf.push_back((long long)colc.size());
+    for (int b = 0; b < nc; ++b) colc.push_back((int)t);
+  }
+  rf.push_back((long long)rc.size());
+  colf.push_back((long long)colc.size());
+  MMC_TRY(upload(c, &T.rows_chain, rc));
+  MMC_TRY(upload(c, &T.rows_first, rf));
+  MMC_TRY(upload(c, &T.cols_chain, colc));
+  MMC_TRY(upload(c, &T.cols_first, colf));
+  T.rows_blocks = (int)rc.size();
+  T.cols_blocks = (int)colc.size();
+  const int Ep = il_padded_of(E);
+  T.rows_smem = (size_t)(Ep + maxPx) * csz;
+  T.cols_smem = (size_t)(Ep + maxPy) * csz;
+  T.inv_smem = (size_t)(Ep + 2 * (E / minPx) + maxPx) * csz;
+  T.ok = true;
+  return MMC_OK;
+}
+
 mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &chains, bool fp64,
                             bool single) {
   const size_t csz = fp64 ? 16 : 8;
@@ -452,9 +506,10 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
     // Py for the column kernel); the inverse row kernel keeps a side array between
     int minPx = 1 << 30;
     for (const ChainDev &D : table) minPx = std::min(minPx, D.Px);
-    rsmem = (size_t)(E + maxPx) * csz;
-    csmem = (size_t)(E + maxPyPz) * csz;
-    P.inv_smem = (size_t)(E + 2 * (E / minPx) + maxPx) * csz;
+    const int Ep = il_padded_elements(fp64);
+    rsmem = (size_t)(Ep + maxPx) * csz;
+    csmem = (size_t)(Ep + maxPyPz) * csz;
+    P.inv_smem = (size_t)(Ep + 2 * (E / minPx) + maxPx) * csz;
   } else {
     const int Gmax = std::max(maxPx / 8, 1);
     T = std::min(512, std::max(64, 3 * Gmax));
@@ -501,8 +556,13 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
   P.cols_cc = cc;
   P.cols_smem = csmem;
   P.fp64 = fp64;
-  P.fft_variant = c->opt.fft_variant == 1 || c->opt.fft_variant == 2 ? c->opt.fft_variant
-                  : (c->tuned_variant ? c->tuned_variant : 1);
+  if (il && !fp64) MMC_TRY(build_il_tables(c, P.small, table, il_elements_small(), false));
+  {
+    int v = c->opt.fft_variant >= 1 && c->opt.fft_variant <= 3 ? c->opt.fft_variant
+            : (c->tuned_variant ? c->tuned_variant : 1);
+    if (v == 3 && !P.small.ok) v = 1;
+    P.fft_variant = v;
+  }
   MMC_TRY(dalloc(c, &P.spec, (size_t)spec_elems * csz));
   CUDA_TRY(cudaMemset(P.spec, 0, (size_t)spec_elems * csz));   // padding columns stay defined
   P.ready = true;
@@ -538,6 +598,11 @@ DemagLaunch make_demag_launch(mmc_ctx *c, const DemagPlan &P, float4 *heff, doub
   D.il2d = P.il2d;
   D.fft_variant = P.fft_variant;
   D.inv_smem = P.inv_smem;
+  if (P.il2d && P.fft_variant == 3 && P.small.ok) {
+    D.rows_chain = P.small.rows_chain; D.rows_first = P.small.rows_first; D.rows_blocks = P.small.rows_blocks;
+    D.cols_chain = P.small.cols_chain; D.cols_first = P.small.cols_first; D.cols_blocks = P.small.cols_blocks;
+    D.rows_smem = P.small.rows_smem; D.cols_smem = P.small.cols_smem; D.inv_smem = P.small.inv_smem;
+  }
   return D;
 }
 
@@ -707,6 +772,8 @@ mmc_status sweep_impl(mmc_ctx *c, int64_t n, uint64_t seed, int sample_every) {
     c->host_sweep += (uint64_t)k;
     n -= k;
   }
+  c->heff_stale = true;
+  c->obs_fresh = false;
   return MMC_OK;
 }
 
@@ -1022,7 +1089,8 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     cudaEvent_t e0, e1;
     CUDA_TRY_OR(cudaEventCreate(&e0));
     CUDA_TRY_OR(cudaEventCreate(&e1));
-    for (int v = 1; v <= 2; ++v) {
+    for (int v = 1; v <= 3; ++v) {
+      if (v == 3 && !c->batch_plan.small.ok) continue;
       c->batch_plan.fft_variant = v;
       issue_demag(c);
       CUDA_TRY_OR(cudaEventRecord(e0, c->stream));
@@ -1107,6 +1175,7 @@ mmc_status mmc_set_field(mmc_ctx *c, int chain, const double B[3]) {
     CUDA_TRY(cudaMemcpyAsync(c->d_ch + i, &c->ch[i], sizeof(ChainDev), cudaMemcpyHostToDevice, c->stream));
   }
   CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->heff_stale = true;
   return MMC_OK;
 }
 
@@ -1115,6 +1184,7 @@ mmc_status mmc_demag_update(mmc_ctx *c) {
   if (!c->any_demag) return MMC_OK;
   issue_demag(c);
   MMC_TRY(check_launch());
+  c->heff_stale = false;
   return MMC_OK;
 }
 
@@ -1122,18 +1192,23 @@ mmc_status mmc_set_m(mmc_ctx *c, int chain, const float *src, int is_device) {
   MMC_TRY(check_chain(c, chain));
   if (!src) return fail(MMC_ERR_ARG, "null source");
   const long long n = c->hc[chain].ncell;
-  if (!is_device) {
-    for (long long i = 0; i < 4 * n; ++i)
-      if ((i & 3) != 3 && !std::isfinite(src[i])) return fail(MMC_ERR_NONFINITE, "non-finite value in m");
-    CUDA_TRY(cudaMemcpyAsync(c->d_nat, src, (size_t)n * sizeof(float4), cudaMemcpyHostToDevice, c->stream));
-  } else {
-    CUDA_TRY(cudaMemcpyAsync(c->d_nat, src, (size_t)n * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
-  }
+  if (!c->d_flag) MMC_TRY(dalloc_t(c, &c->d_flag, 1));
+  CUDA_TRY(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  CUDA_TRY(cudaMemcpyAsync(c->d_nat, src, (size_t)n * sizeof(float4),
+                           is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   Launch L = c->L();
+  // the copy is checked on the device before the state is touched; the wait
+  // below also ends the use of the caller's buffer
+  launch_check_finite(L, c->d_nat, n, c->d_flag);
+  MMC_TRY(check_launch());
+  int bad = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (bad) return fail(MMC_ERR_NONFINITE, "non-finite value in m");
   launch_pack(L, c->d_ch, chain, c->hc[chain].slots, c->d_m, c->d_nat, 1);
   MMC_TRY(check_launch());
-  MMC_TRY(mmc_demag_update(c));
-  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->heff_stale = true;
+  c->obs_fresh = false;
   return MMC_OK;
 }
 
@@ -1173,8 +1248,9 @@ mmc_status mmc_init_random(mmc_ctx *c, uint64_t seed, double len) {
     CUDA_TRY(cudaStreamSynchronize(c->stream));
   }
   MMC_TRY(check_launch());
-  MMC_TRY(mmc_demag_update(c));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->heff_stale = true;
+  c->obs_fresh = false;
   return MMC_OK;
 }
 
@@ -1207,6 +1283,8 @@ mmc_status mmc_sweep_serial(mmc_ctx *c, int64_t n, uint64_t seed) {
     c->host_sweep += (uint64_t)k;
     n -= k;
   }
+  c->heff_stale = true;
+  c->obs_fresh = false;
   return MMC_OK;
 }
 
@@ -1216,6 +1294,7 @@ mmc_status mmc_pass_debug(mmc_ctx *c, int chain, int color, uint32_t sweep, uint
   if (color != 0 && color != 1) return fail(MMC_ERR_ARG, "color must be 0 or 1");
   if (!(theta_deg >= 0 && theta_deg <= 180)) return fail(MMC_ERR_ARG, "theta_deg must be in [0, 180]");
   const long long n = c->hc[chain].ncell;
+  if (c->any_demag && c->heff_stale) MMC_TRY(mmc_demag_update(c));
   CUDA_TRY(cudaMemcpyAsync(c->d_dbg_sweep, &sweep, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(cudaMemsetAsync(c->d_dec, 0, (size_t)n * sizeof(float), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->d_acc, 0xff, (size_t)n, c->stream));
@@ -1230,6 +1309,8 @@ mmc_status mmc_pass_debug(mmc_ctx *c, int chain, int color, uint32_t sweep, uint
   Launch L = c->L();
   launch_sweep_pass(L, P);
   MMC_TRY(check_launch());
+  c->obs_fresh = false;                 // accepted moves changed the state
+  c->heff_stale = true;
   if (dec) CUDA_TRY(cudaMemcpyAsync(dec, c->d_dec, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   if (acc) CUDA_TRY(cudaMemcpyAsync(acc, c->d_acc, (size_t)n, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1245,10 +1326,13 @@ mmc_status mmc_observables(mmc_ctx *c, int chain, mmc_obs *out, int reset) {
   const int nb = c->opt.hist_bins + 1;
   std::vector<unsigned long long> h((size_t)nb, 0);
   if (s.nsnap == 0) {
-    CUDA_TRY(cudaMemsetAsync(c->d_hist_cur, 0, (size_t)c->nchains * nb * sizeof(unsigned long long), c->stream));
-    Launch L = c->L();
-    launch_obs(L, obs_launch(c, 0));
-    MMC_TRY(check_launch());
+    if (!c->obs_fresh) {   // one reduction serves every chain until the state changes
+      CUDA_TRY(cudaMemsetAsync(c->d_hist_cur, 0, (size_t)c->nchains * nb * sizeof(unsigned long long), c->stream));
+      Launch L = c->L();
+      launch_obs(L, obs_launch(c, 0));
+      MMC_TRY(check_launch());
+      c->obs_fresh = true;
+    }
     double o[8];
     CUDA_TRY(cudaMemcpyAsync(o, c->d_obs_out + 8 * chain, sizeof(o), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaMemcpyAsync(h.data(), c->d_hist_cur + (size_t)chain * nb, nb * sizeof(unsigned long long),
@@ -1425,6 +1509,54 @@ mmc_status mmc_energy_grad(mmc_ctx *c, int chain, const void *m, int fp64, const
   return MMC_OK;
 }
 
+mmc_status mmc_minimize(mmc_ctx *c, int chain, int64_t maxit, double tol, int64_t *iters, double *torque,
+                        double E[7]) {
+  MMC_TRY(check_chain(c, chain));
+  if (!(tol > 0) || maxit < 0) return fail(MMC_ERR_ARG, "tol must be > 0 and maxit >= 0");
+  const ChainHost &H = c->hc[chain];
+  if (H.percell) return fail(MMC_ERR_UNSUPPORTED, "steepest descent of a chain with per-cell material");
+  if (!(H.me[0] > 0)) return fail(MMC_ERR_ARG, "steepest descent needs T < Tc (m_e > 0)");
+  const long long n = H.ncell;
+  const double me = H.me[0];
+  if (!c->d_sd) {
+    MMC_TRY(dalloc_t(c, &c->d_sd, (size_t)18 * c->max_ncell));
+    MMC_TRY(dalloc_t(c, &c->d_sd_part, (size_t)5 * sd_blocks(c->max_ncell)));
+    MMC_TRY(dalloc_t(c, &c->d_sd_out, 8));
+  }
+  const size_t v3 = (size_t)3 * c->max_ncell;
+  double *u = c->d_sd, *m = u + v3, *up = m + v3, *gp = up + v3, *G = gp + v3, *g = G + v3;
+  Launch L = c->L();
+  CUDA_TRY(cudaMemsetAsync(up, 0, 2 * v3 * sizeof(double), c->stream));
+  launch_sd_init(L, c->d_ch, chain, n, c->d_m, me, u, m);
+  MMC_TRY(check_launch());
+  double tau = 0.0, tmax = 0.0, e7[7] = {0, 0, 0, 0, 0, 0, 0};
+  int64_t it = 0;
+  for (;;) {
+    MMC_TRY(mmc_energy_grad(c, chain, m, 1, nullptr, e7, G, nullptr));
+    launch_sd_dir(L, n, me, u, G, g, up, gp, c->d_sd_part, c->d_sd_out);
+    MMC_TRY(check_launch());
+    double o[5];
+    CUDA_TRY(cudaMemcpyAsync(o, c->d_sd_out, sizeof(o), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    tmax = o[4];
+    if (!(tmax >= tol) || it >= maxit) break;        // converged (or NaN torque), or out of steps
+    if (it == 0) tau = o[3] > 0 ? 0.01 / std::sqrt(o[3]) : 0.0;
+    else if (o[1] > 0) tau = (it & 1) ? o[0] / o[1] : o[1] / o[2];
+    launch_sd_step(L, n, me, tau, u, g, up, gp, m);
+    ++it;
+  }
+  launch_sd_store(L, c->d_ch, chain, n, m, c->d_m);
+  MMC_TRY(check_launch());
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->heff_stale = true;
+  c->obs_fresh = false;
+  if (iters) *iters = it;
+  if (torque) *torque = tmax;
+  if (E) for (int k = 0; k < 7; ++k) E[k] = e7[k];
+  if (!(tmax == tmax)) return fail(MMC_ERR_NONFINITE, "steepest descent produced a non-finite torque");
+  return MMC_OK;
+}
+
 mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[6], int64_t count[6]) {
   if (!c || !ms || !count) return fail(MMC_ERR_ARG, "null argument");
   if (n < 0) return fail(MMC_ERR_ARG, "negative sweep count");
@@ -1450,16 +1582,17 @@ mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[6], i
     n -= k;
   }
   for (auto e : pt.pool) cudaEventDestroy(e);
+  c->heff_stale = true;
+  c->obs_fresh = false;
   return st;
 }
 
 int64_t mmc_kernel_launches(const mmc_ctx *c) { return c ? c->launches : 0; }
 
-mmc_status mmc_fft_tuning(const mmc_ctx *c, int *variant, double ms[2]) {
+mmc_status mmc_fft_tuning(const mmc_ctx *c, int *variant, double ms[3]) {
   if (!c || !variant || !ms) return fail(MMC_ERR_ARG, "null argument");
   *variant = c->batch_plan.ready && c->batch_plan.il2d ? c->batch_plan.fft_variant : 0;
-  ms[0] = c->tune_ms[0];
-  ms[1] = c->tune_ms[1];
+  for (int k = 0; k < 3; ++k) ms[k] = c->tune_ms[k];
   return MMC_OK;
 }
 int mmc_nchains(const mmc_ctx *c) { return c ? c->nchains : 0; }
@@ -1534,6 +1667,8 @@ mmc_status mmc_restore(mmc_ctx *c, const void *buf, size_t len) {
   const unsigned base = (unsigned)h.host_sweep;
   CUDA_TRY(cudaMemcpyAsync(c->d_sweep_base, &base, sizeof(base), cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->heff_stale = true;
+  c->obs_fresh = false;
   return MMC_OK;
 }
 

@@ -96,6 +96,17 @@ template <typename C, int R> __device__ __forceinline__ void dft_r(C *u) {
   else if (R == 2) dft2(u[0], u[1]);
 }
 
+// Shared-memory view of a block's data with one padding element after every
+// 2^kIlPad elements, so that the strided stores of a Stockham pass (neighbouring
+// butterflies R * nseq elements apart) fall in different banks; 0 disables it.
+constexpr int kIlPad = 4;
+template <typename C> struct SView {
+  C *p;
+  __device__ __forceinline__ C &operator[](int x) const { return kIlPad ? p[x + (x >> kIlPad)] : p[x]; }
+};
+// elements a view of e logical elements occupies
+__host__ __device__ constexpr int il_padded(int e) { return kIlPad ? e + (e >> kIlPad) + 1 : e; }
+
 struct IlMap {
   int lnseq;        // log2 of the interleaved sequences per group (a power of two)
   int ngroups, gstride;
@@ -106,7 +117,7 @@ struct IlMap {
 // half of every sequence is known to be zero and is not read.  HALFOUT (last
 // pass only): only the lower half of every output sequence is stored.
 template <typename C, int R, int V, bool INV, bool ZIN, bool HALFOUT>
-__device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C *__restrict__ tw, int twshift) {
+__device__ __forceinline__ void il_pass(SView<C> buf, int N, int p, IlMap mp, const C *__restrict__ tw, int twshift) {
   constexpr int NB = V / R;
   const int nbf = N / R;              // compile-time: N and R are template constants
   const int nseq = 1 << mp.lnseq;
@@ -167,7 +178,7 @@ __device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C 
 // possible, then the remaining factor; the passes are straight-line code so every pass's register
 // arrays have their own short lifetime.
 template <typename C, int V, bool INV, int N, int P, bool ZIN, bool HALFOUT>
-__device__ __forceinline__ void fft_passes(C *buf, IlMap mp, const C *__restrict__ tw, int twshift) {
+__device__ __forceinline__ void fft_passes(SView<C> buf, IlMap mp, const C *__restrict__ tw, int twshift) {
   if constexpr (P < N) {
     constexpr int REM = N / P;
     constexpr int RMAX = V >= 32 ? 32 : 16;      // radix 32 when a thread holds 32 values
@@ -184,7 +195,7 @@ __device__ __forceinline__ void fft_passes(C *buf, IlMap mp, const C *__restrict
 // ZIN: the upper half of every input sequence is zero (zero padding) and is
 // never read; HALFOUT: only the lower half of every output is written back.
 template <typename C, int V, bool INV, bool ZIN = false, bool HALFOUT = false>
-__device__ __forceinline__ void fft_il(C *buf, int logN, IlMap mp, const C *__restrict__ tw, bool local) {
+__device__ __forceinline__ void fft_il(SView<C> buf, int logN, IlMap mp, const C *__restrict__ tw, bool local) {
   const int twshift = local ? 0 : 12 - logN;
   switch (logN) {
     case 1: fft_passes<C, V, INV, 2, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;

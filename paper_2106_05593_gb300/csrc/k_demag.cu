@@ -298,6 +298,7 @@ __global__ void k_rows_inv(DemagArgs<R> A) {
 struct CfgF16 { using R = float; static constexpr int E = 12288, V = 16, MINB = 1; };
 struct CfgF32 { using R = float; static constexpr int E = 12288, V = 32, MINB = 1; };
 struct CfgD16 { using R = double; static constexpr int E = 6144, V = 16, MINB = 1; };
+struct CfgF16h { using R = float; static constexpr int E = 6144, V = 16, MINB = 2; };
 
 // index of (comp, y, kx) in the column-tiled spectrum layout [comp][kx / CC][y][CC], CC = 2^lcc
 __device__ __forceinline__ long long tiled(int comp, int y, int kx, int ny, int NG, int lcc) {
@@ -312,7 +313,8 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagA
   using C = typename Cx<R>::T;
   constexpr int E = CFG::E, V = CFG::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *buf = reinterpret_cast<C *>(smem_raw);
+  C *raw = reinterpret_cast<C *>(smem_raw);
+  const SView<C> buf{raw};
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagA
   const int lcc = LE3 - ch.ly, CC = 1 << lcc, NG = Sx >> lcc;
   const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
   const int totpairs = (ny + 1) / 2;
-  C *tws = buf + E;                          // twiddles exp(-2 pi i j / Px), j < Px
+  C *tws = raw + il_padded(E);               // twiddles exp(-2 pi i j / Px), j < Px
   for (int j = threadIdx.x; j < Px; j += blockDim.x) tws[j] = A.tw[j << (12 - lx)];
   // the upper half x >= Px/2 is zero padding the first FFT pass never reads
 #pragma unroll 4
@@ -346,10 +348,10 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagA
       }
     }
     C z;
-    C *el = buf + x * np + qq;
-    z.x = M0x; z.y = M0y; el[0] = z;
-    z.x = M1x; z.y = M1y; el[gs] = z;
-    z.x = M0z; z.y = M1z; el[2 * gs] = z;
+    const int e0 = x * np + qq;
+    z.x = M0x; z.y = M0y; buf[e0] = z;
+    z.x = M1x; z.y = M1y; buf[e0 + gs] = z;
+    z.x = M0z; z.y = M1z; buf[e0 + 2 * gs] = z;
   }
   __syncthreads();
   fft_il<C, V, false, true, false>(buf, lx, IlMap{lnp, 3, gs}, tws, true);
@@ -384,7 +386,8 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
   using C = typename Cx<R>::T;
   constexpr int E = CFG::E, V = CFG::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *buf = reinterpret_cast<C *>(smem_raw);
+  C *raw = reinterpret_cast<C *>(smem_raw);
+  const SView<C> buf{raw};
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, Py = ch.Py, ly = ch.ly, ny = ch.ny, Sx = ch.Sx;
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
   const int kx0 = g * CC;
   const int qx = Px / 2 + 1, qy = Py / 2 + 1;
   const C *S = A.S + ch.s_off;
-  C *tws = buf + E;                          // twiddles exp(-2 pi i j / Py), j < Py
+  C *tws = raw + il_padded(E);               // twiddles exp(-2 pi i j / Py), j < Py
   for (int j = threadIdx.x; j < Py; j += blockDim.x) tws[j] = A.tw[j << (12 - ly)];
   // buf[(comp * Py + y) * CC + cc]; rows y >= ny are the zero padding, and the
   // upper half y >= Py/2 is never read by the first FFT pass
@@ -444,8 +447,9 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_inv2(DemagA
   using C = typename Cx<R>::T;
   constexpr int E = CFG::E, V = CFG::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *buf = reinterpret_cast<C *>(smem_raw);
-  C *side = buf + E;                        // B[0] and B[Px/2] of each sequence
+  C *raw = reinterpret_cast<C *>(smem_raw);
+  const SView<C> buf{raw};
+  C *side = raw + il_padded(E);             // B[0] and B[Px/2] of each sequence
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
@@ -476,29 +480,29 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_inv2(DemagA
     v.x = 0; v.y = 0;
     if (r < ny) v = S[tiled(comp, r, kx, ny, NG, lcc)];
     const int s = sq * np + qq;                 // side-array index of the sequence
-    C *seq = buf + sq * gs + qq;
-    if (!is_b) seq[kx * np] = v;
+    const int sb = sq * gs + qq;
+    if (!is_b) buf[sb + kx * np] = v;
     else if (kx == 0) side[2 * s] = v;
     else if (2 * kx == Px) side[2 * s + 1] = v;
-    else seq[(Px - kx) * np] = v;
+    else buf[sb + (Px - kx) * np] = v;
   }
   __syncthreads();
   // z[k] = a[k] + i b[k], z[Px-k] = conj(a[k]) + i conj(b[k]); real parts only at k = 0, Px/2
   for (int idx = threadIdx.x; idx < nseq * half; idx += blockDim.x) {
     const int kx = (idx >> lnp) / 3, s = idx - kx * nseq;
-    C *seq = buf + (s >> lnp) * gs + (s & (np - 1));
+    const int sb = (s >> lnp) * gs + (s & (np - 1));
     if (kx == 0 || 2 * kx == Px) {
-      const C a = seq[kx * np], b = side[2 * s + (kx == 0 ? 0 : 1)];
+      const C a = buf[sb + kx * np], b = side[2 * s + (kx == 0 ? 0 : 1)];
       C z;
       z.x = a.x; z.y = b.x;
-      seq[kx * np] = z;
+      buf[sb + kx * np] = z;
     } else {
-      const C a = seq[kx * np], b = seq[(Px - kx) * np];
+      const C a = buf[sb + kx * np], b = buf[sb + (Px - kx) * np];
       C zk, zm;
       zk.x = a.x - b.y; zk.y = a.y + b.x;
       zm.x = a.x + b.y; zm.y = b.x - a.y;
-      seq[kx * np] = zk;
-      seq[(Px - kx) * np] = zm;
+      buf[sb + kx * np] = zk;
+      buf[sb + (Px - kx) * np] = zm;
     }
   }
   __syncthreads();
@@ -567,6 +571,7 @@ void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
   if (P.il2d) {
     if constexpr (sizeof(R) == 8) launch_il<CfgD16>(L, P, A);
     else if (P.fft_variant == 2) launch_il<CfgF32>(L, P, A);
+    else if (P.fft_variant == 3) launch_il<CfgF16h>(L, P, A);
     else launch_il<CfgF16>(L, P, A);
     return;
   }
@@ -604,11 +609,12 @@ cudaError_t demag_set_smem_limits() {
   e = cudaFuncSetAttribute(k_rows_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e != cudaSuccess) return e;
   const int lil = 200 * 1024;
-  const void *fns[9] = {(const void *)k_rows_fwd2<CfgF16>, (const void *)k_rows_fwd2<CfgF32>,
-                        (const void *)k_rows_fwd2<CfgD16>, (const void *)k_cols2d<CfgF16>,
-                        (const void *)k_cols2d<CfgF32>, (const void *)k_cols2d<CfgD16>,
-                        (const void *)k_rows_inv2<CfgF16>, (const void *)k_rows_inv2<CfgF32>,
-                        (const void *)k_rows_inv2<CfgD16>};
+  const void *fns[12] = {(const void *)k_rows_fwd2<CfgF16>, (const void *)k_rows_fwd2<CfgF32>,
+                         (const void *)k_rows_fwd2<CfgD16>, (const void *)k_rows_fwd2<CfgF16h>,
+                         (const void *)k_cols2d<CfgF16>, (const void *)k_cols2d<CfgF32>,
+                         (const void *)k_cols2d<CfgD16>, (const void *)k_cols2d<CfgF16h>,
+                         (const void *)k_rows_inv2<CfgF16>, (const void *)k_rows_inv2<CfgF32>,
+                         (const void *)k_rows_inv2<CfgD16>, (const void *)k_rows_inv2<CfgF16h>};
   for (const void *f : fns) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lil);
     if (e != cudaSuccess) return e;
@@ -617,5 +623,8 @@ cudaError_t demag_set_smem_limits() {
 }
 
 int il_elements(bool fp64) { return fp64 ? CfgD16::E : CfgF16::E; }
+int il_padded_elements(bool fp64) { return il_padded(il_elements(fp64)); }
+int il_elements_small() { return CfgF16h::E; }
+int il_padded_of(int e) { return il_padded(e); }
 
 }  // namespace mmc

@@ -262,6 +262,21 @@ __global__ void k_pack(const ChainDev *chains, int c, float4 *m, const float4 *n
   }
 }
 
+// flag = 1 if any of the first three components of v[0..n) is not finite
+__global__ void k_check_finite(const float4 *v, long long n, int *flag) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const float4 a = v[q];
+    if (!isfinite(a.x) || !isfinite(a.y) || !isfinite(a.z)) *flag = 1;
+  }
+}
+
+void launch_check_finite(const Launch &L, const float4 *v, long long n, int *flag) {
+  long long nb = (n + 255) / 256;
+  if (nb > 152 * 16) nb = 152 * 16;
+  k_check_finite<<<(int)(nb < 1 ? 1 : nb), 256, 0, L.stream>>>(v, n, flag);
+  ++*L.counter;
+}
+
 void launch_pack(const Launch &L, const ChainDev *chains_d, int c, long long slots, float4 *m,
                  const float4 *nat, int to_split) {
   const int nb = (int)((2 * slots + 255) / 256);

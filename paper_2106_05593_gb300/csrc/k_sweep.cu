@@ -6,8 +6,8 @@
 // m_off + c * nrows * hx + r * hx + s.  The neighbours of a colour-c cell are all
 // in the other colour's array: the in-row ones at slots s - 1 + p and s + p
 // (p = (j + k + c) & 1), the ones in rows j +- 1 and planes k +- 1 at slot s.
-// One thread updates one cell; a block covers 256 consecutive slots of one
-// chain, so a launch covers every chain of the batch.
+// A block covers 256 consecutive slots of one chain (128 threads, two cells
+// each), so a launch covers every chain of the batch.
 //
 // Per cell: Philox4x32-10 at counter (cell, sweep, chain, 0) gives u0..u3;
 // the move is a rotation uniform on the cap of half-angle theta about m/|m|
@@ -42,8 +42,15 @@ struct SweepArgs {
   signed char *acc_dbg;
 };
 
+// A thread handles kSweepCells cells of its block's 256 slots (slot t + j 128):
+// the loads of all of them are issued before any is computed, so each thread
+// keeps two independent trials in flight and the block prologue (block table,
+// chain constants) is paid once per two cells.
+constexpr int kSweepCells = 2;
+constexpr int kSweepThreads = kSweepBlock / kSweepCells;
+
 template <bool PERCELL, bool DEBUG>
-__global__ void __launch_bounds__(kSweepBlock, 4) k_sweep_pass(SweepArgs A) {
+__global__ void __launch_bounds__(kSweepThreads, 5) k_sweep_pass(SweepArgs A) {
   const int blk = A.blk_base + (int)blockIdx.x;
   const int c = A.blk_chain[blk];
   const ChainK K = load_chain(A.chains + c);
@@ -51,56 +58,59 @@ __global__ void __launch_bounds__(kSweepBlock, 4) k_sweep_pass(SweepArgs A) {
   // a chain has fewer than 2^31 cells: 32-bit slot arithmetic
   const unsigned S32 = (unsigned)K.nrows * (unsigned)hx;
   const long long S = (long long)S32;
-  const unsigned q32 = (unsigned)(blk - (int)A.blk_first[c]) * (unsigned)kSweepBlock + threadIdx.x;
-  const long long q = (long long)q32;
+  const unsigned q0 = (unsigned)(blk - (int)A.blk_first[c]) * (unsigned)kSweepBlock + threadIdx.x;
   const int color = A.color;
-  bool valid = q32 < S32;
-  const int row = valid ? (int)divq(q32, K.hx_m, K.hx_l) : 0;
-  const int s = (int)(q32 - (unsigned)row * (unsigned)hx);
-  const int k = (int)divq((unsigned)row, K.ny_m, K.ny_l), j = row - k * ny;
-  const int p = (j + k + color) & 1;
-  const int i = 2 * s + p;
-  valid = valid && (i < nx);
-  int accepted = 0;
+  const int flags = K.flags;
+  float4 *mc = A.m + K.m_off + (long long)color * S;
+  const float4 *mo = A.m + K.m_off + (long long)(1 - color) * S;
+  const float omc = A.omc_override >= 0.f ? A.omc_override : A.st[c].omc;
+  const unsigned sweep = *A.sweep_base + A.sweep_off;
 
-  if (valid) {
-    const int flags = K.flags;
-    float4 *mc = A.m + K.m_off + (long long)color * S;
-    const float4 *mo = A.m + K.m_off + (long long)(1 - color) * S;
-    const float4 a = mc[q];
-
-    // neighbours (other colour); absent bonds have weight 0
-    float4 nb[6];
-    float w[6];
-    load_neighbours(K.pbc, (flags & F_GRAIN) != 0, K.gscale, nx, ny, nz, hx, mo, a, i, j, k, row, s, p, nb, w);
-
-    // material constants of this cell (kT units)
-    const CellMat M = cell_material<PERCELL>(K, A.tab, S, (long long)color * S + q);
-    const float wx = K.wx * M.bs, wy = K.wy * M.bs, wz = K.wz * M.bs;
-    const float cdx = K.cdx * M.bs, cdy = K.cdy * M.bs;
-
-    // static field: h = zee (B + mu0 H_d), kT per unit m
-    float hxs, hys, hzs;
-    if (flags & F_DEMAG) {
-      const float4 h = A.heff[K.h_off + (long long)color * S + q];
-      hxs = h.x; hys = h.y; hzs = h.z;
-    } else {
-      hxs = M.zee * K.Bx; hys = M.zee * K.By; hzs = M.zee * K.Bz;
+  // 1. indices and loads of every cell of this thread
+  bool valid[kSweepCells];
+  unsigned qq[kSweepCells], cellid[kSweepCells];
+  float4 a[kSweepCells], h[kSweepCells];
+  float4 nb[kSweepCells][6];
+  float w[kSweepCells][6];
+  CellMat M[kSweepCells];
+#pragma unroll
+  for (int e = 0; e < kSweepCells; ++e) {
+    const unsigned q32 = q0 + (unsigned)(e * kSweepThreads);
+    bool ok = q32 < S32;
+    const int row = ok ? (int)divq(q32, K.hx_m, K.hx_l) : 0;
+    const int s = (int)(q32 - (unsigned)row * (unsigned)hx);
+    const int k = (int)divq((unsigned)row, K.ny_m, K.ny_l), j = row - k * ny;
+    const int p = (j + k + color) & 1;
+    const int i = 2 * s + p;
+    ok = ok && (i < nx);
+    valid[e] = ok;
+    qq[e] = q32;
+    cellid[e] = (unsigned)i + (unsigned)nx * (unsigned)row;
+    if (ok) {
+      a[e] = mc[q32];
+      load_neighbours(K.pbc, (flags & F_GRAIN) != 0, K.gscale, nx, ny, nz, hx, mo, a[e], i, j, k, row, s, p, nb[e], w[e]);
+      M[e] = cell_material<PERCELL>(K, A.tab, S, (long long)color * S + q32);
+      if (flags & F_DEMAG) h[e] = A.heff[K.h_off + (long long)color * S + q32];
+      else h[e] = make_float4(M[e].zee * K.Bx, M[e].zee * K.By, M[e].zee * K.Bz, 0.f);
     }
+  }
 
-    // random numbers
-    const unsigned cell = (unsigned)i + (unsigned)nx * (unsigned)row;
-    const unsigned sweep = *A.sweep_base + A.sweep_off;
-    const uint4 r = philox4x32_10(make_uint4(cell, sweep, (unsigned)K.chain, 0u), make_uint2(A.key0, A.key1));
+  // 2. the trials
+  int accepted[kSweepCells];
+#pragma unroll
+  for (int e = 0; e < kSweepCells; ++e) {
+    accepted[e] = 0;
+    if (!valid[e]) continue;
+    const float wx = K.wx * M[e].bs, wy = K.wy * M[e].bs, wz = K.wz * M[e].bs;
+    const float cdx = K.cdx * M[e].bs, cdy = K.cdy * M[e].bs;
+    const uint4 r = philox4x32_10(make_uint4(cellid[e], sweep, (unsigned)K.chain, 0u), make_uint2(A.key0, A.key1));
     const float u0 = uniform01(r.x), u1 = uniform01(r.y), u2 = uniform01(r.z), u3 = uniform01(r.w);
-
-    Move v = move_length(a, M.me2h, M.me2l);
-    const float omc = A.omc_override >= 0.f ? A.omc_override : A.st[c].omc;
-    move_direction(v, a, M.sigma, omc, u0, u1, u2);
-    const float fex = exchange_change(v, a, nb, w, wx, wy, wz, nz > 1);
-    const float flin = linear_change(v, nb, w, cdx, cdy, (flags & F_DMI) != 0, hxs, hys, hzs);
-    const float flong = longitudinal_change(v, M.p2, M.p4);
-    const float fan = anisotropy_change(v, flags, M.k1, M.k2, M.ex, M.ey, M.ez);
+    Move v = move_length(a[e], M[e].me2h, M[e].me2l);
+    move_direction(v, a[e], M[e].sigma, omc, u0, u1, u2);
+    const float fex = exchange_change(v, a[e], nb[e], w[e], wx, wy, wz, nz > 1);
+    const float flin = linear_change(v, nb[e], w[e], cdx, cdy, (flags & F_DMI) != 0, h[e].x, h[e].y, h[e].z);
+    const float flong = longitudinal_change(v, M[e].p2, M[e].p4);
+    const float fan = anisotropy_change(v, flags, M[e].k1, M[e].k2, M[e].ex, M[e].ey, M[e].ez);
     const float dF = fex + flin + flong + fan;
     const float lg = log1p_move(v.tt);
     const float dl = dF - 4.f * lg;
@@ -108,28 +118,32 @@ __global__ void __launch_bounds__(kSweepBlock, 4) k_sweep_pass(SweepArgs A) {
     float dec;
     if (DEBUG || dl > 0.f) dec = dl + __logf(u3);
     else dec = dl;
-    accepted = dec < 0.f;
-    if (accepted) mc[q] = make_float4(v.mpx, v.mpy, v.mpz, a.w);
+    accepted[e] = dec < 0.f;
+    if (accepted[e]) mc[qq[e]] = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
     if (DEBUG) {
-      A.dec_dbg[cell] = dec;
-      A.acc_dbg[cell] = (signed char)accepted;
+      A.dec_dbg[cellid[e]] = dec;
+      A.acc_dbg[cellid[e]] = (signed char)accepted[e];
     }
   }
 
   // acceptance counts: warp ballots, then one atomic per block
-  __shared__ unsigned wacc[kSweepBlock / 32], watt[kSweepBlock / 32];
-  const unsigned ba = __ballot_sync(0xffffffffu, accepted);
-  const unsigned bv = __ballot_sync(0xffffffffu, valid);
+  __shared__ unsigned wacc[kSweepThreads / 32], watt[kSweepThreads / 32];
+  unsigned na = 0, nv = 0;
+#pragma unroll
+  for (int e = 0; e < kSweepCells; ++e) {
+    na += __popc(__ballot_sync(0xffffffffu, accepted[e]));
+    nv += __popc(__ballot_sync(0xffffffffu, valid[e]));
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
-    wacc[warp] = __popc(ba);
-    watt[warp] = __popc(bv);
+    wacc[warp] = na;
+    watt[warp] = nv;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned sa = 0, sv = 0;
 #pragma unroll
-    for (int w2 = 0; w2 < kSweepBlock / 32; ++w2) { sa += wacc[w2]; sv += watt[w2]; }
+    for (int w2 = 0; w2 < kSweepThreads / 32; ++w2) { sa += wacc[w2]; sv += watt[w2]; }
     if (sv) {
       atomicAdd(&A.st[c].win_acc, (unsigned long long)sa);
       atomicAdd(&A.st[c].win_att, (unsigned long long)sv);
@@ -146,11 +160,11 @@ void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
   A.omc_override = P.omc_override; A.dec_dbg = P.dec_dbg; A.acc_dbg = P.acc_dbg;
   const bool dbg = P.dec_dbg != nullptr;
   if (P.percell) {
-    if (dbg) k_sweep_pass<true, true><<<P.nblocks, kSweepBlock, 0, L.stream>>>(A);
-    else k_sweep_pass<true, false><<<P.nblocks, kSweepBlock, 0, L.stream>>>(A);
+    if (dbg) k_sweep_pass<true, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A);
+    else k_sweep_pass<true, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A);
   } else {
-    if (dbg) k_sweep_pass<false, true><<<P.nblocks, kSweepBlock, 0, L.stream>>>(A);
-    else k_sweep_pass<false, false><<<P.nblocks, kSweepBlock, 0, L.stream>>>(A);
+    if (dbg) k_sweep_pass<false, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A);
+    else k_sweep_pass<false, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A);
   }
   ++*L.counter;
 }

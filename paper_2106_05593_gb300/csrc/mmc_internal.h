@@ -192,6 +192,16 @@ void launch_serial_sweep(const Launch &L, const SerialLaunch &P);
 size_t serial_smem_need(const ChainDev &ch);
 cudaError_t serial_set_smem_limit(size_t bytes);
 
+// steepest-descent minimizer (k_sdesc.cu)
+int sd_blocks(long long n);
+void launch_sd_init(const Launch &L, const ChainDev *chains, int c, long long n, const float4 *mstate, double me,
+                    double *u, double *m);
+void launch_sd_dir(const Launch &L, long long n, double me, const double *u, const double *G, double *g,
+                   const double *up, const double *gp, double *part, double *out5);
+void launch_sd_step(const Launch &L, long long n, double me, double tau, double *u, const double *g, double *up,
+                    double *gp, double *m);
+void launch_sd_store(const Launch &L, const ChainDev *chains, int c, long long n, const double *m, float4 *mstate);
+
 struct DemagLaunch {
   const ChainDev *chains;
   const float4 *m;
@@ -219,6 +229,9 @@ struct DemagLaunch {
   size_t inv_smem;              // shared memory of the 2D inverse row kernel
 };
 int il_elements(bool fp64);     // complex elements per block of the 2D kernels
+int il_padded_elements(bool fp64);   // shared-memory elements those occupy (bank padding)
+int il_padded_of(int e);             // shared-memory elements of e logical elements
+int il_elements_small();             // block size of the 2-blocks-per-SM FP32 variant
 void launch_demag(const Launch &L, const DemagLaunch &P, bool fp64);
 cudaError_t demag_set_smem_limits();
 
@@ -261,6 +274,7 @@ void launch_energy(const Launch &L, const ChainDev *chains_d, int c, long long s
 void launch_energy_grad(const Launch &L, const ChainDev *chains_d, int c, long long ncell, const void *m,
                         bool fp64, const double *Hd, const GradCoef &G, void *dEdm, double *part,
                         double *out8);
+void launch_check_finite(const Launch &L, const float4 *v, long long n, int *flag);
 void launch_pack(const Launch &L, const ChainDev *chains_d, int c, long long slots, float4 *m,
                  const float4 *nat, int to_split);
 void launch_init_random(const Launch &L, const ChainDev *chains_d, int c, long long slots, float4 *m,

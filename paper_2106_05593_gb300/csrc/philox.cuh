@@ -15,16 +15,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
       k.x += 0x9E3779B9u;
       k.y += 0xBB67AE85u;
     }
-    const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    // one 32 x 32 -> 64-bit product per multiplier (both halves at once)
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    const unsigned lo0 = (unsigned)p0, hi0 = (unsigned)(p0 >> 32);
+    const unsigned lo1 = (unsigned)p1, hi1 = (unsigned)(p1 >> 32);
     c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
   }
   return c;
 }
 
-// uniform in (0, 1): ((r >> 9) + 1/2) * 2^-23, exact in FP32
+// uniform in (0, 1): ((r >> 9) + 1/2) * 2^-23, exact in FP32.  Built from the
+// bits: 1 + (r >> 9) 2^-23 is a float in [1, 2) whose mantissa is r >> 9, and
+// subtracting 1 - 2^-24 is exact (Sterbenz: the operands are within a factor 2).
 __device__ __forceinline__ float uniform01(unsigned r) {
-  return ((float)(r >> 9) + 0.5f) * 1.1920928955078125e-07f;
+  return __uint_as_float(0x3F800000u | (r >> 9)) - 0.99999994039535522461f;
 }
 
 }  // namespace mmc

@@ -104,6 +104,26 @@ __device__ __forceinline__ void load_neighbours(int pbc, bool grain, float gscal
   }
 }
 
+// sin(pi x) and cos(pi x) for x in [0, 2]: x = n / 2 + r with n = rint(2 x) and
+// |r| <= 1/4 (r exact), sin and cos of t = pi r from their Taylor series through
+// t^9 and t^10 (|t| <= pi / 4: truncation below 2e-9), then the rotation by
+// n quarter turns.
+__device__ __forceinline__ void sincospi_move(float x, float &s, float &c) {
+  const float n = rintf(2.f * x);
+  const float r = fmaf(-0.5f, n, x);
+  const float t = 3.14159265358979323846f * r;
+  const float t2 = t * t;
+  // 1/3!, 1/5!, 1/7!, 1/9!  and  1/2!, 1/4!, 1/6!, 1/8!, 1/10!
+  const float sr = t * fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 2.7557319224e-6f, -1.9841269841e-4f),
+                                               8.3333333333e-3f), -1.6666666667e-1f), 1.f);
+  const float cr = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, -2.7557319224e-7f, 2.4801587302e-5f),
+                                                    -1.3888888889e-3f), 4.1666666667e-2f), -0.5f), 1.f);
+  const int q = (int)n & 3;
+  const float a = (q & 1) ? cr : sr, b = (q & 1) ? sr : cr;
+  s = (q & 2) ? -a : a;
+  c = ((q + 1) & 2) ? -b : b;
+}
+
 // The move: a rotation uniform on the cap of half-angle theta about m/|m|
 // (cos = 1 - u0 (1 - cos theta), phi = 2 pi u1, orthonormal basis of Duff et
 // al., JCGT 6(1), 2017) times the length factor 1 + sigma (2 u2 - 1).
@@ -152,7 +172,7 @@ __device__ __forceinline__ void move_direction(Move &v, float4 a, float sigma, f
   const float t2 = t * (2.f - t);                  // > 0: t = u0 (1 - cos theta) in (0, 2)
   const float st = t2 * rsqrtf(t2);
   float sp, cp;
-  sincospif(2.f * u1, &sp, &cp);
+  sincospi_move(2.f * u1, sp, cp);
   v.dx = ct * v.n0 + st * (cp * e1x + sp * e2x);
   v.dy = ct * v.n1 + st * (cp * e1y + sp * e2y);
   v.dz = ct * v.n2 + st * (cp * e1z + sp * e2z);

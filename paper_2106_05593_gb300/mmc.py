@@ -148,6 +148,19 @@ class MMC:
         order, demag field updated after every accepted move."""
         check(load().mmc_sweep_serial(self._ctx, int(n), int(seed)), "mmc_sweep_serial")
 
+    def minimize(self, chain=0, maxit=20000, tol=1e-5):
+        """Zero-temperature steepest descent of one chain (the paper's SDesc,
+        Sec. III); the chain's state becomes the result.  Returns a dict with
+        the steps taken, the final largest normalized torque and the energy
+        terms of the result."""
+        it = C.c_int64(0)
+        tq = np.zeros(1)
+        E = np.zeros(7)
+        check(load().mmc_minimize(self._ctx, int(chain), int(maxit), float(tol), C.byref(it), _dptr(tq), _dptr(E)),
+              "mmc_minimize")
+        return {"iters": int(it.value), "torque": float(tq[0]), "converged": bool(tq[0] < tol),
+                "energy": E.copy()}
+
     def sweep_sampled(self, n, seed, every):
         check(load().mmc_sweep_sampled(self._ctx, int(n), int(seed), int(every)), "mmc_sweep_sampled")
 
@@ -222,11 +235,11 @@ class MMC:
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(kinds)}
 
     def fft_tuning(self):
-        """(variant, (ms radix-16, ms radix-32)) of the FP32 2D demag kernels."""
+        """(variant, create-time ms of variants 1, 2, 3) of the FP32 2D demag kernels."""
         v = C.c_int(0)
-        ms = np.zeros(2)
+        ms = np.zeros(3)
         check(load().mmc_fft_tuning(self._ctx, C.byref(v), _dptr(ms)), "mmc_fft_tuning")
-        return int(v.value), (float(ms[0]), float(ms[1]))
+        return int(v.value), tuple(float(x) for x in ms)
 
     @property
     def launches(self) -> int:
