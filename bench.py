@@ -217,6 +217,30 @@ def cpu_baseline(specs, demag, nsweeps=3):
                       f"{nsweeps} iterations after 1 warm-up, demag {'FFT FP64' if demag else 'off'}"}
 
 
+def replica_seed(rank):
+    """Seed of rank's replica: every rank runs the whole workload as an
+    independent replica (weak scaling), so the ranks draw different numbers."""
+    return 1 + rank
+
+
+def reduce_max(x, device):
+    """Max of x over all ranks (identity without a process group); the device
+    follows the backend (CUDA tensors for NCCL, CPU tensors for gloo)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(local_ms, units_per_rank, world, device):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time.  Returns (max ms, units / s)."""
+    ms_max = reduce_max(local_ms, device)
+    return ms_max, units_per_rank * world / (ms_max * 1e-3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -272,13 +296,13 @@ def run_ours(args):
     if args.profile_run > 0:
         gp = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), use_graphs=0,
                  fft_variant=args.fft_variant, stream=stream)
-        gp.init_random(1 + rank)
-        gp.sweep(args.profile_run, 1 + rank)
+        gp.init_random(replica_seed(rank))
+        gp.sweep(args.profile_run, replica_seed(rank))
         torch.cuda.synchronize()
         print("profile run ok", gp.launches, flush=True)
         return
     g = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=args.fft_variant, stream=stream)
-    seed = 1 + rank
+    seed = replica_seed(rank)
     g.init_random(seed)
     ncell = sum(g.ncell)
     cells_per_step = ncell * SWEEPS_PER_STEP
@@ -307,11 +331,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     launches = g.launches - l0
     clk = clocks.stop()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = cells_per_step * args.steps * world / (ms_max * 1e-3)
+    ms_max, value = job_throughput(ms, cells_per_step * args.steps, world, "cuda")
 
     # per-kernel durations (CUDA events on the library's stream), one more window
     phases = g.phase_times(SWEEPS_PER_STEP, seed)
@@ -397,11 +417,8 @@ def run_ours(args):
                 d2h += 8 * (3 + 2) + 8 * ob["hist"].size
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = float(tt.item())
-        e2e = {"value": cells_per_step * args.e2e_steps * world / dt, "unit": UNIT,
+        _, e2e_value = job_throughput(1e3 * dt, cells_per_step * args.e2e_steps, world, "cuda")
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(sum(h.nbytes for h in host_m)),
                "d2h_bytes_per_step": int(d2h // args.e2e_steps)}
 

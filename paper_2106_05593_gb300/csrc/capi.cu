@@ -146,6 +146,7 @@ struct mmc_ctx {
   void *d_tw32 = nullptr, *d_tw64 = nullptr;
   int *d_sw_chain = nullptr;
   long long *d_sw_first = nullptr;
+  int2 *d_sw_desc = nullptr;
   std::vector<long long> sw_first;
   int sw_blocks = 0;
   int *d_obs_chain = nullptr;
@@ -619,8 +620,7 @@ SweepLaunch sweep_launch(mmc_ctx *c, int color, unsigned off, unsigned key0, uns
   SweepLaunch P;
   P.chains = c->d_ch;
   P.st = c->d_st;
-  P.blk_chain = c->d_sw_chain;
-  P.blk_first = c->d_sw_first;
+  P.blk_desc = c->d_sw_desc;
   P.blk_base = 0;
   P.nblocks = c->sw_blocks;
   P.m = c->d_m;
@@ -1053,6 +1053,11 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     c->sw_blocks = (int)bc.size();
     MMC_TRY_OR(upload(c, &c->d_sw_chain, bc));
     MMC_TRY_OR(upload(c, &c->d_sw_first, bf));
+    // one 8-byte descriptor per block (chain, block index within the chain):
+    // a single load tells a sweep block where it works
+    std::vector<int2> bd(bc.size());
+    for (size_t b = 0; b < bc.size(); ++b) bd[b] = make_int2(bc[b], (int)((long long)b - bf[(size_t)bc[b]]));
+    MMC_TRY_OR(upload(c, &c->d_sw_desc, bd));
     std::vector<int> oc;
     std::vector<long long> of;
     for (int ci = 0; ci < nchains; ++ci) {

@@ -27,8 +27,7 @@ namespace mmc {
 struct SweepArgs {
   const ChainDev *chains;
   ChainState *st;
-  const int *blk_chain;
-  const long long *blk_first;
+  const int2 *blk_desc;     // per block: (chain, block index within the chain)
   int blk_base;
   float4 *m;
   const float4 *heff;
@@ -51,14 +50,14 @@ constexpr int kSweepThreads = kSweepBlock / kSweepCells;
 
 template <bool PERCELL, bool DEBUG>
 __global__ void __launch_bounds__(kSweepThreads, 5) k_sweep_pass(SweepArgs A) {
-  const int blk = A.blk_base + (int)blockIdx.x;
-  const int c = A.blk_chain[blk];
+  const int2 bd = A.blk_desc[A.blk_base + (int)blockIdx.x];
+  const int c = bd.x;
   const ChainK K = load_chain(A.chains + c);
   const int nx = K.nx, ny = K.ny, nz = K.nz, hx = K.hx;
   // a chain has fewer than 2^31 cells: 32-bit slot arithmetic
   const unsigned S32 = (unsigned)K.nrows * (unsigned)hx;
   const long long S = (long long)S32;
-  const unsigned q0 = (unsigned)(blk - (int)A.blk_first[c]) * (unsigned)kSweepBlock + threadIdx.x;
+  const unsigned q0 = (unsigned)bd.y * (unsigned)kSweepBlock + threadIdx.x;
   const int color = A.color;
   const int flags = K.flags;
   float4 *mc = A.m + K.m_off + (long long)color * S;
@@ -153,7 +152,7 @@ __global__ void __launch_bounds__(kSweepThreads, 5) k_sweep_pass(SweepArgs A) {
 
 void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
   SweepArgs A;
-  A.chains = P.chains; A.st = P.st; A.blk_chain = P.blk_chain; A.blk_first = P.blk_first;
+  A.chains = P.chains; A.st = P.st; A.blk_desc = P.blk_desc;
   A.blk_base = P.blk_base;
   A.m = P.m; A.heff = P.heff; A.tab = P.tab; A.sweep_base = P.sweep_base;
   A.sweep_off = P.sweep_off; A.key0 = P.key0; A.key1 = P.key1; A.color = P.color;

@@ -149,8 +149,7 @@ struct Launch {
 struct SweepLaunch {
   const ChainDev *chains;
   ChainState *st;
-  const int *blk_chain;
-  const long long *blk_first;
+  const int2 *blk_desc;         // per block: (chain, block index within the chain)
   int blk_base;                 // first block of this launch in the block tables
   int nblocks;
   float4 *m;
