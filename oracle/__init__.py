@@ -56,7 +56,7 @@ class _Problem(C.Structure):
         ("Ms0", C.POINTER(C.c_double)), ("K1", C.POINTER(C.c_double)),
         ("K2", C.POINTER(C.c_double)), ("eA", C.POINTER(C.c_double)),
         ("Tc", C.POINTER(C.c_double)), ("T", C.POINTER(C.c_double)),
-        ("grain", C.POINTER(C.c_int)),
+        ("grain", C.POINTER(C.c_int)), ("cell_base", C.c_uint32),
     ]
 
 
@@ -261,6 +261,7 @@ class Oracle:
         p.demag = int(bool(spec.get("demag", False)))
         p.demag_self = int(bool(demag_self))
         p.len_power = int(len_power)
+        p.cell_base = int(spec.get("cell_base", 0))
         p.aniso_cubic = 1 if spec.get("aniso", "uniaxial") == "cubic" else 0
         for k in ("Ms0", "K1", "K2", "eA", "Tc", "T"):
             setattr(p, k, _dp(self._keep[k]))

@@ -849,7 +849,7 @@ static int trial(orc_ctx *c, double *m, const double *H, int q, uint32_t sweep, 
                  uint64_t seed, double cos_tc, double *dec, double *band)
 {
     double u[4], mn[3], t[7];
-    draw4((uint32_t)q, sweep, chain, 0u, seed, u);
+    draw4((uint32_t)q + c->p.cell_base, sweep, chain, 0u, seed, u);
     propose(m + 3 * q, cos_tc, c->sigma[q], u, mn);
     orc_local_dF(c, m, H, q, mn, t);
     double kT = c->kT[q];

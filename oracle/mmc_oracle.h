@@ -64,6 +64,9 @@ typedef struct {
     const double *Tc;           /* Curie temperature (K) */
     const double *T;            /* temperature (K) */
     const int *grain;           /* grain id per cell, or NULL for a single grain */
+    uint32_t cell_base;         /* natural index of this mesh's first cell in a larger
+                                   lattice it is a window of (the Philox counter word 0
+                                   is the cell's index in the whole lattice); 0 normally */
 } orc_problem;
 
 typedef struct orc_ctx orc_ctx;

@@ -49,7 +49,7 @@ constexpr int kSweepCells = 2;
 constexpr int kSweepThreads = kSweepBlock / kSweepCells;
 
 template <bool PERCELL, bool DEBUG>
-__global__ void __launch_bounds__(kSweepThreads, 5) k_sweep_pass(SweepArgs A) {
+__global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 6) k_sweep_pass(SweepArgs A) {
   const int2 bd = A.blk_desc[A.blk_base + (int)blockIdx.x];
   const int c = bd.x;
   const ChainK K = load_chain(A.chains + c);

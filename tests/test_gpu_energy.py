@@ -113,3 +113,14 @@ def test_full_size_energy3d_sampled(P):
         rel = np.linalg.norm(d - go) / np.linalg.norm(go)
         print("energy3d 256x256x4", dt, "grad rel", rel, "E rel", abs(E[0] - Eo[0]) / abs(Eo[0]))
         assert rel < tol
+        # time one forward + backward evaluation (the call returns after the
+        # device work and the read-back of the energies), after a warm-up
+        import time
+        for _ in range(3):
+            g.energy_grad(mt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(10):
+            g.energy_grad(mt)
+        torch.cuda.synchronize()
+        print("energy3d 256x256x4", dt, "forward+backward ms %.3f" % ((time.perf_counter() - t0) * 100))

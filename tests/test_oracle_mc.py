@@ -231,3 +231,23 @@ def test_serial_form_without_demag_is_the_index_order_sweep():
         m1, acc, _, _ = o.sweep_pass(cur, None, (i + j) & 1, 0, 0, 9, 40.0)
         cur[q] = m1[q]
     assert np.array_equal(ms, cur)
+
+
+def test_window_of_rows_reproduces_the_full_pass():
+    """A band of rows given with the natural index of its first cell (the
+    Philox counter is the cell's index in the whole lattice) decides its
+    interior rows exactly as the pass over the whole film."""
+    import workloads as W
+    full = W._base((24, 16, 1), (4e-9, 4e-9, 4e-9), D0=1e-3, K1=2e5, B=(0.01, 0.0, 0.02))
+    rng = np.random.default_rng(5)
+    m = rng.standard_normal((24 * 16, 3))
+    m *= 0.8 / np.linalg.norm(m, axis=1, keepdims=True)
+    r0, nr = 4, 8
+    _, acc_f, dec_f, _ = O.Oracle(full).sweep_pass(m, None, 1, 3, 0, 17, 40.0)
+    band = dict(full, mesh=(24, nr, 1), cell_base=r0 * 24)
+    mb = m.reshape(16, 24, 3)[r0:r0 + nr].reshape(-1, 3)
+    _, acc_b, dec_b, _ = O.Oracle(band).sweep_pass(mb, None, 1, 3, 0, 17, 40.0)   # r0 even: same colours
+    inner = slice(24, (nr - 1) * 24)
+    full_inner = slice((r0 + 1) * 24, (r0 + nr - 1) * 24)
+    assert np.array_equal(acc_b[inner], acc_f[full_inner])
+    assert np.array_equal(dec_b[inner], dec_f[full_inner])
