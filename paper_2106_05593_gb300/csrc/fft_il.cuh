@@ -96,16 +96,15 @@ template <typename C, int R> __device__ __forceinline__ void dft_r(C *u) {
   else if (R == 2) dft2(u[0], u[1]);
 }
 
-// Shared-memory view of a block's data with one padding element after every
-// 2^kIlPad elements, so that the strided stores of a Stockham pass (neighbouring
-// butterflies R * nseq elements apart) fall in different banks; 0 disables it.
+// Bank padding: the stores of a first Stockham pass put neighbouring
+// butterflies R * nseq elements apart, which maps many lanes of a warp to the
+// same shared-memory bank.  That pass therefore writes, and the next pass reads,
+// a layout with one padding element after every 2^kIlPad elements; all other
+// passes, and the kernels around the transform, use the plain layout.
 constexpr int kIlPad = 4;
-template <typename C> struct SView {
-  C *p;
-  __device__ __forceinline__ C &operator[](int x) const { return kIlPad ? p[x + (x >> kIlPad)] : p[x]; }
-};
-// elements a view of e logical elements occupies
-__host__ __device__ constexpr int il_padded(int e) { return kIlPad ? e + (e >> kIlPad) + 1 : e; }
+template <bool PAD> __device__ __forceinline__ int il_at(int x) { return PAD ? x + (x >> kIlPad) : x; }
+// elements a block buffer of e logical elements must hold (padded layout included)
+__host__ __device__ constexpr int il_padded(int e) { return e + (e >> kIlPad) + 1; }
 
 struct IlMap {
   int lnseq;        // log2 of the interleaved sequences per group (a power of two)
@@ -115,9 +114,10 @@ struct IlMap {
 // one radix-R Stockham pass over all interleaved sequences (p = product of the
 // radices already done); V values per thread.  ZIN (first pass only): the upper
 // half of every sequence is known to be zero and is not read.  HALFOUT (last
-// pass only): only the lower half of every output sequence is stored.
-template <typename C, int R, int V, bool INV, bool ZIN, bool HALFOUT>
-__device__ __forceinline__ void il_pass(SView<C> buf, int N, int p, IlMap mp, const C *__restrict__ tw, int twshift) {
+// pass only): only the lower half of every output sequence is stored.  PIN /
+// POUT: the input / output layout is the padded one.
+template <typename C, int R, int V, bool INV, bool ZIN, bool HALFOUT, bool PIN, bool POUT>
+__device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C *__restrict__ tw, int twshift) {
   constexpr int NB = V / R;
   const int nbf = N / R;              // compile-time: N and R are template constants
   const int nseq = 1 << mp.lnseq;
@@ -142,7 +142,7 @@ __device__ __forceinline__ void il_pass(SView<C> buf, int N, int p, IlMap mp, co
         if (ZIN && 2 * r >= R) {          // element b + r N / R >= N / 2
           t.x = 0; t.y = 0;
         } else {
-          t = buf[addr[i] + ((b + r * nbf) << mp.lnseq)];
+          t = buf[il_at<PIN>(addr[i] + ((b + r * nbf) << mp.lnseq))];
         }
         if (INV) t.y = -t.y;
         v[i * R + r] = t;
@@ -168,7 +168,7 @@ __device__ __forceinline__ void il_pass(SView<C> buf, int N, int p, IlMap mp, co
       if (HALFOUT && 2 * r >= R) continue;   // last pass: output k + r N / R >= N / 2
       C t = u[r];
       if (INV) t.y = -t.y;
-      buf[addr[i] + ((r * p) << mp.lnseq)] = t;
+      buf[il_at<POUT>(addr[i] + ((r * p) << mp.lnseq))] = t;
     }
   }
   __syncthreads();
@@ -177,14 +177,15 @@ __device__ __forceinline__ void il_pass(SView<C> buf, int N, int p, IlMap mp, co
 // Compile-time pass schedule for N = 2^LOGN: radix 32 (V >= 32) or 16 while
 // possible, then the remaining factor; the passes are straight-line code so every pass's register
 // arrays have their own short lifetime.
-template <typename C, int V, bool INV, int N, int P, bool ZIN, bool HALFOUT>
-__device__ __forceinline__ void fft_passes(SView<C> buf, IlMap mp, const C *__restrict__ tw, int twshift) {
+template <typename C, int V, bool INV, int N, int P, bool ZIN, bool HALFOUT, bool PIN = false>
+__device__ __forceinline__ void fft_passes(C *buf, IlMap mp, const C *__restrict__ tw, int twshift) {
   if constexpr (P < N) {
     constexpr int REM = N / P;
     constexpr int RMAX = V >= 32 ? 32 : 16;      // radix 32 when a thread holds 32 values
     constexpr int R = REM >= RMAX ? RMAX : REM;
-    il_pass<C, R, V, INV, ZIN && P == 1, HALFOUT && P * R == N>(buf, N, P, mp, tw, twshift);
-    fft_passes<C, V, INV, N, P * R, ZIN, HALFOUT>(buf, mp, tw, twshift);
+    constexpr bool POUT = P == 1 && P * R < N;   // the first pass writes padded unless it is the last
+    il_pass<C, R, V, INV, ZIN && P == 1, HALFOUT && P * R == N, PIN, POUT>(buf, N, P, mp, tw, twshift);
+    fft_passes<C, V, INV, N, P * R, ZIN, HALFOUT, POUT>(buf, mp, tw, twshift);
   }
 }
 
@@ -195,7 +196,7 @@ __device__ __forceinline__ void fft_passes(SView<C> buf, IlMap mp, const C *__re
 // ZIN: the upper half of every input sequence is zero (zero padding) and is
 // never read; HALFOUT: only the lower half of every output is written back.
 template <typename C, int V, bool INV, bool ZIN = false, bool HALFOUT = false>
-__device__ __forceinline__ void fft_il(SView<C> buf, int logN, IlMap mp, const C *__restrict__ tw, bool local) {
+__device__ __forceinline__ void fft_il(C *buf, int logN, IlMap mp, const C *__restrict__ tw, bool local) {
   const int twshift = local ? 0 : 12 - logN;
   switch (logN) {
     case 1: fft_passes<C, V, INV, 2, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;

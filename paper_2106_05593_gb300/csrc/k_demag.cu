@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagA
   constexpr int E = CFG::E, V = CFG::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *raw = reinterpret_cast<C *>(smem_raw);
-  const SView<C> buf{raw};
+  C *buf = raw;
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
   constexpr int E = CFG::E, V = CFG::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *raw = reinterpret_cast<C *>(smem_raw);
-  const SView<C> buf{raw};
+  C *buf = raw;
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, Py = ch.Py, ly = ch.ly, ny = ch.ny, Sx = ch.Sx;
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_inv2(DemagA
   constexpr int E = CFG::E, V = CFG::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *raw = reinterpret_cast<C *>(smem_raw);
-  const SView<C> buf{raw};
+  C *buf = raw;
   C *side = raw + il_padded(E);             // B[0] and B[Px/2] of each sequence
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
