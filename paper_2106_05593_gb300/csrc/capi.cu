@@ -423,12 +423,11 @@ inline long long split_index(const ChainDev &D, int i, int row) {
 
 mmc_status build_il_tables(mmc_ctx *c, IlTables &T, const std::vector<ChainDev> &table, int E, bool fp64) {
   const size_t csz = fp64 ? 16 : 8;
-  int maxPx = 1, maxPy = 1, minPx = 1 << 30;
+  int maxPx = 1, maxPy = 1;
   for (const ChainDev &D : table) {
     if (D.Pz != 1 || 3 * D.Px > E || 3 * D.Py > E) return MMC_OK;   // T.ok stays false
     maxPx = std::max(maxPx, D.Px);
     maxPy = std::max(maxPy, D.Py);
-    minPx = std::min(minPx, D.Px);
   }
   std::vector<int> rc, colc;
   std::vector<long long> rf, colf;
@@ -454,7 +453,7 @@ mmc_status build_il_tables(mmc_ctx *c, IlTables &T, const std::vector<ChainDev> 
   const int Ep = il_padded_of(E);
   T.rows_smem = (size_t)(Ep + maxPx) * csz;
   T.cols_smem = (size_t)(Ep + maxPy) * csz;
-  T.inv_smem = (size_t)(Ep + 2 * (E / minPx) + maxPx) * csz;
+  T.inv_smem = (size_t)(Ep + maxPx) * csz;
   T.ok = true;
   return MMC_OK;
 }
@@ -503,14 +502,12 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
       colf.push_back((long long)colc.size());
       for (int b = 0; b < nc; ++b) colc.push_back((int)t);
     }
-    // data block, then the block's twiddle table (Px entries for the row kernels,
-    // Py for the column kernel); the inverse row kernel keeps a side array between
-    int minPx = 1 << 30;
-    for (const ChainDev &D : table) minPx = std::min(minPx, D.Px);
+    // data block (padded capacity), then the block's twiddle table (Px entries for
+    // the row kernels, Py for the column kernel)
     const int Ep = il_padded_elements(fp64);
     rsmem = (size_t)(Ep + maxPx) * csz;
     csmem = (size_t)(Ep + maxPyPz) * csz;
-    P.inv_smem = (size_t)(Ep + 2 * (E / minPx) + maxPx) * csz;
+    P.inv_smem = (size_t)(Ep + maxPx) * csz;
   } else {
     const int Gmax = std::max(maxPx / 8, 1);
     T = std::min(512, std::max(64, 3 * Gmax));

@@ -8,8 +8,9 @@
 // every thread loads V complex values (V / R butterflies) into registers,
 // all threads synchronize, then twiddle, transform and store them; a sequence of
 // length N takes ceil(log16 N) passes.  The inverse pass is conj(F(conj(x))).
-// Twiddles come from the FP64-built table tw[t] = exp(-2 pi i t / 4096), or
-// from a block-local copy of the N entries a transform of length N uses.
+// Twiddles come from per-pass tables built from the FP64-built table
+// tw[t] = exp(-2 pi i t / 4096), laid out so that the butterflies of one warp
+// read neighbouring entries.
 #pragma once
 
 #include "fft.cuh"
@@ -116,8 +117,8 @@ struct IlMap {
 // half of every sequence is known to be zero and is not read.  HALFOUT (last
 // pass only): only the lower half of every output sequence is stored.  PIN /
 // POUT: the input / output layout is the padded one.
-template <typename C, int R, int V, bool INV, bool ZIN, bool HALFOUT, bool PIN, bool POUT>
-__device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C *__restrict__ tw, int twshift) {
+template <typename C, int R, int V, bool INV, bool ZIN, bool HALFOUT, bool PIN, bool POUT, int TOFF>
+__device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C *__restrict__ tw) {
   constexpr int NB = V / R;
   const int nbf = N / R;              // compile-time: N and R are template constants
   const int nseq = 1 << mp.lnseq;
@@ -158,9 +159,10 @@ __device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C 
     C *u = v + i * R;
     const int k = kk[i];
     if (k != 0) {
-      const int step = (k * (N / (p * R))) << twshift;
+      // this pass's table: entry (r - 1) p + k is exp(-2 pi i r k / (p R)); butterflies
+      // of neighbouring k read neighbouring entries
 #pragma unroll
-      for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw[r * step]);   // r step < N << twshift
+      for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw[TOFF + (r - 1) * p + k]);
     }
     dft_r<C, R>(u);
 #pragma unroll
@@ -177,40 +179,80 @@ __device__ __forceinline__ void il_pass(C *buf, int N, int p, IlMap mp, const C 
 // Compile-time pass schedule for N = 2^LOGN: radix 32 (V >= 32) or 16 while
 // possible, then the remaining factor; the passes are straight-line code so every pass's register
 // arrays have their own short lifetime.
-template <typename C, int V, bool INV, int N, int P, bool ZIN, bool HALFOUT, bool PIN = false>
-__device__ __forceinline__ void fft_passes(C *buf, IlMap mp, const C *__restrict__ tw, int twshift) {
+template <typename C, int V, bool INV, int N, int P, bool ZIN, bool HALFOUT, bool PIN = false, int TOFF = 0>
+__device__ __forceinline__ void fft_passes(C *buf, IlMap mp, const C *__restrict__ tw) {
   if constexpr (P < N) {
     constexpr int REM = N / P;
     constexpr int RMAX = V >= 32 ? 32 : 16;      // radix 32 when a thread holds 32 values
     constexpr int R = REM >= RMAX ? RMAX : REM;
     constexpr bool POUT = P == 1 && P * R < N;   // the first pass writes padded unless it is the last
-    il_pass<C, R, V, INV, ZIN && P == 1, HALFOUT && P * R == N, PIN, POUT>(buf, N, P, mp, tw, twshift);
-    fft_passes<C, V, INV, N, P * R, ZIN, HALFOUT, POUT>(buf, mp, tw, twshift);
+    il_pass<C, R, V, INV, ZIN && P == 1, HALFOUT && P * R == N, PIN, POUT, TOFF>(buf, N, P, mp, tw);
+    fft_passes<C, V, INV, N, P * R, ZIN, HALFOUT, POUT, TOFF + (P > 1 ? (R - 1) * P : 0)>(buf, mp, tw);
+  }
+}
+
+// Twiddle tables of the passes of a length-N transform, one after the other in
+// the order of the passes (the first pass needs none): for a pass after p
+// elements with radix R, entry (r - 1) p + k (r = 1..R-1, k < p) holds
+// exp(-2 pi i r k / (p R)), taken from the 4096-entry table tw4096.  Together
+// they take at most N entries.
+template <typename C, int V, int N, int P, int TOFF>
+__device__ __forceinline__ void il_build_tw(C *tab, const C *__restrict__ tw4096, int shift) {
+  if constexpr (P < N) {
+    constexpr int REM = N / P;
+    constexpr int RMAX = V >= 32 ? 32 : 16;
+    constexpr int R = REM >= RMAX ? RMAX : REM;
+    if constexpr (P > 1) {
+      constexpr int Q = N / (P * R);
+      for (int t = threadIdx.x; t < (R - 1) * P; t += blockDim.x) {
+        const int r = 1 + t / P, k = t % P;      // P is a power of two
+        tab[TOFF + t] = tw4096[((r * k * Q) & (N - 1)) << shift];
+      }
+    }
+    il_build_tw<C, V, N, P * R, TOFF + (P > 1 ? (R - 1) * P : 0)>(tab, tw4096, shift);
+  }
+}
+
+template <typename C, int V>
+__device__ __forceinline__ void il_twiddles(C *tab, const C *__restrict__ tw4096, int logN) {
+  const int sh = 12 - logN;
+  switch (logN) {
+    case 1: il_build_tw<C, V, 2, 1, 0>(tab, tw4096, sh); break;
+    case 2: il_build_tw<C, V, 4, 1, 0>(tab, tw4096, sh); break;
+    case 3: il_build_tw<C, V, 8, 1, 0>(tab, tw4096, sh); break;
+    case 4: il_build_tw<C, V, 16, 1, 0>(tab, tw4096, sh); break;
+    case 5: il_build_tw<C, V, 32, 1, 0>(tab, tw4096, sh); break;
+    case 6: il_build_tw<C, V, 64, 1, 0>(tab, tw4096, sh); break;
+    case 7: il_build_tw<C, V, 128, 1, 0>(tab, tw4096, sh); break;
+    case 8: il_build_tw<C, V, 256, 1, 0>(tab, tw4096, sh); break;
+    case 9: il_build_tw<C, V, 512, 1, 0>(tab, tw4096, sh); break;
+    case 10: il_build_tw<C, V, 1024, 1, 0>(tab, tw4096, sh); break;
+    case 11: il_build_tw<C, V, 2048, 1, 0>(tab, tw4096, sh); break;
+    case 12: il_build_tw<C, V, 4096, 1, 0>(tab, tw4096, sh); break;
+    default: break;
   }
 }
 
 // Full transform (forward or unnormalized inverse), 2 <= N <= 4096.
-// blockDim.x * V must cover ngroups * nseq * N elements.  tw is either the
-// 4096-entry table exp(-2 pi i t / 4096) (local = false) or a table of the N
-// entries exp(-2 pi i t / N) (local = true, typically staged in shared memory).
-// ZIN: the upper half of every input sequence is zero (zero padding) and is
-// never read; HALFOUT: only the lower half of every output is written back.
+// blockDim.x * V must cover ngroups * nseq * N elements; tw holds the pass
+// tables of il_twiddles (typically in shared memory).  ZIN: the upper half of
+// every input sequence is zero (zero padding) and is never read; HALFOUT: only
+// the lower half of every output is written back.
 template <typename C, int V, bool INV, bool ZIN = false, bool HALFOUT = false>
-__device__ __forceinline__ void fft_il(C *buf, int logN, IlMap mp, const C *__restrict__ tw, bool local) {
-  const int twshift = local ? 0 : 12 - logN;
+__device__ __forceinline__ void fft_il(C *buf, int logN, IlMap mp, const C *__restrict__ tw) {
   switch (logN) {
-    case 1: fft_passes<C, V, INV, 2, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
-    case 2: fft_passes<C, V, INV, 4, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
-    case 3: fft_passes<C, V, INV, 8, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
-    case 4: fft_passes<C, V, INV, 16, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
-    case 5: fft_passes<C, V, INV, 32, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
-    case 6: fft_passes<C, V, INV, 64, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
-    case 7: fft_passes<C, V, INV, 128, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
-    case 8: fft_passes<C, V, INV, 256, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
-    case 9: fft_passes<C, V, INV, 512, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
-    case 10: fft_passes<C, V, INV, 1024, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
-    case 11: fft_passes<C, V, INV, 2048, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
-    case 12: fft_passes<C, V, INV, 4096, 1, ZIN, HALFOUT>(buf, mp, tw, twshift); break;
+    case 1: fft_passes<C, V, INV, 2, 1, ZIN, HALFOUT>(buf, mp, tw); break;
+    case 2: fft_passes<C, V, INV, 4, 1, ZIN, HALFOUT>(buf, mp, tw); break;
+    case 3: fft_passes<C, V, INV, 8, 1, ZIN, HALFOUT>(buf, mp, tw); break;
+    case 4: fft_passes<C, V, INV, 16, 1, ZIN, HALFOUT>(buf, mp, tw); break;
+    case 5: fft_passes<C, V, INV, 32, 1, ZIN, HALFOUT>(buf, mp, tw); break;
+    case 6: fft_passes<C, V, INV, 64, 1, ZIN, HALFOUT>(buf, mp, tw); break;
+    case 7: fft_passes<C, V, INV, 128, 1, ZIN, HALFOUT>(buf, mp, tw); break;
+    case 8: fft_passes<C, V, INV, 256, 1, ZIN, HALFOUT>(buf, mp, tw); break;
+    case 9: fft_passes<C, V, INV, 512, 1, ZIN, HALFOUT>(buf, mp, tw); break;
+    case 10: fft_passes<C, V, INV, 1024, 1, ZIN, HALFOUT>(buf, mp, tw); break;
+    case 11: fft_passes<C, V, INV, 2048, 1, ZIN, HALFOUT>(buf, mp, tw); break;
+    case 12: fft_passes<C, V, INV, 4096, 1, ZIN, HALFOUT>(buf, mp, tw); break;
     default: break;
   }
 }

@@ -325,8 +325,8 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagA
   const int lcc = LE3 - ch.ly, CC = 1 << lcc, NG = Sx >> lcc;
   const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
   const int totpairs = (ny + 1) / 2;
-  C *tws = raw + il_padded(E);               // twiddles exp(-2 pi i j / Px), j < Px
-  for (int j = threadIdx.x; j < Px; j += blockDim.x) tws[j] = A.tw[j << (12 - lx)];
+  C *tws = raw + il_padded(E);               // pass twiddle tables (at most Px entries)
+  il_twiddles<C, V>(tws, A.tw, lx);
   // the upper half x >= Px/2 is zero padding the first FFT pass never reads
 #pragma unroll 4
   for (int idx = threadIdx.x; idx < np * (Px >> 1); idx += blockDim.x) {
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagA
     z.x = M0z; z.y = M1z; buf[e0 + 2 * gs] = z;
   }
   __syncthreads();
-  fft_il<C, V, false, true, false>(buf, lx, IlMap{lnp, 3, gs}, tws, true);
+  fft_il<C, V, false, true, false>(buf, lx, IlMap{lnp, 3, gs}, tws);
   // half spectra (kx <= Px/2) of the six real rows of each pair, written in
   // tiled order: c fastest, then the block's rows, then column group, then comp
   const int half = Px / 2 + 1;
@@ -397,8 +397,8 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
   const int kx0 = g * CC;
   const int qx = Px / 2 + 1, qy = Py / 2 + 1;
   const C *S = A.S + ch.s_off;
-  C *tws = raw + il_padded(E);               // twiddles exp(-2 pi i j / Py), j < Py
-  for (int j = threadIdx.x; j < Py; j += blockDim.x) tws[j] = A.tw[j << (12 - ly)];
+  C *tws = raw + il_padded(E);               // pass twiddle tables (at most Py entries)
+  il_twiddles<C, V>(tws, A.tw, ly);
   // buf[(comp * Py + y) * CC + cc]; rows y >= ny are the zero padding, and the
   // upper half y >= Py/2 is never read by the first FFT pass
 #pragma unroll 8
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
     buf[(comp * Py + y) * CC + cc] = v;
   }
   __syncthreads();
-  fft_il<C, V, false, true, false>(buf, ly, IlMap{lcc, 3, Py * CC}, tws, true);
+  fft_il<C, V, false, true, false>(buf, ly, IlMap{lcc, 3, Py * CC}, tws);
   const long long Q = (long long)qx * qy;
   const R *nh = A.nhat[ch.spec];
   for (int idx = threadIdx.x; idx < Py * CC; idx += blockDim.x) {
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
     buf[b0] = hx_; buf[b1] = hy_; buf[b2] = hz_;
   }
   __syncthreads();
-  fft_il<C, V, true, false, true>(buf, ly, IlMap{lcc, 3, Py * CC}, tws, true);
+  fft_il<C, V, true, false, true>(buf, ly, IlMap{lcc, 3, Py * CC}, tws);
   C *So = A.S + ch.s_off;
   for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
     const int cc = idx & (CC - 1), y = (idx >> lcc) & (Py - 1), comp = idx >> LE3;
@@ -449,64 +449,60 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_inv2(DemagA
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *raw = reinterpret_cast<C *>(smem_raw);
   C *buf = raw;
-  C *side = raw + il_padded(E);             // B[0] and B[Px/2] of each sequence
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
   constexpr int LE3 = ilog2c(E / 3);         // E / 3 is a power of two
-  const int lnp = LE3 - lx, np = 1 << lnp, gs = Px * np, nseq = 3 * np;
+  const int lnp = LE3 - lx, np = 1 << lnp, gs = Px * np;
   const int lcc = LE3 - ch.ly, CC = 1 << lcc, NG = Sx >> lcc;
   const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
   const int half = Px / 2 + 1;
   const int nrb = 2 * np, lnrb = lnp + 1;
   const int ngu = (half + CC - 1) / CC;
   const C *S = A.S + ch.s_off;
-  C *tws = side + 2 * nseq;                  // twiddles exp(-2 pi i j / Px), j < Px
-  for (int j = threadIdx.x; j < Px; j += blockDim.x) tws[j] = A.tw[j << (12 - lx)];
-  // stage: sequence s = a + i b; a[k] at position k, b[k] at position Px - k
-  // (b[0], b[Px/2] in side[])
-  const int tot = 3 * ngu * nrb * CC;
-#pragma unroll 16
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int cc = idx & (CC - 1), rr = (idx >> lcc) & (nrb - 1), o = idx >> (lcc + lnrb);
-    const int comp = (o >= ngu) + (o >= 2 * ngu), g = o - comp * ngu;
-    const int kx = g * CC + cc;
-    if (kx >= half) continue;
-    const int r = 2 * pair0 + rr;
-    const int qq = rr >> 1, h = rr & 1;
-    const int sq = comp == 2 ? 2 : h;
-    const bool is_b = comp == 1 || (comp == 2 && h == 1);
-    C v;
-    v.x = 0; v.y = 0;
-    if (r < ny) v = S[tiled(comp, r, kx, ny, NG, lcc)];
-    const int s = sq * np + qq;                 // side-array index of the sequence
-    const int sb = sq * gs + qq;
-    if (!is_b) buf[sb + kx * np] = v;
-    else if (kx == 0) side[2 * s] = v;
-    else if (2 * kx == Px) side[2 * s + 1] = v;
-    else buf[sb + (Px - kx) * np] = v;
-  }
-  __syncthreads();
-  // z[k] = a[k] + i b[k], z[Px-k] = conj(a[k]) + i conj(b[k]); real parts only at k = 0, Px/2
-  for (int idx = threadIdx.x; idx < nseq * half; idx += blockDim.x) {
-    const int kx = (idx >> lnp) / 3, s = idx - kx * nseq;
-    const int sb = (s >> lnp) * gs + (s & (np - 1));
+  C *tws = raw + il_padded(E);               // pass twiddle tables (at most Px entries)
+  il_twiddles<C, V>(tws, A.tw, lx);
+  // Each sequence is z = a + i b for the half spectra a, b of two real rows:
+  // z[k] = a[k] + i b[k] and z[Px - k] = conj(a[k]) + i conj(b[k]), real parts only
+  // at k = 0 and Px/2 (where the spectra of real rows are real).  Sequence
+  // (h, qq) pairs x and y of row 2 qq + h, sequence (2, qq) the z of rows 2 qq and
+  // 2 qq + 1; a work item (kx, row) reads its values and writes z directly.
+  auto put = [&](int sb, int kx, C a, C b) {
     if (kx == 0 || 2 * kx == Px) {
-      const C a = buf[sb + kx * np], b = side[2 * s + (kx == 0 ? 0 : 1)];
       C z;
       z.x = a.x; z.y = b.x;
       buf[sb + kx * np] = z;
     } else {
-      const C a = buf[sb + kx * np], b = buf[sb + (Px - kx) * np];
       C zk, zm;
       zk.x = a.x - b.y; zk.y = a.y + b.x;
       zm.x = a.x + b.y; zm.y = b.x - a.y;
       buf[sb + kx * np] = zk;
       buf[sb + (Px - kx) * np] = zm;
     }
+  };
+  const int tot = ngu * nrb * CC;
+#pragma unroll 8
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int cc = idx & (CC - 1), rr = (idx >> lcc) & (nrb - 1), g = idx >> (lcc + lnrb);
+    const int kx = g * CC + cc;
+    if (kx >= half) continue;
+    const int r = 2 * pair0 + rr;
+    const int qq = rr >> 1, h = rr & 1;
+    C ax, ay, z0, z1;
+    ax.x = ax.y = ay.x = ay.y = z0.x = z0.y = z1.x = z1.y = 0;
+    if (r < ny) {
+      ax = S[tiled(0, r, kx, ny, NG, lcc)];
+      ay = S[tiled(1, r, kx, ny, NG, lcc)];
+      if (h == 0) {
+        z0 = S[tiled(2, r, kx, ny, NG, lcc)];
+        if (r + 1 < ny) z1 = S[tiled(2, r + 1, kx, ny, NG, lcc)];
+      }
+    }
+    put(h * gs + qq, kx, ax, ay);
+    if (h == 0) put(2 * gs + qq, kx, z0, z1);
   }
   __syncthreads();
-  fft_il<C, V, true, false, true>(buf, lx, IlMap{lnp, 3, gs}, tws, true);
+  fft_il<C, V, true, false, true>(buf, lx, IlMap{lnp, 3, gs}, tws);
   const R scale = (R)1 / ((R)Px * (R)ch.Py * (R)ch.Pz);
   const long long Sl = (long long)ny * ch.hx;
   const bool percell = ch.t_off >= 0;
