@@ -168,6 +168,16 @@ void mmc_destroy(mmc_ctx *ctx);
 /* Applied field of one chain (chain < 0: all chains), tesla. */
 mmc_status mmc_set_field(mmc_ctx *ctx, int chain, const double B[3]);
 
+/* Temperature of one chain (chain < 0: all chains), kelvin: recomputes the
+ * temperature-dependent tables exactly as at create -- m_e(T), chi(T) (Eqs. 8-9),
+ * sigma (Eq. 13), the longitudinal coefficients of Eq. 7, K(T) ~ m_e^{l(l+1)/2}
+ * and the kT-unit coefficients of the sweep -- and leaves the state, the sweep
+ * counter and the cone angle alone.  T_cell (optional HOST, ncell values in
+ * natural order, one chain only) gives per-cell temperatures to a chain that
+ * has per-cell tables (MMC_ERR_UNSUPPORTED otherwise).  MMC_ERR_ARG: T <= 0 or
+ * a non-positive T_cell value. */
+mmc_status mmc_set_temperature(mmc_ctx *ctx, int chain, double T, const double *T_cell);
+
 /* Copy m of one chain in/out as float4 per cell in natural order.  src/dst are
  * HOST pointers when is_device == 0, DEVICE pointers otherwise; the caller's
  * buffer is no longer used when the call returns.  mmc_set_m rejects non-finite

@@ -82,6 +82,10 @@ struct ChainHost {
   std::vector<double> etab;             // per-cell energy table, 10 doubles per cell
   std::vector<float> init_len;          // per-cell initial length (natural order)
   std::vector<float> grain;             // natural order, or empty
+  // temperature-independent inputs kept for mmc_set_temperature
+  double e[3];                          // normalized easy axis
+  int l1, l2;                           // exponents of m_e in K1(T), K2(T)
+  std::vector<double> Ms0_cell, K1_cell, Tc_cell, eA_cell;   // copies of the per-cell inputs, or empty
 };
 
 // block tables of the 2D interleaved kernels for one block size E
@@ -298,6 +302,72 @@ mmc_status validate(const mmc_chain_desc &d, const mmc_options &o, int idx) {
   return MMC_OK;
 }
 
+// temperature-dependent tables of a chain (Eqs. 7-9, 13 and the m_e scaling
+// laws): thermodynamic tables, kT-unit coefficients of ChainDev and, for
+// per-cell chains, the per-cell energy table; T_cell (natural order) or the
+// scalar T
+void apply_temperature(ChainHost &H, ChainDev &D, const mmc_options &o, double Tscalar, const double *T_cell) {
+  EnergyCoef &E = H.ecoef;
+  const int l1 = H.l1, l2 = H.l2;
+  const double *e = H.e;
+  H.T = Tscalar;
+  if (!H.percell) {
+    const double kT = kB * Tscalar;
+    H.Tref = Tscalar;
+    const Thermo t = thermo(Tscalar, H.Tc, H.mu, H.V, H.Ms0, o.sigma_cap);
+    H.me = {t.me}; H.chi = {t.chi}; H.sigma = {t.sigma};
+    D.p2 = (float)(t.c2 / kT);
+    D.p4 = (float)(t.c4 / kT);
+    split_f(t.me2, D.me2h, D.me2l);
+    D.sigma = (float)t.sigma;
+    D.zee = (float)(H.V * H.Ms0 / kT);
+    const double K1T = H.K1 * std::pow(t.me, l1), K2T = H.K2 * std::pow(t.me, l2);
+    D.k1 = (float)(H.V * K1T / kT);
+    D.k2 = (float)(H.V * K2T / kT);
+    for (int a = 0; a < 3; ++a) (&D.wx)[a] = (float)(E.cex[a] / kT);
+    D.cdx = (float)(E.cdmi[0] / kT);
+    D.cdy = (float)(E.cdmi[1] / kT);
+    D.ex = (float)e[0]; D.ey = (float)e[1]; D.ez = (float)e[2];
+    E.c2 = t.c2; E.c4 = t.c4; E.me2 = t.me2; E.K1T = K1T; E.K2T = K2T;
+    const double len = t.me > 0 ? t.me : rms_len_eq7(Tscalar, H.Tc, H.mu, H.V, H.Ms0);
+    H.init_len.assign((size_t)H.ncell, (float)len);
+  } else {
+    double Tref = 0;
+    for (long long i = 0; i < H.ncell; ++i) Tref = std::max(Tref, T_cell ? T_cell[i] : Tscalar);
+    H.Tref = Tref;
+    const double kTr = kB * Tref;
+    for (int a = 0; a < 3; ++a) (&D.wx)[a] = (float)(E.cex[a] / kTr);
+    D.cdx = (float)(E.cdmi[0] / kTr);
+    D.cdy = (float)(E.cdmi[1] / kTr);
+    H.me.assign((size_t)H.ncell, 0); H.chi.assign((size_t)H.ncell, 0); H.sigma.assign((size_t)H.ncell, 0);
+    H.etab.assign((size_t)H.ncell * 10, 0.0);
+    H.init_len.assign((size_t)H.ncell, 0.f);
+    const double cap = o.sigma_cap, mu = H.mu, V = H.V, K2 = H.K2;
+    parallel_for(H.ncell, [&](long long i) {
+      const double T = T_cell ? T_cell[i] : Tscalar;
+      const double Tc = H.Tc_cell.empty() ? H.Tc : H.Tc_cell[(size_t)i];
+      const double Ms = H.Ms0_cell.empty() ? H.Ms0 : H.Ms0_cell[(size_t)i];
+      const double K1 = H.K1_cell.empty() ? H.K1 : H.K1_cell[(size_t)i];
+      const Thermo t = thermo(T, Tc, mu, V, Ms, cap);
+      H.me[i] = t.me; H.chi[i] = t.chi; H.sigma[i] = t.sigma;
+      double ee[3] = {e[0], e[1], e[2]};
+      if (!H.eA_cell.empty()) {
+        double n2 = 0;
+        for (int a = 0; a < 3; ++a) { ee[a] = H.eA_cell[(size_t)(3 * i + a)]; n2 += ee[a] * ee[a]; }
+        n2 = std::sqrt(n2);
+        if (!(n2 > 0)) { ee[0] = 0; ee[1] = 0; ee[2] = 1; n2 = 1; }
+        for (int a = 0; a < 3; ++a) ee[a] /= n2;
+        if (ee[2] < 0) for (int a = 0; a < 3; ++a) ee[a] = -ee[a];
+      }
+      double *et = &H.etab[10 * i];
+      et[0] = t.c2; et[1] = t.c4; et[2] = t.me2; et[3] = Ms;
+      et[4] = K1 * std::pow(t.me, l1); et[5] = K2 * std::pow(t.me, l2);
+      et[6] = ee[0]; et[7] = ee[1]; et[8] = ee[2]; et[9] = kB * T;
+      H.init_len[i] = (float)(t.me > 0 ? t.me : 0.3);
+    });
+  }
+}
+
 // tables of one chain (host); a batch in which any chain has per-cell inputs
 // gives every chain per-cell tables (force_percell), since one sweep launch
 // reads all chains of the batch the same way
@@ -353,61 +423,14 @@ void build_chain(ChainHost &H, ChainDev &D, const mmc_chain_desc &d, const mmc_o
   for (int a = 0; a < 3; ++a) { E.B[a] = d.B[a]; E.e[a] = e[a]; }
   E.Ms0 = mt.Ms0;
 
-  if (!H.percell) {
-    const double kT = kB * d.T;
-    H.Tref = d.T;
-    const Thermo t = thermo(d.T, mt.Tc, H.mu, H.V, mt.Ms0, o.sigma_cap);
-    H.me = {t.me}; H.chi = {t.chi}; H.sigma = {t.sigma};
-    D.p2 = (float)(t.c2 / kT);
-    D.p4 = (float)(t.c4 / kT);
-    split_f(t.me2, D.me2h, D.me2l);
-    D.sigma = (float)t.sigma;
-    D.zee = (float)(H.V * mt.Ms0 / kT);
-    const double K1T = mt.K1 * std::pow(t.me, l1), K2T = mt.K2 * std::pow(t.me, l2);
-    D.k1 = (float)(H.V * K1T / kT);
-    D.k2 = (float)(H.V * K2T / kT);
-    for (int a = 0; a < 3; ++a) (&D.wx)[a] = (float)(E.cex[a] / kT);
-    D.cdx = (float)(E.cdmi[0] / kT);
-    D.cdy = (float)(E.cdmi[1] / kT);
-    D.ex = (float)e[0]; D.ey = (float)e[1]; D.ez = (float)e[2];
-    E.c2 = t.c2; E.c4 = t.c4; E.me2 = t.me2; E.K1T = K1T; E.K2T = K2T;
-    const double len = t.me > 0 ? t.me : rms_len_eq7(d.T, mt.Tc, H.mu, H.V, mt.Ms0);
-    H.init_len.assign((size_t)H.ncell, (float)len);
-  } else {
-    double Tref = 0;
-    for (long long i = 0; i < H.ncell; ++i) Tref = std::max(Tref, d.T_cell ? d.T_cell[i] : d.T);
-    H.Tref = Tref;
-    const double kTr = kB * Tref;
-    for (int a = 0; a < 3; ++a) (&D.wx)[a] = (float)(E.cex[a] / kTr);
-    D.cdx = (float)(E.cdmi[0] / kTr);
-    D.cdy = (float)(E.cdmi[1] / kTr);
-    H.me.assign((size_t)H.ncell, 0); H.chi.assign((size_t)H.ncell, 0); H.sigma.assign((size_t)H.ncell, 0);
-    H.etab.assign((size_t)H.ncell * 10, 0.0);
-    H.init_len.assign((size_t)H.ncell, 0.f);
-    const double cap = o.sigma_cap, mu = H.mu, V = H.V, K2 = mt.K2;
-    parallel_for(H.ncell, [&](long long i) {
-      const double T = d.T_cell ? d.T_cell[i] : d.T;
-      const double Tc = mt.Tc_cell ? mt.Tc_cell[i] : mt.Tc;
-      const double Ms = mt.Ms0_cell ? mt.Ms0_cell[i] : mt.Ms0;
-      const double K1 = mt.K1_cell ? mt.K1_cell[i] : mt.K1;
-      const Thermo t = thermo(T, Tc, mu, V, Ms, cap);
-      H.me[i] = t.me; H.chi[i] = t.chi; H.sigma[i] = t.sigma;
-      double ee[3] = {e[0], e[1], e[2]};
-      if (mt.e_A_cell) {
-        double n2 = 0;
-        for (int a = 0; a < 3; ++a) { ee[a] = mt.e_A_cell[3 * i + a]; n2 += ee[a] * ee[a]; }
-        n2 = std::sqrt(n2);
-        if (!(n2 > 0)) { ee[0] = 0; ee[1] = 0; ee[2] = 1; n2 = 1; }
-        for (int a = 0; a < 3; ++a) ee[a] /= n2;
-        if (ee[2] < 0) for (int a = 0; a < 3; ++a) ee[a] = -ee[a];
-      }
-      double *et = &H.etab[10 * i];
-      et[0] = t.c2; et[1] = t.c4; et[2] = t.me2; et[3] = Ms;
-      et[4] = K1 * std::pow(t.me, l1); et[5] = K2 * std::pow(t.me, l2);
-      et[6] = ee[0]; et[7] = ee[1]; et[8] = ee[2]; et[9] = kB * T;
-      H.init_len[i] = (float)(t.me > 0 ? t.me : 0.3);
-    });
-  }
+  for (int a = 0; a < 3; ++a) H.e[a] = e[a];
+  H.l1 = l1;
+  H.l2 = l2;
+  if (mt.Ms0_cell) H.Ms0_cell.assign(mt.Ms0_cell, mt.Ms0_cell + H.ncell);
+  if (mt.K1_cell) H.K1_cell.assign(mt.K1_cell, mt.K1_cell + H.ncell);
+  if (mt.Tc_cell) H.Tc_cell.assign(mt.Tc_cell, mt.Tc_cell + H.ncell);
+  if (mt.e_A_cell) H.eA_cell.assign(mt.e_A_cell, mt.e_A_cell + 3 * H.ncell);
+  apply_temperature(H, D, o, d.T, d.T_cell);
   if (mt.grain) {
     H.grain.resize((size_t)H.ncell);
     for (long long i = 0; i < H.ncell; ++i) H.grain[i] = (float)mt.grain[i];
@@ -419,6 +442,25 @@ inline long long split_index(const ChainDev &D, int i, int row) {
   const int j = row % D.ny, k = row / D.ny;
   const int col = (i + j + k) & 1;
   return (long long)col * D.nrows * D.hx + (long long)row * D.hx + (i >> 1);
+}
+
+// per-cell tables of a chain in the split layout: 3 float4 arrays of 2 S entries
+// ({p2, p4, m_e^2, sigma}, {zee, k1, k2, T_ref / T}, {e_A}) and Ms0 per cell
+void fill_percell_tables(const ChainHost &H, const ChainDev &D, float4 *tab, float *ms) {
+  const long long S = H.slots;
+  for (int row = 0; row < D.nrows; ++row)
+    for (int i = 0; i < D.nx; ++i) {
+      const long long nat = i + (long long)D.nx * row;
+      const long long si = split_index(D, i, row);
+      const double *et = &H.etab[10 * nat];
+      const double kT = et[9];
+      const float bs = (float)(kB * H.Tref / kT);
+      tab[si] = make_float4((float)(et[0] / kT), (float)(et[1] / kT), (float)et[2], (float)H.sigma[(size_t)nat]);
+      tab[2 * S + si] =
+          make_float4((float)(H.V * et[3] / kT), (float)(H.V * et[4] / kT), (float)(H.V * et[5] / kT), bs);
+      tab[4 * S + si] = make_float4((float)et[6], (float)et[7], (float)et[8], 0.f);
+      ms[si] = (float)et[3];
+    }
 }
 
 mmc_status build_il_tables(mmc_ctx *c, IlTables &T, const std::vector<ChainDev> &table, int E, bool fp64) {
@@ -972,18 +1014,8 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
           const long long si = split_index(D, i, row);
           const float g = H.grain.empty() ? 0.f : H.grain[(size_t)nat];
           m[(size_t)(D.m_off + si)] = make_float4(H.init_len[(size_t)nat], 0.f, 0.f, g);
-          if (H.percell) {
-            const double *et = &H.etab[10 * nat];
-            const double kT = et[9];
-            const float bs = (float)(kB * H.Tref / kT);
-            tab[(size_t)(D.t_off + si)] = make_float4((float)(et[0] / kT), (float)(et[1] / kT), (float)et[2],
-                                                      (float)H.sigma[(size_t)nat]);
-            tab[(size_t)(D.t_off + 2 * S + si)] =
-                make_float4((float)(H.V * et[3] / kT), (float)(H.V * et[4] / kT), (float)(H.V * et[5] / kT), bs);
-            tab[(size_t)(D.t_off + 4 * S + si)] = make_float4((float)et[6], (float)et[7], (float)et[8], 0.f);
-            ms[(size_t)(D.ms_off + si)] = (float)et[3];
-          }
         }
+      if (H.percell) fill_percell_tables(H, D, tab.data() + D.t_off, ms.data() + D.ms_off);
     }
     MMC_TRY_OR(upload(c, &c->d_m, m));
     if (toff) MMC_TRY_OR(upload(c, &c->d_tab, tab));
@@ -1175,6 +1207,39 @@ mmc_status mmc_set_field(mmc_ctx *c, int chain, const double B[3]) {
     c->ch[i].Bz = (float)B[2];
     for (int a = 0; a < 3; ++a) c->hc[i].ecoef.B[a] = B[a];
     CUDA_TRY(cudaMemcpyAsync(c->d_ch + i, &c->ch[i], sizeof(ChainDev), cudaMemcpyHostToDevice, c->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->heff_stale = true;
+  return MMC_OK;
+}
+
+mmc_status mmc_set_temperature(mmc_ctx *c, int chain, double T, const double *T_cell) {
+  if (!c) return fail(MMC_ERR_ARG, "null context");
+  if (chain >= c->nchains) return fail(MMC_ERR_ARG, "chain index out of range");
+  if (!(T > 0)) return fail(MMC_ERR_ARG, "T must be > 0");
+  if (T_cell && chain < 0) return fail(MMC_ERR_ARG, "per-cell temperatures need one chain");
+  if (T_cell) {
+    const ChainHost &H = c->hc[chain];
+    if (!H.percell) return fail(MMC_ERR_UNSUPPORTED, "per-cell temperature on a chain created without per-cell tables");
+    for (long long i = 0; i < H.ncell; ++i)
+      if (!(T_cell[i] > 0)) return fail(MMC_ERR_ARG, "T_cell must be > 0");
+  }
+  for (int i = 0; i < c->nchains; ++i) {
+    if (chain >= 0 && i != chain) continue;
+    ChainHost &H = c->hc[i];
+    ChainDev &D = c->ch[i];
+    apply_temperature(H, D, c->opt, T, T_cell);
+    if (H.percell) {
+      std::vector<float4> tab((size_t)(6 * H.slots));
+      std::vector<float> ms((size_t)(2 * H.slots));
+      fill_percell_tables(H, D, tab.data(), ms.data());
+      CUDA_TRY(cudaMemcpyAsync(c->d_tab + D.t_off, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                               c->stream));
+      CUDA_TRY(cudaMemcpyAsync(c->d_ms + D.ms_off, ms.data(), ms.size() * sizeof(float), cudaMemcpyHostToDevice,
+                               c->stream));
+      CUDA_TRY(cudaStreamSynchronize(c->stream));   // the host vectors go out of scope
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->d_ch + i, &D, sizeof(ChainDev), cudaMemcpyHostToDevice, c->stream));
   }
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->heff_stale = true;

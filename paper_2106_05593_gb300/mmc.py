@@ -118,6 +118,16 @@ class MMC:
         b = np.asarray(B, dtype=np.float64).reshape(3)
         check(load().mmc_set_field(self._ctx, int(chain), _dptr(b)), "mmc_set_field")
 
+    def set_temperature(self, T, chain=-1, T_cell=None):
+        """Temperature of one chain (chain < 0: all), kelvin; T_cell: optional
+        per-cell temperatures (natural order) of one chain with per-cell tables."""
+        tc = None
+        if T_cell is not None:
+            tc = np.ascontiguousarray(T_cell, dtype=np.float64).reshape(-1)
+            assert tc.size == self.ncell[chain]
+        check(load().mmc_set_temperature(self._ctx, int(chain), float(T), _dptr(tc) if tc is not None else None),
+              "mmc_set_temperature")
+
     def set_m(self, m, chain=0):
         """m: numpy float32 (ncell, 4) on the host, or a CUDA torch tensor."""
         if hasattr(m, "is_cuda") and m.is_cuda:

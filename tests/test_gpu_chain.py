@@ -113,3 +113,42 @@ def test_equilibrium_permalloy32_matches_oracle(P):
         print("observable", q, gval[:, q].mean(), oval[:, q].mean(), "se", se, "gpu", gval[:, q], "oracle", oval[:, q])
         assert diff < 3 * se + 1e-12, (q, gval[:, q].mean(), oval[:, q].mean(), se)
     assert abs(gval[:, 0].mean() - me) < 2e-3      # <|m|> tracks m_e below Tc (Eq. 7)
+
+
+def test_set_temperature_equals_a_fresh_context(P):
+    """mmc_set_temperature recomputes every temperature-dependent table as at
+    create: after it, the tables and one pass (decisions and state) equal
+    those of a context created at the new temperature, bit for bit; the
+    per-cell form on a granular chain likewise."""
+    import workloads as W
+    spec = W.chiral(48, 300.0)
+    hot = dict(spec, T=590.0)
+    a = P.MMC(spec, demag=1, fft_variant=1)       # same FFT variant: bitwise-comparable fields
+    b = P.MMC(hot, demag=1, fft_variant=1)
+    a.set_temperature(590.0)
+    ta, tb = a.tables(0), b.tables(0)
+    for k in ta:
+        assert np.array_equal(ta[k], tb[k]), k
+    m4 = W.random_state(48 * 48, 4, 0.3, 0.6)
+    for g in (a, b):
+        g.set_m(m4)
+    da, aa = a.pass_debug(0, 1, 3, 9, 25.0)
+    db, ab = b.pass_debug(0, 1, 3, 9, 25.0)
+    assert np.array_equal(da, db) and np.array_equal(aa, ab)
+    assert np.array_equal(a.get_m(), b.get_m())
+    # per-cell temperatures on a granular chain
+    gs = W.granular_chain(40, 2, demag=False)
+    Tnew = np.asarray(gs["T"]) + 50.0
+    c = P.MMC(gs)
+    d = P.MMC(dict(gs, T=Tnew))
+    c.set_temperature(float(Tnew.max()), 0, Tnew)
+    m4 = W.random_state(40 * 40, 5, 0.4, 0.8)
+    for g in (c, d):
+        g.set_m(m4)
+    dc, ac = c.pass_debug(0, 0, 2, 5, 30.0)
+    dd, ad = d.pass_debug(0, 0, 2, 5, 30.0)
+    assert np.array_equal(dc, dd) and np.array_equal(ac, ad)
+    with pytest.raises(Exception):
+        a.set_temperature(300.0, 0, np.full(48 * 48, 300.0))    # uniform chain: no per-cell tables
+    with pytest.raises(Exception):
+        a.set_temperature(-1.0)
