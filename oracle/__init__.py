@@ -117,6 +117,7 @@ def lib():
         L.orc_pass.restype = C.c_int64
         L.orc_pass.argtypes = [C.c_void_p, dp, dp, C.c_int, C.c_uint32, C.c_uint32, C.c_uint64,
                                C.c_double, C.POINTER(C.c_int8), dp, dp]
+        L.orc_angle_hist.argtypes = [C.c_void_p, dp, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_int64), dp]
         L.orc_sdesc.restype = C.c_int
         L.orc_sdesc.argtypes = [C.c_void_p, dp, C.c_int, C.c_double, C.POINTER(C.c_int), dp]
         L.orc_serial_sweep.restype = C.c_int64
@@ -343,6 +344,16 @@ class Oracle:
         nacc = lib().orc_serial_sweep(self._ctx, _dp(mm), _dp(Hh), int(sweep), int(chain),
                                       int(seed), float(theta_deg))
         return mm.reshape(self.n, 3), Hh.reshape(self.n, 3), nacc
+
+    def angle_hist(self, m, bins=100, lo=0.0, hi=np.pi):
+        """Histogram of the polar angle to the mean direction (Sec. II, Fig. 1d-f):
+        (counts of bins + 1 entries, the last for angles outside [lo, hi), mean direction)."""
+        mm = self._m(m)
+        h = np.zeros(bins + 1, dtype=np.int64)
+        d = np.zeros(3)
+        lib().orc_angle_hist(self._ctx, _dp(mm), int(bins), float(lo), float(hi),
+                             h.ctypes.data_as(C.POINTER(C.c_int64)), _dp(d))
+        return h, d
 
     def sdesc(self, m, maxit=20000, tol=1e-5):
         """Zero-temperature steepest descent (Sec. III SDesc) from m; returns

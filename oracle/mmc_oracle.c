@@ -1173,3 +1173,31 @@ int orc_sdesc(orc_ctx *c, double *m, int maxit, double tol, int *iters, double *
     free(u); free(up); free(G); free(g); free(gp); free(mm);
     return done ? 0 : 1;
 }
+
+
+/* Sec. II, transverse distribution check (Fig. 1d-f): the polar angle of every
+ * cell to the configuration's mean direction, histogrammed in bins equal
+ * bins on [lo, hi); angles outside go to the last entry hist[bins].  FP64. */
+void orc_angle_hist(const orc_ctx *c, const double *m, int bins, double lo, double hi, int64_t *hist,
+                    double mean_dir[3])
+{
+    double s[3] = {0, 0, 0};
+    for (int q = 0; q < c->n; ++q)
+        for (int a = 0; a < 3; ++a) s[a] += m[3 * q + a];
+    double l = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    double n[3] = {0, 0, 1};
+    if (l > 0) for (int a = 0; a < 3; ++a) n[a] = s[a] / l;
+    if (mean_dir) for (int a = 0; a < 3; ++a) mean_dir[a] = n[a];
+    for (int b = 0; b <= bins; ++b) hist[b] = 0;
+    for (int q = 0; q < c->n; ++q) {
+        const double *v = m + 3 * q;
+        double lv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        double ct = lv > 0 ? (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / lv : 1.0;
+        if (ct > 1.0) ct = 1.0;
+        if (ct < -1.0) ct = -1.0;
+        double th = acos(ct);
+        double f = (th - lo) / (hi - lo) * bins;
+        int b = (f >= 0.0 && f < (double)bins) ? (int)f : bins;
+        hist[b] += 1;
+    }
+}

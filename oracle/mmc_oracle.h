@@ -135,6 +135,12 @@ int64_t orc_pass(orc_ctx *c, double *m, const double *H, int color, uint32_t swe
 int64_t orc_serial_sweep(orc_ctx *c, double *m, double *H, uint32_t sweep,
                          uint32_t chain, uint64_t seed, double theta_deg);
 
+/* Sec. II transverse check (Fig. 1d-f): histogram of the polar angle of every
+ * cell to the mean direction of m, `bins` equal bins on [lo, hi), outside
+ * angles in hist[bins]; mean_dir (optional) receives the mean direction. */
+void orc_angle_hist(const orc_ctx *c, const double *m, int bins, double lo, double hi, int64_t *hist,
+                    double mean_dir[3]);
+
 /* Sec. III comparison method (SDesc): steepest descent over directions with
  * |m_i| = m_e(T_i), Barzilai-Borwein steps, until the largest normalized
  * torque is below tol (or maxit steps).  m in/out (3 n).  Returns 0 when
