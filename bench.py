@@ -164,7 +164,7 @@ def recorded_traffic(kernel, workload_name, src_hash):
     return None
 
 
-# algorithmic bytes per cell per launch (documented in the design doc)
+# algorithmic bytes per cell per launch: what each kernel must read and write
 def algorithmic_bytes(kind, demag, percell):
     if kind == "sweep_pass":     # per pass: half the cells updated; 48 B/cell-update (+48 per-cell table)
         return 0.5 * (48.0 if demag else 32.0) + (0.5 * 48.0 if percell else 0.0)

@@ -49,7 +49,7 @@ typedef enum {
     MMC_ERR_CUDA = -2,        /* a CUDA runtime / cuFFT call failed */
     MMC_ERR_TIMEOUT = -3,     /* a bounded device-side wait gave up */
     MMC_ERR_NONFINITE = -4,   /* non-finite values in input or state */
-    MMC_ERR_UNSUPPORTED = -5, /* a combination this build does not implement */
+    MMC_ERR_UNSUPPORTED = -5, /* a combination the library does not implement */
     MMC_ERR_NOMEM = -6        /* device or host allocation failed */
 } mmc_status;
 
@@ -98,6 +98,11 @@ typedef struct {
     int hist_bins;            /* |m| histogram bins on [0, hist_max)              [200] */
     double hist_max;          /*                                                    [1] */
     int use_graphs;           /* 1: capture 100-sweep blocks in CUDA graphs         [1] */
+    int stream_groups;        /* chain groups whose iterations run concurrently on
+                                 their own streams, so that one group's kernel tails
+                                 overlap the other's work; 0 auto (2 when the batch
+                                 has >= 2 chains), 1 one stream, G > 1 G groups.
+                                 Results are identical for any value.            [0] */
     int demag_self;           /* serial form (mmc_sweep_serial) only: add the demag
                                  self term (mu0 V / 2) Ms0^2 dm.N(0).dm to Eq. 14,
                                  making its demag energy change exact           [0] */
@@ -247,6 +252,16 @@ mmc_status mmc_pass_debug(mmc_ctx *ctx, int chain, int color, uint32_t sweep, ui
 /* Observables of one chain (see mmc_obs); reset != 0 clears the snapshot
  * accumulators after reading them. */
 mmc_status mmc_observables(mmc_ctx *ctx, int chain, mmc_obs *out, int reset);
+
+/* Angular-deviation histogram of one chain's current state (Sec. II, Fig. 1d-f):
+ * the polar angle of every cell to the chain's mean direction, counted in `bins`
+ * equal bins on [theta_lo, theta_hi) (radians, 1 <= bins <= 1024); angles outside
+ * go to hist[bins].  The paper bins each configuration between its own minimum
+ * and maximum angle and averages over ensembles; averaging needs common bins, so
+ * the range is the caller's.  hist: HOST, bins + 1 counters; mean_dir (optional
+ * HOST) receives the unit mean direction.  Angles in FP64 of the FP32 state. */
+mmc_status mmc_angle_hist(mmc_ctx *ctx, int chain, int bins, double theta_lo, double theta_hi, int64_t *hist,
+                          double mean_dir[3]);
 
 /* Energy terms of one chain, in J: out[7] = {total, exchange, dmi, anisotropy,
  * zeeman, longitudinal (Eq. 7), demag (E_d = -(mu0 V/2) sum Ms0 m.H_d)}.

@@ -10,6 +10,7 @@
 
 #include "../../include/mmc.h"
 #include "mmc_internal.h"
+#include "angles.h"
 
 using namespace mmc;
 
@@ -161,6 +162,16 @@ struct mmc_ctx {
   double *d_obs_out = nullptr;
   DemagPlan batch_plan;
   std::vector<CufftGroup> cf;           // cuFFT comparison path (demag_cufft)
+  // chain groups whose iterations run concurrently on their own streams (the
+  // tail of one group's kernels overlaps the other's); empty: one stream
+  struct ChainGroup {
+    int c0 = 0, c1 = 0;                 // chains [c0, c1)
+    DemagPlan plan;                     // demag over the group (batch spectrum buffer)
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+  std::vector<ChainGroup> groups;
+  cudaEvent_t ev_fork = nullptr;
   int tuned_variant = 0;                // FFT variant picked at create (0: not tuned)
   double tune_ms[3] = {0.0, 0.0, 0.0};  // per-update time of the variants when tuned
   std::vector<DemagPlan> single[2];     // per chain and precision (0 FP32, 1 FP64), built lazily
@@ -184,6 +195,7 @@ struct mmc_ctx {
   bool heff_stale = true;               // state or field changed since the last demag update
   bool obs_fresh = false;               // current-state observables of all chains are up to date
   int *d_flag = nullptr;                // device scratch int (input checks)
+  unsigned long long *d_ang = nullptr;  // angular histogram counters (kHistMax + 1)
   std::vector<GraphEntry> graphs;
   std::vector<void *> allocs;
 
@@ -463,7 +475,10 @@ void fill_percell_tables(const ChainHost &H, const ChainDev &D, float4 *tab, flo
     }
 }
 
-mmc_status build_il_tables(mmc_ctx *c, IlTables &T, const std::vector<ChainDev> &table, int E, bool fp64) {
+// block tables of the 2D kernels: block -> chain id (ids[t] for the t-th chain of
+// `table`) and, per chain id, its first block
+mmc_status build_il_tables(mmc_ctx *c, IlTables &T, const std::vector<ChainDev> &table, const std::vector<int> &ids,
+                           int nid, int E, bool fp64) {
   const size_t csz = fp64 ? 16 : 8;
   int maxPx = 1, maxPy = 1;
   for (const ChainDev &D : table) {
@@ -472,20 +487,18 @@ mmc_status build_il_tables(mmc_ctx *c, IlTables &T, const std::vector<ChainDev> 
     maxPy = std::max(maxPy, D.Py);
   }
   std::vector<int> rc, colc;
-  std::vector<long long> rf, colf;
+  std::vector<long long> rf((size_t)nid + 1, 0), colf((size_t)nid + 1, 0);
   for (size_t t = 0; t < table.size(); ++t) {
     const ChainDev &D = table[t];
     const int np = E / (3 * D.Px);
     const int nb = ((D.nrows + 1) / 2 + np - 1) / np;
-    rf.push_back((long long)rc.size());
-    for (int b = 0; b < nb; ++b) rc.push_back((int)t);
+    rf[(size_t)ids[t]] = (long long)rc.size();
+    for (int b = 0; b < nb; ++b) rc.push_back(ids[t]);
     const int CC = E / (3 * D.Py);
     const int nc = D.Sx / CC;
-    colf.push_back((long long)colc.size());
-    for (int b = 0; b < nc; ++b) colc.push_back((int)t);
+    colf[(size_t)ids[t]] = (long long)colc.size();
+    for (int b = 0; b < nc; ++b) colc.push_back(ids[t]);
   }
-  rf.push_back((long long)rc.size());
-  colf.push_back((long long)colc.size());
   MMC_TRY(upload(c, &T.rows_chain, rc));
   MMC_TRY(upload(c, &T.rows_first, rf));
   MMC_TRY(upload(c, &T.cols_chain, colc));
@@ -500,9 +513,16 @@ mmc_status build_il_tables(mmc_ctx *c, IlTables &T, const std::vector<ChainDev> 
   return MMC_OK;
 }
 
+// Plan of the demag kernels over `chains`.  single: the plan carries its own
+// chain table and spectrum buffer (chain ids are positions in `chains`);
+// otherwise it indexes the context's chain table by global chain id and uses the
+// spectrum buffer shared_spec when given (chain offsets are the batch's).
 mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &chains, bool fp64,
-                            bool single) {
+                            bool single, void *shared_spec = nullptr) {
   const size_t csz = fp64 ? 16 : 8;
+  std::vector<int> ids(chains.size());
+  for (size_t t = 0; t < chains.size(); ++t) ids[t] = single ? (int)t : chains[t];
+  const int nid = single ? (int)chains.size() : c->nchains;
   std::vector<ChainDev> table;
   long long spec_elems = 0;
   int maxPx = 1, maxPyPz = 1;
@@ -529,7 +549,7 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
   for (const ChainDev &D : table)
     if (D.Pz != 1 || 3 * D.Px > E || 3 * D.Py > E) il = false;
   std::vector<int> rc, colc;
-  std::vector<long long> rf, colf;
+  std::vector<long long> rf((size_t)nid + 1, 0), colf((size_t)nid + 1, 0);
   size_t rsmem = 0, csmem = 0;
   int T = 384, Tc = 384, cc = 1;
   if (il) {
@@ -537,12 +557,12 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
       const ChainDev &D = table[t];
       const int np = E / (3 * D.Px);
       const int nb = ((D.nrows + 1) / 2 + np - 1) / np;
-      rf.push_back((long long)rc.size());
-      for (int b = 0; b < nb; ++b) rc.push_back((int)t);
+      rf[(size_t)ids[t]] = (long long)rc.size();
+      for (int b = 0; b < nb; ++b) rc.push_back(ids[t]);
       const int CC = E / (3 * D.Py);
       const int nc = D.Sx / CC;
-      colf.push_back((long long)colc.size());
-      for (int b = 0; b < nc; ++b) colc.push_back((int)t);
+      colf[(size_t)ids[t]] = (long long)colc.size();
+      for (int b = 0; b < nc; ++b) colc.push_back(ids[t]);
     }
     // data block (padded capacity), then the block's twiddle table (Px entries for
     // the row kernels, Py for the column kernel)
@@ -561,8 +581,8 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
       const int np = std::max(1, std::min(8, T / (3 * G)));
       const int pairs = (D.nrows + 1) / 2;
       const int nb = (pairs + np - 1) / np;
-      rf.push_back((long long)rc.size());
-      for (int b = 0; b < nb; ++b) rc.push_back((int)t);
+      rf[(size_t)ids[t]] = (long long)rc.size();
+      for (int b = 0; b < nb; ++b) rc.push_back(ids[t]);
       rsmem = std::max(rsmem, (size_t)3 * np * D.Px * csz);
     }
     cc = 8;
@@ -574,15 +594,13 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
       const ChainDev &D = table[t];
       Gy = std::max(Gy, std::max(D.Py / 8, std::max(D.Pz / 8, 1)));
       const int nb = (D.Px / 2 + 1 + cc - 1) / cc;
-      colf.push_back((long long)colc.size());
-      for (int b = 0; b < nb; ++b) colc.push_back((int)t);
+      colf[(size_t)ids[t]] = (long long)colc.size();
+      for (int b = 0; b < nb; ++b) colc.push_back(ids[t]);
     }
     Tc = std::min(512, std::max(128, 3 * cc * Gy));
     Tc = (Tc + 31) / 32 * 32;
     if (Tc < Gy) Tc = Gy;
   }
-  rf.push_back((long long)rc.size());
-  colf.push_back((long long)colc.size());
   P.il2d = il;
   MMC_TRY(upload(c, &P.rows_chain, rc));
   MMC_TRY(upload(c, &P.rows_first, rf));
@@ -596,15 +614,19 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
   P.cols_cc = cc;
   P.cols_smem = csmem;
   P.fp64 = fp64;
-  if (il && !fp64) MMC_TRY(build_il_tables(c, P.small, table, il_elements_small(), false));
+  if (il && !fp64) MMC_TRY(build_il_tables(c, P.small, table, ids, nid, il_elements_small(), false));
   {
     int v = c->opt.fft_variant >= 1 && c->opt.fft_variant <= 3 ? c->opt.fft_variant
             : (c->tuned_variant ? c->tuned_variant : 1);
     if (v == 3 && !P.small.ok) v = 1;
     P.fft_variant = v;
   }
-  MMC_TRY(dalloc(c, &P.spec, (size_t)spec_elems * csz));
-  CUDA_TRY(cudaMemset(P.spec, 0, (size_t)spec_elems * csz));   // padding columns stay defined
+  if (shared_spec) {
+    P.spec = shared_spec;
+  } else {
+    MMC_TRY(dalloc(c, &P.spec, (size_t)spec_elems * csz));
+    CUDA_TRY(cudaMemset(P.spec, 0, (size_t)spec_elems * csz));   // padding columns stay defined
+  }
   P.ready = true;
   return MMC_OK;
 }
@@ -753,6 +775,31 @@ void timed(mmc_ctx *c, PhaseTimer *pt, int kind, F fn) {
 void issue_block(mmc_ctx *c, int k, unsigned key0, unsigned key1, int sample_every, uint64_t start,
                  PhaseTimer *pt = nullptr) {
   Launch L = c->L();
+  if (!c->groups.empty() && !pt && sample_every == 0) {
+    // fork: every group runs its k iterations on its own stream (the chains of
+    // different groups never interact), join before the window step
+    cudaEventRecord(c->ev_fork, c->stream);
+    for (auto &g : c->groups) {
+      cudaStreamWaitEvent(g.stream, c->ev_fork, 0);
+      Launch Lg{g.stream, &c->launches};
+      const int b0 = (int)c->sw_first[(size_t)g.c0], nb = (int)(c->sw_first[(size_t)g.c1] - b0);
+      for (int off = 0; off < k; ++off) {
+        for (int color = 0; color < 2; ++color) {
+          if (c->any_demag && (color == 0 || c->opt.demag_per_pass))
+            launch_demag(Lg, make_demag_launch(c, g.plan, c->d_heff, nullptr, -1), g.plan.fp64);
+          SweepLaunch P = sweep_launch(c, color, (unsigned)off, key0, key1);
+          P.blk_base = b0;
+          P.nblocks = nb;
+          launch_sweep_pass(Lg, P);
+        }
+      }
+      cudaEventRecord(g.done, g.stream);
+      cudaStreamWaitEvent(c->stream, g.done, 0);
+    }
+    const int adapt_now = ((start + k) % 100 == 0) ? 1 : 0;
+    launch_advance(L, c->d_st, c->nchains, (unsigned)k, c->d_sweep_base, adapt_now, c->opt.adapt, 1.f, 180.f);
+    return;
+  }
   for (int off = 0; off < k; ++off) {
     if (c->any_demag) issue_demag(c, pt);
     timed(c, pt, 3, [&] { launch_sweep_pass(L, sweep_launch(c, 0, (unsigned)off, key0, key1)); });
@@ -887,6 +934,7 @@ mmc_status mmc_default_options(mmc_options *o) {
   o->hist_bins = 200;
   o->hist_max = 1.0;
   o->use_graphs = 1;
+  o->stream_groups = 0;
   o->demag_self = 0;
   o->fft_variant = 0;
   return MMC_OK;
@@ -897,6 +945,11 @@ void mmc_destroy(mmc_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (auto &g : c->cf) destroy_cufft_plans(g);
+  for (auto &g : c->groups) {
+    if (g.done) cudaEventDestroy(g.done);
+    if (g.stream) cudaStreamDestroy(g.stream);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   for (void *p : c->allocs) cudaFree(p);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -1140,6 +1193,37 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     cudaEventDestroy(e1);
     c->batch_plan.fft_variant = pick;
     c->tuned_variant = pick;
+  }
+  if (o.stream_groups != 1 && nchains >= 2 && !o.demag_cufft) {
+    // two groups of contiguous chains with about equal cell counts
+    const int G = o.stream_groups > 1 ? std::min(o.stream_groups, nchains) : 2;
+    long long total = 0;
+    for (int i = 0; i < nchains; ++i) total += c->hc[i].ncell;
+    int start = 0;
+    long long done = 0;
+    for (int gi = 0; gi < G; ++gi) {
+      int end = start + 1;
+      const long long target = total * (gi + 1) / G;
+      long long acc = done + c->hc[start].ncell;
+      while (end < nchains - (G - 1 - gi) && acc + c->hc[end].ncell / 2 <= target) acc += c->hc[end++].ncell;
+      if (gi == G - 1) { end = nchains; acc = total; }
+      mmc_ctx::ChainGroup g;
+      g.c0 = start;
+      g.c1 = end;
+      c->groups.push_back(g);
+      start = end;
+      done = acc;
+    }
+    CUDA_TRY_OR(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    for (auto &g : c->groups) {
+      CUDA_TRY_OR(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
+      CUDA_TRY_OR(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+      if (o.demag) {
+        std::vector<int> ids;
+        for (int i = g.c0; i < g.c1; ++i) ids.push_back(i);
+        MMC_TRY_OR(build_demag_plan(c, g.plan, ids, o.demag_fp64 != 0, false, c->batch_plan.spec));
+      }
+    }
   }
   if (o.demag && o.demag_cufft) {
     // one batched cuFFT plan pair per padded size
@@ -1445,6 +1529,41 @@ static mmc_status demag64_chain(mmc_ctx *c, int chain) {
   Launch L = c->L();
   launch_demag(L, make_demag_launch(c, *P, nullptr, c->d_Hd, 0), true);
   return check_launch();
+}
+
+mmc_status mmc_angle_hist(mmc_ctx *c, int chain, int bins, double theta_lo, double theta_hi, int64_t *hist,
+                          double mean_dir[3]) {
+  MMC_TRY(check_chain(c, chain));
+  if (!hist) return fail(MMC_ERR_ARG, "null histogram");
+  if (bins < 1 || bins > kHistMax) return fail(MMC_ERR_ARG, "bins must be in [1, 1024]");
+  if (!(theta_hi > theta_lo)) return fail(MMC_ERR_ARG, "theta_hi must exceed theta_lo");
+  Launch L = c->L();
+  // the mean direction from the current-state reduction (shared with mmc_observables)
+  if (!c->obs_fresh) {
+    const int nb = c->opt.hist_bins + 1;
+    CUDA_TRY(cudaMemsetAsync(c->d_hist_cur, 0, (size_t)c->nchains * nb * sizeof(unsigned long long), c->stream));
+    launch_obs(L, obs_launch(c, 0));
+    MMC_TRY(check_launch());
+    c->obs_fresh = true;
+  }
+  double o[8];
+  CUDA_TRY(cudaMemcpyAsync(o, c->d_obs_out + 8 * chain, sizeof(o), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  double n[3] = {o[0], o[1], o[2]};
+  const double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  if (l > 0) for (int a = 0; a < 3; ++a) n[a] /= l;
+  else { n[0] = 0; n[1] = 0; n[2] = 1; }
+  if (mean_dir) for (int a = 0; a < 3; ++a) mean_dir[a] = n[a];
+  if (!c->d_ang) MMC_TRY(dalloc_t(c, &c->d_ang, (size_t)kHistMax + 1));
+  unsigned long long *d_h = c->d_ang;
+  CUDA_TRY(cudaMemsetAsync(d_h, 0, ((size_t)bins + 1) * sizeof(unsigned long long), c->stream));
+  launch_angle_hist(L, c->d_ch, chain, c->hc[chain].slots, c->d_m, n, theta_lo, theta_hi, bins, d_h);
+  MMC_TRY(check_launch());
+  std::vector<unsigned long long> h((size_t)bins + 1);
+  CUDA_TRY(cudaMemcpyAsync(h.data(), d_h, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  for (int b = 0; b <= bins; ++b) hist[b] = (int64_t)h[(size_t)b];
+  return MMC_OK;
 }
 
 mmc_status mmc_demag_field(mmc_ctx *c, int chain, double *H) {

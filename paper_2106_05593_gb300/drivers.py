@@ -83,3 +83,19 @@ def crossing_probability(trace):
     before each sample (App. B, Fig. 12b)."""
     crossed = np.maximum.accumulate(np.asarray(trace) > 0.0, axis=0)
     return crossed.mean(axis=1)
+
+
+def angular_histogram(engine, chain, nsnap, every, seed, bins=100, lo=0.0, hi=np.pi):
+    """The transverse check of Sec. II (Fig. 1d-f): after every `every`
+    iterations the polar angle of each cell to the configuration's mean
+    direction is histogrammed; returns the bin centres and the histogram
+    averaged over nsnap configurations, normalized to unit area."""
+    acc = np.zeros(bins)
+    for _ in range(nsnap):
+        engine.sweep(every, seed)
+        h, _ = engine.angle_hist(chain, bins, lo, hi)
+        acc += h[:bins]
+    width = (hi - lo) / bins
+    centres = lo + (np.arange(bins) + 0.5) * width
+    total = acc.sum()
+    return centres, (acc / (total * width) if total > 0 else acc)

@@ -207,6 +207,15 @@ class MMC:
         check(load().mmc_demag_field(self._ctx, int(chain), _dptr(H)), "mmc_demag_field")
         return H.reshape(-1, 3)
 
+    def angle_hist(self, chain=0, bins=100, lo=0.0, hi=np.pi):
+        """Angular-deviation histogram of the current state (Sec. II, Fig. 1d-f):
+        (counts, bins + 1 entries with the out-of-range angles last; mean direction)."""
+        h = np.zeros(bins + 1, dtype=np.int64)
+        d = np.zeros(3)
+        check(load().mmc_angle_hist(self._ctx, int(chain), int(bins), float(lo), float(hi),
+                                    h.ctypes.data_as(C.POINTER(C.c_int64)), _dptr(d)), "mmc_angle_hist")
+        return h, d
+
     def tables(self, chain=0):
         n = self.ncell[chain]
         me, chi, sg = np.zeros(n), np.zeros(n), np.zeros(n)

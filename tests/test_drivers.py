@@ -102,3 +102,29 @@ def test_switching_trace_sequences_calls():
     assert list(its) == [10, 20, 25]
     assert e.calls == [("serial", 10), ("serial", 10), ("serial", 5)]
     assert np.allclose(tr[:, 0], [0.0, 1.0, 1.5]) and np.allclose(tr[:, 1], [1.0, 3.0, 4.0])
+
+
+class _FakeAngles:
+    nchains = 1
+
+    def __init__(self):
+        self.calls = 0
+
+    def sweep(self, n, seed):
+        self.calls += 1
+
+    def angle_hist(self, chain, bins, lo, hi):
+        h = np.zeros(bins + 1, dtype=np.int64)
+        h[0] = 3
+        h[bins - 1] = 1
+        h[bins] = 5                      # out of range: not part of the density
+        return h, np.array([0.0, 0.0, 1.0])
+
+
+def test_angular_histogram_averages_to_a_density():
+    from paper_2106_05593_gb300.drivers import angular_histogram
+    e = _FakeAngles()
+    c, dens = angular_histogram(e, 0, 4, 10, 1, bins=10, lo=0.0, hi=1.0)
+    assert e.calls == 4
+    assert np.allclose(c, (np.arange(10) + 0.5) / 10)
+    assert np.isclose(dens.sum() * 0.1, 1.0) and np.isclose(dens[0], 0.75 / 0.1)

@@ -216,3 +216,19 @@ def test_full_iterations_match_oracle(P, per_pass):
     print("full iterations per_pass=%d: max |dm| over agreeing cells %.2e, differing cells %d"
           % (per_pass, d[d <= 1e-5].max(), differ))
     assert differ <= 2          # a flipped decision inside the FP32 bound changes a cell and its neighbours later
+
+
+@pytest.mark.parametrize("mesh,bins,lo,hi", [((48, 40, 1), 100, 0.0, np.pi), ((12, 10, 6), 37, 0.1, 1.2)])
+def test_angle_hist_matches_oracle(P, mesh, bins, lo, hi):
+    """Angular-deviation histogram (Sec. II, Fig. 1d-f) of one chain of a batch
+    equals the oracle's on the same state, count for count."""
+    spec = W._base(mesh, (3e-9,) * 3)
+    n = int(np.prod(mesh))
+    m4 = W.smooth_state(mesh, 9, 0.8, tilt=0.9)
+    g = P.MMC([W.permalloy32(8), spec])
+    g.set_m(m4, 1)
+    h, d = g.angle_hist(1, bins, lo, hi)
+    ho, do = O.Oracle(spec).angle_hist(m4[:, :3].astype(np.float64), bins, lo, hi)
+    assert np.allclose(d, do, rtol=0, atol=1e-14)
+    assert h.sum() == n
+    assert np.array_equal(h, ho)
