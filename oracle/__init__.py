@@ -57,6 +57,7 @@ class _Problem(C.Structure):
         ("K2", C.POINTER(C.c_double)), ("eA", C.POINTER(C.c_double)),
         ("Tc", C.POINTER(C.c_double)), ("T", C.POINTER(C.c_double)),
         ("grain", C.POINTER(C.c_int)), ("cell_base", C.c_uint32),
+        ("demag_images", C.c_int),
     ]
 
 
@@ -110,6 +111,7 @@ def lib():
         L.orc_set_field.argtypes = [C.c_void_p, dp]
         L.orc_tables.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
         L.orc_demag_field.argtypes = [C.c_void_p, dp, dp, C.c_int]
+        L.orc_kernel.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, dp]
         L.orc_energy.argtypes = [C.c_void_p, dp, dp]
         L.orc_pervector_sums.argtypes = [C.c_void_p, dp, dp]
         L.orc_local_dF.argtypes = [C.c_void_p, dp, dp, C.c_int, dp, dp]
@@ -230,7 +232,8 @@ class Oracle:
     ``spec`` is a plain dict (see ``workloads.py``):
       mesh (nx, ny, nz), pbc (3 bools), h (3 floats, m), Ms0, A0, D0, K1, K2, eA,
       Tc, T (scalars or per-cell arrays), mu, B (T), sigma_cap, demag,
-      grain (per-cell int or None), grain_exch_scale, aniso ('uniaxial'|'cubic').
+      grain (per-cell int or None), grain_exch_scale, aniso ('uniaxial'|'cubic'),
+      demag_images (periodic demag images per side along the pbc axes; 0 open).
     """
 
     def __init__(self, spec, len_power=4, demag_self=False):
@@ -263,6 +266,7 @@ class Oracle:
         p.demag_self = int(bool(demag_self))
         p.len_power = int(len_power)
         p.cell_base = int(spec.get("cell_base", 0))
+        p.demag_images = int(spec.get("demag_images", 0))
         p.aniso_cubic = 1 if spec.get("aniso", "uniaxial") == "cubic" else 0
         for k in ("Ms0", "K1", "K2", "eA", "Tc", "T"):
             setattr(p, k, _dp(self._keep[k]))
@@ -288,6 +292,14 @@ class Oracle:
         out = [np.zeros(n) for _ in range(5)]
         lib().orc_tables(self._ctx, *[_dp(a) for a in out])
         return dict(zip(("me", "chi", "sigma", "K1T", "K2T"), out))
+
+    def kernel(self, X, Y, Z):
+        """Demag kernel at cell offset (X, Y, Z): the Newell tensor, or along
+        periodic demag axes its truncated sum over images (Sec. III films);
+        [xx, yy, zz, xy, xz, yz]."""
+        out = np.zeros(6)
+        lib().orc_kernel(self._ctx, int(X), int(Y), int(Z), _dp(out))
+        return out
 
     def demag_field(self, m, method="direct"):
         """Eq. 14 field (A/m), shape (n, 3)."""

@@ -23,6 +23,10 @@
  *   Newell tensor        self term trace 1, cube 1/3, uniform-prism factors of
  *                        Aharoni's closed form; near/far formulas agree
  *   FFT demag            direct sum agreement
+ *   periodic demag       exact circular-shift covariance; the thickness-averaged
+ *                        field of a cosine magnetization in a film infinite in
+ *                        the plane (closed form of the charge sheets, summed over
+ *                        the cell aliases); half-period offsets by hand
  */
 #include "mmc_oracle.h"
 
@@ -394,6 +398,56 @@ static size_t toff(const orc_ctx *c, int X, int Y, int Z)
 
 static void fft1(double complex *a, int n, int stride, int inverse);
 
+/* Demag kernel of Eq. 14 at cell offset (X, Y, Z).  Open axes: the tensor at
+ * that offset.  The granular and chiral films of Sec. III-IV are periodic in the
+ * plane; the paper does not spell out the periodic convolution, and the reading
+ * taken here is the lattice sum over periodic
+ * images truncated at P = demag_images images on each side of the mesh: along a
+ * periodic axis of extent n an offset X stands for the displacements
+ * X~ + p n, p = -P..P, with X~ the minimal image of X (|X~| <= n/2); when X~ is
+ * exactly half the period both minimal images n/2 and -n/2 are taken, with weight
+ * 1/2 each, so that the kernel keeps the parity of the tensor. */
+void orc_kernel(const orc_ctx *c, int X, int Y, int Z, double out[6])
+{
+    const orc_problem *p = &c->p;
+    const int n[3] = {p->nx, p->ny, p->nz}, o[3] = {X, Y, Z};
+    int nrep[3], rep[3][2], P[3];
+    double wrep[3][2];
+    for (int a = 0; a < 3; ++a) {
+        if (p->demag_images <= 0 || !p->pbc[a]) {
+            nrep[a] = 1; rep[a][0] = o[a]; wrep[a][0] = 1.0; P[a] = 0;
+            continue;
+        }
+        P[a] = p->demag_images;
+        int r = ((o[a] % n[a]) + n[a]) % n[a];          /* X mod n in [0, n) */
+        if (2 * r == n[a]) {
+            nrep[a] = 2;
+            rep[a][0] = r; rep[a][1] = r - n[a];
+            wrep[a][0] = wrep[a][1] = 0.5;
+        } else {
+            nrep[a] = 1;
+            rep[a][0] = 2 * r < n[a] ? r : r - n[a];
+            wrep[a][0] = 1.0;
+        }
+    }
+    for (int k = 0; k < 6; ++k) out[k] = 0.0;
+    for (int ra = 0; ra < nrep[0]; ++ra)
+        for (int rb = 0; rb < nrep[1]; ++rb)
+            for (int rc = 0; rc < nrep[2]; ++rc) {
+                double w = wrep[0][ra] * wrep[1][rb] * wrep[2][rc];
+                for (int pz = -P[2]; pz <= P[2]; ++pz)
+                    for (int py = -P[1]; py <= P[1]; ++py)
+                        for (int px = -P[0]; px <= P[0]; ++px) {
+                            double t[6];
+                            int dx = rep[0][ra] + px * n[0];
+                            int dy = rep[1][rb] + py * n[1];
+                            int dz = rep[2][rc] + pz * n[2];
+                            orc_tensor(p->h[0], p->h[1], p->h[2], dx * p->h[0], dy * p->h[1], dz * p->h[2], t);
+                            for (int k = 0; k < 6; ++k) out[k] += w * t[k];
+                        }
+            }
+}
+
 static void build_demag(orc_ctx *c)
 {
     const orc_problem *p = &c->p;
@@ -401,12 +455,14 @@ static void build_demag(orc_ctx *c)
     size_t nt = (size_t)(2 * c->ox + 1) * (2 * c->oy + 1) * (2 * c->oz + 1);
     c->Nt = (double *)malloc(sizeof(double) * 6 * nt);
     /* compute one octant, fill the rest by parity: xx,yy,zz even; xy odd in x,y;
-     * xz odd in x,z; yz odd in y,z */
+     * xz odd in x,z; yz odd in y,z (the periodic kernel has the same parity).
+     * The convolution below is linear over offsets -(n-1)..n-1, which with the
+     * periodic kernel K(X) = K(X mod n) is the circular convolution exactly. */
     for (int Z = 0; Z <= c->oz; ++Z)
         for (int Y = 0; Y <= c->oy; ++Y)
             for (int X = 0; X <= c->ox; ++X) {
                 double t[6];
-                orc_tensor(p->h[0], p->h[1], p->h[2], X * p->h[0], Y * p->h[1], Z * p->h[2], t);
+                orc_kernel(c, X, Y, Z, t);
                 for (int sz = -1; sz <= 1; sz += 2)
                     for (int sy = -1; sy <= 1; sy += 2)
                         for (int sx = -1; sx <= 1; sx += 2) {

@@ -17,7 +17,8 @@
  *   Eq. 12    cubic anisotropy                               (Sec. II)
  *   Eq. 13    length-move width sigma, capped at 0.03        (Sec. II)
  *   Eq. 14    demagnetizing field by convolution with the demag tensor and the
- *             frozen-field energy change                     (Sec. III)
+ *             frozen-field energy change                     (Sec. III); periodic
+ *             along pbc axes as a truncated sum over images  (Sec. III, films)
  *   Eq. 15    interfacial DMI                                (Sec. IV)
  *   Sec. II   MMC iteration: cone rotation + length change, red-black passes,
  *             cone angle adapted every 100 iterations by +-1 deg outside 0.5+-0.05
@@ -67,6 +68,10 @@ typedef struct {
     uint32_t cell_base;         /* natural index of this mesh's first cell in a larger
                                    lattice it is a window of (the Philox counter word 0
                                    is the cell's index in the whole lattice); 0 normally */
+    int demag_images;           /* > 0: the demag convolution is periodic along every
+                                   pbc axis, summed over this many periodic images on
+                                   each side (the in-plane periodic films of
+                                   Sec. III-IV); 0: open boundaries */
 } orc_problem;
 
 typedef struct orc_ctx orc_ctx;
@@ -99,6 +104,9 @@ void orc_newell(double dx, double dy, double dz, double X, double Y, double Z, d
 void orc_tensor_quad(double dx, double dy, double dz, double X, double Y, double Z,
                      int npts, double out[6]);
 void orc_tensor(double dx, double dy, double dz, double X, double Y, double Z, double out[6]);
+/* demag kernel at cell offset (X, Y, Z) of the problem: the tensor, or along
+ * periodic demag axes the sum over images (see orc_problem.demag_images) */
+void orc_kernel(const orc_ctx *c, int X, int Y, int Z, double out[6]);
 
 /* ---- context ------------------------------------------------------------ */
 orc_ctx *orc_create(const orc_problem *p);
