@@ -56,11 +56,19 @@ typedef enum {
 typedef struct mmc_ctx mmc_ctx;   /* opaque; owned by the library */
 
 /* Mesh (Sec. II): nx*ny*nz cells; periodic[a] != 0 makes axis a periodic for the
- * exchange and DMI bonds and requires an even extent >= 2 on that axis.  The
- * demagnetizing field always uses open (zero-padded) boundaries. */
+ * exchange and DMI bonds and requires an even extent >= 2 on that axis.
+ * demag_images selects the boundaries of the demagnetizing convolution (Eq. 14):
+ * 0 open (zero padded) on every axis; P in [1, 64] periodic along every periodic
+ * axis (the in-plane periodic films of Sec. III-IV), the kernel being the Newell
+ * tensor summed over P periodic images on each side, each offset taken at its
+ * minimal image and the half-period offset split evenly between its two minimal
+ * images.  The periodic kernel is built on the host at create, at a cost that
+ * grows as (2P + 1)^(periodic axes) tensor evaluations per offset; the device
+ * work per update is the same as with open boundaries. */
 typedef struct {
     int nx, ny, nz;
     int periodic[3];
+    int demag_images;
 } mmc_mesh;
 
 /* Material (Sec. II-IV).  Scalars apply to every cell unless the matching

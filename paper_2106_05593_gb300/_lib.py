@@ -32,7 +32,8 @@ class MmcError(RuntimeError):
 
 
 class Mesh(C.Structure):
-    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("periodic", C.c_int * 3)]
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("periodic", C.c_int * 3),
+                ("demag_images", C.c_int)]
 
 
 class Material(C.Structure):

@@ -120,6 +120,7 @@ struct DemagPlan {
 struct SpecSet {
   double h[3];
   int Px, Py, Pz;
+  DemagPeriodic pd;                     // periodic axes of the convolution
   void *d32 = nullptr, *d64 = nullptr;
 };
 
@@ -287,6 +288,8 @@ mmc_status validate(const mmc_chain_desc &d, const mmc_options &o, int idx) {
   for (int a = 0; a < 3; ++a)
     if (m.periodic[a] && (ext[a] < 2 || ext[a] % 2))
       return fail(MMC_ERR_ARG, w + "a periodic extent must be even and >= 2");
+  if (m.demag_images < 0 || m.demag_images > kMaxDemagImages)
+    return fail(MMC_ERR_ARG, w + "demag_images must be in [0, " + std::to_string(kMaxDemagImages) + "]");
   for (int a = 0; a < 3; ++a)
     if (!(d.cellsize[a] > 0.0)) return fail(MMC_ERR_ARG, w + "cell size must be > 0");
   const mmc_material &mt = d.material;
@@ -871,7 +874,7 @@ mmc_status serial_prepare(mmc_ctx *c) {
     for (auto &ss : c->specs) {
       const int ox = std::max(ss.Px / 2, 1), oy = std::max(ss.Py / 2, 1), oz = std::max(ss.Pz / 2, 1);
       std::vector<double> oct;
-      demag_octant(ss.h, ox, oy, oz, oct);
+      demag_octant(ss.h, ox, oy, oz, oct, ss.pd);
       const size_t n = (size_t)ox * oy * oz;
       std::vector<float> soa(6 * n);
       for (size_t q = 0; q < n; ++q)
@@ -1030,17 +1033,28 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
       }
       D.s_off = soff;
       soff += 3LL * D.nrows * D.Sx;
+      DemagPeriodic pd;
+      {
+        const mmc_mesh &ms = c->hc[i].mesh;
+        const int ext[3] = {ms.nx, ms.ny, ms.nz};
+        for (int a = 0; a < 3; ++a) {
+          pd.n[a] = ext[a];
+          pd.per[a] = ms.periodic[a] ? 1 : 0;
+        }
+        pd.images = ms.demag_images;
+      }
       int found = -1;
       for (size_t s = 0; s < c->specs.size(); ++s) {
         const SpecSet &ss = c->specs[s];
         if (ss.Px == D.Px && ss.Py == D.Py && ss.Pz == D.Pz && ss.h[0] == c->hc[i].h[0] &&
-            ss.h[1] == c->hc[i].h[1] && ss.h[2] == c->hc[i].h[2])
+            ss.h[1] == c->hc[i].h[1] && ss.h[2] == c->hc[i].h[2] && ss.pd == pd)
           found = (int)s;
       }
       if (found < 0) {
         SpecSet ss;
         for (int a = 0; a < 3; ++a) ss.h[a] = c->hc[i].h[a];
         ss.Px = D.Px; ss.Py = D.Py; ss.Pz = D.Pz;
+        ss.pd = pd;
         c->specs.push_back(ss);
         found = (int)c->specs.size() - 1;
       }
@@ -1080,7 +1094,7 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     std::vector<void *> p32, p64;
     for (auto &ss : c->specs) {
       std::vector<double> sp;
-      demag_spectra(ss.h, ss.Px, ss.Py, ss.Pz, sp);
+      demag_spectra(ss.h, ss.Px, ss.Py, ss.Pz, sp, ss.pd);
       std::vector<float> spf(sp.begin(), sp.end());
       float *d32 = nullptr;
       double *d64 = nullptr;

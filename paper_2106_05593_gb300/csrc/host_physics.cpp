@@ -259,17 +259,21 @@ static void dipole_average(const double h[3], const double R[3], const TriRule q
 }
 
 struct TensorRules {
-  TriRule r8[3], r6[3], r4[3], r3[3];
+  TriRule r8[3], r6[3], r4[3], r3[3], r2[3];
   explicit TensorRules(const double h[3]) {
     for (int a = 0; a < 3; ++a) {
       r8[a] = tri_rule(h[a], 8);
       r6[a] = tri_rule(h[a], 6);
       r4[a] = tri_rule(h[a], 4);
       r3[a] = tri_rule(h[a], 3);
+      r2[a] = tri_rule(h[a], 2);
     }
   }
 };
 
+// n Gauss points per half integrate the cell-pair average with a relative error
+// of order (h/R)^(2n); the ladder keeps it below ~1e-12 (1e-10 from 300 h on,
+// where only far offsets and periodic images fall)
 static void tensor_with(const double h[3], const double R[3], const TensorRules &rules, double out[6]) {
   const double hmax = std::max(h[0], std::max(h[1], h[2]));
   const double r = std::sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]) / hmax;
@@ -277,7 +281,8 @@ static void tensor_with(const double h[3], const double R[3], const TensorRules 
   else if (r < 12.0) dipole_average(h, R, rules.r8, out);
   else if (r < 40.0) dipole_average(h, R, rules.r6, out);
   else if (r < 100.0) dipole_average(h, R, rules.r4, out);
-  else dipole_average(h, R, rules.r3, out);
+  else if (r < 300.0) dipole_average(h, R, rules.r3, out);
+  else dipole_average(h, R, rules.r2, out);
 }
 
 void demag_tensor(const double h[3], const double R[3], double out[6]) {
@@ -308,27 +313,113 @@ static void fft_inplace(std::complex<double> *a, int n, long long s) {
   }
 }
 
-// the six tensor components (xx yy zz xy xz yz) at offsets (x, y, z) h with
-// 0 <= x < ox, 0 <= y < oy, 0 <= z < oz, interleaved: oct[6 (x + ox (y + oy z)) + c];
-// the other octants follow by symmetry (xy odd in x and y, xz in x and z, yz in y and z)
-void demag_octant(const double h[3], int ox, int oy, int oz, std::vector<double> &oct) {
-  oct.assign((size_t)6 * ox * oy * oz, 0.0);
-  TensorRules rules(h);
+template <typename F>
+static void parallel_for(long long total, F fn) {
   const int nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
   std::vector<std::thread> th;
-  const long long total = 1LL * ox * oy * oz;
   for (int t = 0; t < nth; ++t)
     th.emplace_back([&, t]() {
-      for (long long q = t; q < total; q += nth) {
-        const int x = (int)(q % ox), y = (int)((q / ox) % oy), z = (int)(q / (1LL * ox * oy));
-        const double R[3] = {x * h[0], y * h[1], z * h[2]};
-        tensor_with(h, R, rules, &oct[6 * q]);
-      }
+      for (long long q = t; q < total; q += nth) fn(q);
     });
   for (auto &x : th) x.join();
 }
 
-void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double> &out) {
+// Periodic kernel at base offsets 0 <= d_a <= n_a / 2 along the periodic axes
+// (0 <= d_a < o_a along open ones): the tensor summed over the images
+// d_a + p n_a, |p| <= images, the half period d_a = n_a / 2 split between
+// +n_a / 2 and -n_a / 2 with weight 1/2 each.
+static void periodic_base(const double h[3], const DemagPeriodic &pd, const TensorRules &rules, int bx, int by,
+                          int bz, std::vector<double> &base) {
+  parallel_for(1LL * bx * by * bz, [&](long long q) {
+    const int d[3] = {(int)(q % bx), (int)((q / bx) % by), (int)(q / (1LL * bx * by))};
+    int nrep[3], rep[3][2], P[3];
+    double w[3][2];
+    for (int a = 0; a < 3; ++a) {
+      const bool per = pd.images > 0 && pd.per[a];
+      P[a] = per ? pd.images : 0;
+      rep[a][0] = d[a];
+      w[a][0] = 1.0;
+      nrep[a] = 1;
+      if (per && 2 * d[a] == pd.n[a]) {
+        nrep[a] = 2;
+        rep[a][1] = -d[a];
+        w[a][0] = w[a][1] = 0.5;
+      }
+    }
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < nrep[0]; ++i)
+      for (int j = 0; j < nrep[1]; ++j)
+        for (int k = 0; k < nrep[2]; ++k) {
+          const double wt = w[0][i] * w[1][j] * w[2][k];
+          for (int pz = -P[2]; pz <= P[2]; ++pz)
+            for (int py = -P[1]; py <= P[1]; ++py)
+              for (int px = -P[0]; px <= P[0]; ++px) {
+                const double R[3] = {(rep[0][i] + px * pd.n[0]) * h[0], (rep[1][j] + py * pd.n[1]) * h[1],
+                                     (rep[2][k] + pz * pd.n[2]) * h[2]};
+                double t[6];
+                tensor_with(h, R, rules, t);
+                for (int c = 0; c < 6; ++c) acc[c] += wt * t[c];
+              }
+        }
+    for (int c = 0; c < 6; ++c) base[6 * q + c] = acc[c];
+  });
+}
+
+// the six tensor components (xx yy zz xy xz yz) at offsets (x, y, z) h with
+// 0 <= x < ox, 0 <= y < oy, 0 <= z < oz, interleaved: oct[6 (x + ox (y + oy z)) + c];
+// the other octants follow by symmetry (xy odd in x and y, xz in x and z, yz in y and z).
+// Along a periodic axis of pd the value at x is the periodic kernel at x mod n,
+// taken from its base offset min(r, n - r), r = x mod n, with the sign of the
+// components odd in that axis flipped when r > n / 2 (the kernel is periodic and
+// has the tensor's parity).
+void demag_octant(const double h[3], int ox, int oy, int oz, std::vector<double> &oct, const DemagPeriodic &pd) {
+  oct.assign((size_t)6 * ox * oy * oz, 0.0);
+  TensorRules rules(h);
+  if (!pd.any()) {
+    parallel_for(1LL * ox * oy * oz, [&](long long q) {
+      const int x = (int)(q % ox), y = (int)((q / ox) % oy), z = (int)(q / (1LL * ox * oy));
+      const double R[3] = {x * h[0], y * h[1], z * h[2]};
+      tensor_with(h, R, rules, &oct[6 * q]);
+    });
+    return;
+  }
+  const int o[3] = {ox, oy, oz};
+  bool per[3];
+  int b[3];
+  for (int a = 0; a < 3; ++a) {
+    per[a] = pd.per[a] != 0;
+    b[a] = per[a] ? pd.n[a] / 2 + 1 : o[a];
+  }
+  std::vector<double> base((size_t)6 * b[0] * b[1] * b[2]);
+  periodic_base(h, pd, rules, b[0], b[1], b[2], base);
+  // odd components per axis: xy (3) in x, y; xz (4) in x, z; yz (5) in y, z
+  static const int odd[3][6] = {{0, 0, 0, 1, 1, 0}, {0, 0, 0, 1, 0, 1}, {0, 0, 0, 0, 1, 1}};
+  for (int z = 0; z < oz; ++z)
+    for (int y = 0; y < oy; ++y)
+      for (int x = 0; x < ox; ++x) {
+        const int v[3] = {x, y, z};
+        int d[3];
+        bool flip[3] = {false, false, false};
+        for (int a = 0; a < 3; ++a) {
+          d[a] = v[a];
+          if (per[a]) {
+            const int r = v[a] % pd.n[a];
+            flip[a] = 2 * r > pd.n[a];
+            d[a] = flip[a] ? pd.n[a] - r : r;
+          }
+        }
+        const double *src = &base[6 * (d[0] + 1LL * b[0] * (d[1] + 1LL * b[1] * d[2]))];
+        double *dst = &oct[6 * (x + 1LL * ox * (y + 1LL * oy * z))];
+        for (int c = 0; c < 6; ++c) {
+          double s = 1.0;
+          for (int a = 0; a < 3; ++a)
+            if (flip[a] && odd[a][c]) s = -s;
+          dst[c] = s * src[c];
+        }
+      }
+}
+
+void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double> &out, const DemagPeriodic &pd) {
   const int ncomp = Pz > 1 ? 6 : 4;
   const int qx = Px / 2 + 1, qy = Py / 2 + 1, qz = Pz / 2 + 1;
   const long long P = 1LL * Px * Py * Pz;
@@ -340,7 +431,7 @@ void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double
   // which keeps every spectrum real)
   const int ox = std::max(Px / 2, 1), oy = std::max(Py / 2, 1), oz = std::max(Pz / 2, 1);
   std::vector<double> oct;
-  demag_octant(h, ox, oy, oz, oct);
+  demag_octant(h, ox, oy, oz, oct, pd);
   static const int comp_map[6] = {0, 1, 2, 3, 4, 5};  // xx yy zz xy xz yz
   std::vector<std::complex<double>> a((size_t)P);
   for (int c = 0; c < ncomp; ++c) {

@@ -16,6 +16,7 @@ constexpr double mu0 = 1.25663706212e-6;
 constexpr double kPi = 3.14159265358979323846;
 
 constexpr int kMaxFFT = 4096;        // largest padded FFT length per axis (twiddle table length)
+constexpr int kMaxDemagImages = 64;  // largest number of periodic demag images per side
 constexpr int kHistMax = 1024;       // largest histogram bin count
 constexpr int kSweepBlock = 256;     // threads per sweep-pass block
 constexpr int kReduceBlock = 256;
@@ -136,8 +137,29 @@ double sigma_of_T(double T, double Tc, double mu, double V, double Ms0, double c
 void long_coeffs(double T, double Tc, double mu, double V, double Ms0, double *c2, double *c4);
 double rms_len_eq7(double T, double Tc, double mu, double V, double Ms0);
 void demag_tensor(const double h[3], const double R[3], double out[6]);
-void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double> &out);
-void demag_octant(const double h[3], int ox, int oy, int oz, std::vector<double> &oct);
+// Periodic demag along the axes a with per[a] set (extent n[a]): the kernel is the
+// tensor summed over `images` periodic images on each side, each offset at its
+// minimal image, the half period split between its two minimal images.  With
+// images == 0 (or no periodic axis) the convolution has open boundaries.  The
+// zero-padded convolution with this kernel on offsets -(n-1)..n-1 is the
+// circular convolution exactly.
+struct DemagPeriodic {
+  int n[3] = {1, 1, 1};
+  int per[3] = {0, 0, 0};
+  int images = 0;
+  bool any() const { return images > 0 && (per[0] || per[1] || per[2]); }
+  bool operator==(const DemagPeriodic &o) const {
+    if (any() != o.any()) return false;
+    if (!any()) return true;
+    for (int a = 0; a < 3; ++a)
+      if (per[a] != o.per[a] || (per[a] && n[a] != o.n[a])) return false;
+    return images == o.images;
+  }
+};
+void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double> &out,
+                   const DemagPeriodic &pd = DemagPeriodic());
+void demag_octant(const double h[3], int ox, int oy, int oz, std::vector<double> &oct,
+                  const DemagPeriodic &pd = DemagPeriodic());
 
 // ---------------------------------------------------------------------------
 // launches

@@ -6,7 +6,9 @@ marshals arguments (problem dicts -> C structs, arrays -> pointers).
 A problem ("chain") is a dict with the keys
   mesh (nx, ny, nz), pbc (3 bools), h (3 cell sizes, m), Ms0, A0, D0, K1, K2,
   eA (3), Tc, T, mu, B (3, tesla), grain (per-cell ints or None),
-  grain_exch_scale, aniso ('uniaxial' | 'cubic');
+  grain_exch_scale, aniso ('uniaxial' | 'cubic'), demag_images (periodic images
+  per side of the demag convolution along the pbc axes; 0, the default, keeps it
+  open);
 Ms0, K1, eA, Tc and T may be per-cell arrays (natural order i + nx (j + ny k)).
 """
 from __future__ import annotations
@@ -60,7 +62,8 @@ class MMC:
             d = descs[k]
             nx, ny, nz = sp["mesh"]
             n = nx * ny * nz
-            d.mesh = Mesh(nx, ny, nz, (C.c_int * 3)(*[int(bool(p)) for p in sp.get("pbc", (0, 0, 0))]))
+            d.mesh = Mesh(nx, ny, nz, (C.c_int * 3)(*[int(bool(p)) for p in sp.get("pbc", (0, 0, 0))]),
+                          int(sp.get("demag_images", 0)))
             d.cellsize = (C.c_double * 3)(*sp["h"])
             mat = Material()
             cell, val = _percell(sp["Ms0"], n)

@@ -17,9 +17,10 @@ def lib_or_skip():
     return P
 
 
-def oracle_pass(spec, m4, color, sweep, chain, seed, theta, H=None):
-    """Oracle sublattice pass on an FP32 state given as (n, 4)."""
-    o = O.Oracle(spec)
+def oracle_pass(spec, m4, color, sweep, chain, seed, theta, H=None, o=None):
+    """Oracle sublattice pass on an FP32 state given as (n, 4) (o: an oracle of
+    spec to reuse, or None)."""
+    o = O.Oracle(spec) if o is None else o
     m = m4[:, :3].astype(np.float64)
     if spec.get("demag") and H is None:
         H = o.demag_field(m, "fft" if o.n > 1024 else "direct")

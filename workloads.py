@@ -63,6 +63,12 @@ def chiral(n=512, T=300.0):
                  K1=8e5, eA=(0.0, 0.0, 1.0), Tc=600.0, T=T, demag=True)
 
 
+def chiral_periodic(n=512, T=300.0, images=10):
+    """Chiral film (Sec. IV) periodic in the plane for exchange, DMI and the
+    demag convolution (images periodic images on each side)."""
+    return chiral(n, T) | {"pbc": (True, True, False), "demag_images": int(images)}
+
+
 def chiral512_batch(nchains=16, n=512):
     """Temperature scan T = 50 + 40 c K, c = 0..15 (crosses Tc = 600 K)."""
     return [chiral(n, 50.0 + 40.0 * c) for c in range(nchains)]
