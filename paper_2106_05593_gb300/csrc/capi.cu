@@ -872,7 +872,10 @@ mmc_status serial_prepare(mmc_ctx *c) {
     std::vector<float *> ptrs;
     std::vector<int4> dims;
     for (auto &ss : c->specs) {
-      const int ox = std::max(ss.Px / 2, 1), oy = std::max(ss.Py / 2, 1), oz = std::max(ss.Pz / 2, 1);
+      // offsets up to n - 1 per axis: P / 2 >= n on padded axes, P = n on circular ones
+      const int ox = ss.pd.circ[0] ? ss.Px : std::max(ss.Px / 2, 1);
+      const int oy = ss.pd.circ[1] ? ss.Py : std::max(ss.Py / 2, 1);
+      const int oz = ss.pd.circ[2] ? ss.Pz : std::max(ss.Pz / 2, 1);
       std::vector<double> oct;
       demag_octant(ss.h, ox, oy, oz, oct, ss.pd);
       const size_t n = (size_t)ox * oy * oz;
@@ -1021,9 +1024,24 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     }
     D.Px = D.Py = D.Pz = 1;
     if (o.demag) {
-      D.Px = pad_len(D.nx, true);
-      D.Py = pad_len(D.ny, true);
-      D.Pz = pad_len(D.nz, D.nz > 1);
+      // periodic demag axes whose extent is a power of two are transformed
+      // circularly (length n); the others are zero padded to >= 2 n
+      DemagPeriodic pd;
+      {
+        const mmc_mesh &ms = c->hc[i].mesh;
+        const int ext[3] = {ms.nx, ms.ny, ms.nz};
+        for (int a = 0; a < 3; ++a) {
+          pd.n[a] = ext[a];
+          pd.per[a] = ms.periodic[a] ? 1 : 0;
+          pd.circ[a] = ms.demag_images > 0 && ms.periodic[a] && ext[a] >= kCircMin &&
+                       (ext[a] & (ext[a] - 1)) == 0;
+        }
+        pd.images = ms.demag_images;
+      }
+      D.circ = (pd.circ[0] ? 1 : 0) | (pd.circ[1] ? 2 : 0) | (pd.circ[2] ? 4 : 0);
+      D.Px = pd.circ[0] ? D.nx : pad_len(D.nx, true);
+      D.Py = pd.circ[1] ? D.ny : pad_len(D.ny, true);
+      D.Pz = pd.circ[2] ? D.nz : pad_len(D.nz, D.nz > 1);
       D.lx = ilog2(D.Px); D.ly = ilog2(D.Py); D.lz = ilog2(D.Pz);
       // spectrum row stride: a multiple of 8 and of the column-group width
       // 4096 / Py of the tiled 2D layout
@@ -1033,16 +1051,6 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
       }
       D.s_off = soff;
       soff += 3LL * D.nrows * D.Sx;
-      DemagPeriodic pd;
-      {
-        const mmc_mesh &ms = c->hc[i].mesh;
-        const int ext[3] = {ms.nx, ms.ny, ms.nz};
-        for (int a = 0; a < 3; ++a) {
-          pd.n[a] = ext[a];
-          pd.per[a] = ms.periodic[a] ? 1 : 0;
-        }
-        pd.images = ms.demag_images;
-      }
       int found = -1;
       for (size_t s = 0; s < c->specs.size(); ++s) {
         const SpecSet &ss = c->specs[s];

@@ -361,6 +361,12 @@ static void periodic_base(const double h[3], const DemagPeriodic &pd, const Tens
                 for (int c = 0; c < 6; ++c) acc[c] += wt * t[c];
               }
         }
+    // at a half period the components odd in that axis cancel exactly (parity)
+    static const int odd[3][6] = {{0, 0, 0, 1, 1, 0}, {0, 0, 0, 1, 0, 1}, {0, 0, 0, 0, 1, 1}};
+    for (int a = 0; a < 3; ++a)
+      if (nrep[a] == 2)
+        for (int c = 0; c < 6; ++c)
+          if (odd[a][c]) acc[c] = 0.0;
     for (int c = 0; c < 6; ++c) base[6 * q + c] = acc[c];
   });
 }
@@ -426,10 +432,13 @@ void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double
   const long long Q = 1LL * qx * qy * qz;
   out.assign((size_t)ncomp * Q, 0.0);
 
-  // tensor on the symmetric octant of offsets |X| < Px/2, ... (the Nyquist
-  // offsets -P/2 never reach a mesh cell when n <= P/2 and are left at zero,
-  // which keeps every spectrum real)
-  const int ox = std::max(Px / 2, 1), oy = std::max(Py / 2, 1), oz = std::max(Pz / 2, 1);
+  // tensor on the symmetric octant of offsets |X| < Px/2, ... (on a padded axis
+  // the Nyquist offset -P/2 never reaches a mesh cell when n <= P/2 and is left
+  // at zero, which keeps every spectrum real; on a circular axis, P = n, it is
+  // the periodic kernel's half-period value, whose odd components vanish)
+  const int ox = pd.circ[0] ? Px / 2 + 1 : std::max(Px / 2, 1);
+  const int oy = pd.circ[1] ? Py / 2 + 1 : std::max(Py / 2, 1);
+  const int oz = pd.circ[2] ? Pz / 2 + 1 : std::max(Pz / 2, 1);
   std::vector<double> oct;
   demag_octant(h, ox, oy, oz, oct, pd);
   static const int comp_map[6] = {0, 1, 2, 3, 4, 5};  // xx yy zz xy xz yz
@@ -443,7 +452,8 @@ void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double
           const int Y = y < (Py + 1) / 2 ? y : y - Py;
           const int Z = z < (Pz + 1) / 2 ? z : z - Pz;
           double v = 0.0;
-          const bool nyq = (Px > 1 && X == -Px / 2) || (Py > 1 && Y == -Py / 2) || (Pz > 1 && Z == -Pz / 2);
+          const bool nyq = (Px > 1 && !pd.circ[0] && X == -Px / 2) || (Py > 1 && !pd.circ[1] && Y == -Py / 2) ||
+                           (Pz > 1 && !pd.circ[2] && Z == -Pz / 2);
           if (!nyq) {
             const int ax = std::abs(X), ay = std::abs(Y), az = std::abs(Z);
             v = oct[6 * (ax + 1LL * ox * (ay + 1LL * oy * az)) + cc];

@@ -16,51 +16,11 @@
 //            also H_d in FP64, natural order.
 // The FFTs are the shared-memory Stockham transforms of fft.cuh; R = float or
 // double selects the arithmetic of the whole convolution.
-#include "fft.cuh"
+#include "demag_args.cuh"
+#include "demag_il.h"
 #include "fft_il.cuh"
-#include "mmc_internal.h"
 
 namespace mmc {
-
-template <typename R>
-struct DemagArgs {
-  using C = typename Cx<R>::T;
-  const ChainDev *chains;
-  const int *blk_chain;
-  const long long *blk_first;
-  const float4 *m;
-  const float4 *tab;
-  const float *ms;
-  C *S;
-  const R *const *nhat;
-  const C *tw;
-  float4 *heff;
-  double *Hd;
-  int Hd_chain;
-  const R *m_nat;     // optional natural-order input (3 per cell) instead of the split state
-  R Ms_override;      // > 0: uniform Ms0 used with m_nat
-};
-
-__device__ __forceinline__ int pairs_per_block(int Px) {
-  const int G = Px >= 8 ? Px >> 3 : 1;
-  int np = (int)blockDim.x / (3 * G);
-  return np < 1 ? 1 : (np > 8 ? 8 : np);
-}
-
-// M = Ms0 m of cell (x, row r) from the split layout, formed in the convolution's precision
-template <typename R>
-__device__ __forceinline__ void load_M(const ChainDev &ch, const float4 *m, const float *ms, int r, int x,
-                                       R &Mx, R &My, R &Mz) {
-  const int k = (int)divq((unsigned)r, ch.ny_m, ch.ny_l), j = r - k * ch.ny;
-  const int col = (x + j + k) & 1;
-  const long long S = (long long)ch.nrows * ch.hx;
-  const long long idx = (long long)col * S + (long long)r * ch.hx + (x >> 1);
-  const float4 v = m[ch.m_off + idx];
-  const R Ms = ch.ms_off >= 0 ? (R)ms[ch.ms_off + idx] : (R)ch.Ms0d;
-  Mx = Ms * (R)v.x;
-  My = Ms * (R)v.y;
-  Mz = Ms * (R)v.z;
-}
 
 template <typename R>
 __global__ void k_rows_fwd(DemagArgs<R> A) {
@@ -283,276 +243,6 @@ __global__ void k_rows_inv(DemagArgs<R> A) {
   }
 }
 
-// ---------------------------------------------------------------------------
-// 2D fast path (Pz == 1): interleaved radix-16 transforms, E complex elements
-// per block, V per thread (E / V threads).  The spectrum buffer is tiled by
-// column groups of CC = E / (3 Py) columns: element (comp, y, kx) at
-// ((comp * NG + kx / CC) * ny + y) * CC + kx % CC, NG = Sx / CC, so a row kernel
-// block (2 E / (3 Px) consecutive rows) writes runs of rows * CC elements and a
-// column kernel block reads and writes contiguous ny * CC runs.
-
-// kernel configurations: E elements per block, V values per thread (E / V
-// threads), MINB blocks per SM for the register budget.  Two FP32 variants
-// (radix 16 with 384 threads, radix 32 with 192 threads) are timed against each
-// other on the actual batch; FP64 uses radix 16.
-struct CfgF16 { using R = float; static constexpr int E = 12288, V = 16, MINB = 1; };
-struct CfgF32 { using R = float; static constexpr int E = 12288, V = 32, MINB = 1; };
-struct CfgD16 { using R = double; static constexpr int E = 6144, V = 16, MINB = 1; };
-struct CfgF16h { using R = float; static constexpr int E = 6144, V = 16, MINB = 2; };
-
-// index of (comp, y, kx) in the column-tiled spectrum layout [comp][kx / CC][y][CC], CC = 2^lcc
-__device__ __forceinline__ long long tiled(int comp, int y, int kx, int ny, int NG, int lcc) {
-  return ((long long)(comp * NG + (kx >> lcc)) * ny + y) * (1 << lcc) + (kx & ((1 << lcc) - 1));
-}
-
-__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
-
-template <typename CFG>
-__global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagArgs<typename CFG::R> A) {
-  using R = typename CFG::R;
-  using C = typename Cx<R>::T;
-  constexpr int E = CFG::E, V = CFG::V;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *raw = reinterpret_cast<C *>(smem_raw);
-  C *buf = raw;
-  const int c = A.blk_chain[blockIdx.x];
-  const ChainDev &ch = A.chains[c];
-  const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
-  // 3 groups (x+iy of the even row, x+iy of the odd row, z_even + i z_odd) of np
-  // interleaved sequences: element (g, x, qq) at g * Px * np + x * np + qq
-  constexpr int LE3 = ilog2c(E / 3);         // E / 3 is a power of two
-  const int lnp = LE3 - lx, np = 1 << lnp, gs = Px * np;
-  const int lcc = LE3 - ch.ly, CC = 1 << lcc, NG = Sx >> lcc;
-  const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
-  const int totpairs = (ny + 1) / 2;
-  C *tws = raw + il_padded(E);               // pass twiddle tables (at most Px entries)
-  il_twiddles<C, V>(tws, A.tw, lx);
-  // the upper half x >= Px/2 is zero padding the first FFT pass never reads
-#pragma unroll 4
-  for (int idx = threadIdx.x; idx < np * (Px >> 1); idx += blockDim.x) {
-    const int qq = idx >> (lx - 1), x = idx & ((Px >> 1) - 1);
-    const int pr = pair0 + qq, r0 = 2 * pr, r1 = r0 + 1;
-    R M0x = 0, M0y = 0, M0z = 0, M1x = 0, M1y = 0, M1z = 0;
-    if (pr < totpairs && x < nx) {
-      if (A.m_nat) {
-        const R Ms = A.Ms_override;
-        const R *v0 = A.m_nat + 3 * ((long long)r0 * nx + x);
-        M0x = Ms * v0[0]; M0y = Ms * v0[1]; M0z = Ms * v0[2];
-        if (r1 < ny) {
-          const R *v1 = A.m_nat + 3 * ((long long)r1 * nx + x);
-          M1x = Ms * v1[0]; M1y = Ms * v1[1]; M1z = Ms * v1[2];
-        }
-      } else {
-        load_M<R>(ch, A.m, A.ms, r0, x, M0x, M0y, M0z);
-        if (r1 < ny) load_M<R>(ch, A.m, A.ms, r1, x, M1x, M1y, M1z);
-      }
-    }
-    C z;
-    const int e0 = x * np + qq;
-    z.x = M0x; z.y = M0y; buf[e0] = z;
-    z.x = M1x; z.y = M1y; buf[e0 + gs] = z;
-    z.x = M0z; z.y = M1z; buf[e0 + 2 * gs] = z;
-  }
-  __syncthreads();
-  fft_il<C, V, false, true, false>(buf, lx, IlMap{lnp, 3, gs}, tws);
-  // half spectra (kx <= Px/2) of the six real rows of each pair, written in
-  // tiled order: c fastest, then the block's rows, then column group, then comp
-  const int half = Px / 2 + 1;
-  const int nrb = 2 * np, lnrb = lnp + 1;
-  const int ngu = (half + CC - 1) / CC;
-  C *S = A.S + ch.s_off;
-  const int tot = 3 * ngu * nrb * CC;
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int cc = idx & (CC - 1), rr = (idx >> lcc) & (nrb - 1), o = idx >> (lcc + lnrb);
-    const int comp = (o >= ngu) + (o >= 2 * ngu), g = o - comp * ngu;
-    const int kx = g * CC + cc;
-    const int r = 2 * pair0 + rr;
-    if (kx >= half || r >= ny) continue;
-    const int qq = rr >> 1, h = rr & 1;
-    const int sq = comp == 2 ? 2 : h;
-    const bool take_b = comp == 1 || (comp == 2 && h == 1);
-    const int km = (Px - kx) & (Px - 1);
-    const C Z = buf[sq * gs + kx * np + qq], Zm = buf[sq * gs + km * np + qq];
-    C o2;
-    if (!take_b) { o2.x = (R)0.5 * (Z.x + Zm.x); o2.y = (R)0.5 * (Z.y - Zm.y); }
-    else { o2.x = (R)0.5 * (Z.y + Zm.y); o2.y = (R)0.5 * (Zm.x - Z.x); }
-    S[tiled(comp, r, kx, ny, NG, lcc)] = o2;
-  }
-}
-
-template <typename CFG>
-__global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs<typename CFG::R> A) {
-  using R = typename CFG::R;
-  using C = typename Cx<R>::T;
-  constexpr int E = CFG::E, V = CFG::V;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *raw = reinterpret_cast<C *>(smem_raw);
-  C *buf = raw;
-  const int c = A.blk_chain[blockIdx.x];
-  const ChainDev &ch = A.chains[c];
-  const int Px = ch.Px, Py = ch.Py, ly = ch.ly, ny = ch.ny, Sx = ch.Sx;
-  constexpr int LE3 = ilog2c(E / 3);         // E / 3 is a power of two
-  const int lcc = LE3 - ly, CC = 1 << lcc, NG = Sx >> lcc;
-  const int g = (int)(blockIdx.x - A.blk_first[c]);
-  const int kx0 = g * CC;
-  const int qx = Px / 2 + 1, qy = Py / 2 + 1;
-  const C *S = A.S + ch.s_off;
-  C *tws = raw + il_padded(E);               // pass twiddle tables (at most Py entries)
-  il_twiddles<C, V>(tws, A.tw, ly);
-  // buf[(comp * Py + y) * CC + cc]; rows y >= ny are the zero padding, and the
-  // upper half y >= Py/2 is never read by the first FFT pass
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < E / 2; idx += blockDim.x) {
-    const int cc = idx & (CC - 1), y = (idx >> lcc) & ((Py >> 1) - 1), comp = idx >> (LE3 - 1);
-    C v;
-    v.x = 0; v.y = 0;
-    if (y < ny) v = S[((long long)(comp * NG + g) * ny + y) * CC + cc];
-    buf[(comp * Py + y) * CC + cc] = v;
-  }
-  __syncthreads();
-  fft_il<C, V, false, true, false>(buf, ly, IlMap{lcc, 3, Py * CC}, tws);
-  const long long Q = (long long)qx * qy;
-  const R *nh = A.nhat[ch.spec];
-  for (int idx = threadIdx.x; idx < Py * CC; idx += blockDim.x) {
-    const int cc = idx & (CC - 1), ky = idx >> lcc;
-    const int kx = kx0 + cc;
-    if (kx >= qx) continue;
-    const int kyq = ky <= Py / 2 ? ky : Py - ky;
-    const R sy = ky <= Py / 2 ? (R)1 : (R)-1;
-    const long long qi = (long long)kyq * qx + kx;
-    const R Nxx = nh[qi], Nyy = nh[Q + qi], Nzz = nh[2 * Q + qi], Nxy = sy * nh[3 * Q + qi];
-    const int b0 = ky * CC + cc, b1 = (Py + ky) * CC + cc, b2 = (2 * Py + ky) * CC + cc;
-    const C Mx = buf[b0], My = buf[b1], Mz = buf[b2];
-    C hx_, hy_, hz_;
-    hx_.x = -(Nxx * Mx.x + Nxy * My.x);
-    hx_.y = -(Nxx * Mx.y + Nxy * My.y);
-    hy_.x = -(Nxy * Mx.x + Nyy * My.x);
-    hy_.y = -(Nxy * Mx.y + Nyy * My.y);
-    hz_.x = -(Nzz * Mz.x);
-    hz_.y = -(Nzz * Mz.y);
-    buf[b0] = hx_; buf[b1] = hy_; buf[b2] = hz_;
-  }
-  __syncthreads();
-  fft_il<C, V, true, false, true>(buf, ly, IlMap{lcc, 3, Py * CC}, tws);
-  C *So = A.S + ch.s_off;
-  for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
-    const int cc = idx & (CC - 1), y = (idx >> lcc) & (Py - 1), comp = idx >> LE3;
-    if (y < ny) So[((long long)(comp * NG + g) * ny + y) * CC + cc] = buf[idx];
-  }
-}
-
-template <typename CFG>
-__global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_inv2(DemagArgs<typename CFG::R> A) {
-  using R = typename CFG::R;
-  using C = typename Cx<R>::T;
-  constexpr int E = CFG::E, V = CFG::V;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *raw = reinterpret_cast<C *>(smem_raw);
-  C *buf = raw;
-  const int c = A.blk_chain[blockIdx.x];
-  const ChainDev &ch = A.chains[c];
-  const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
-  constexpr int LE3 = ilog2c(E / 3);         // E / 3 is a power of two
-  const int lnp = LE3 - lx, np = 1 << lnp, gs = Px * np;
-  const int lcc = LE3 - ch.ly, CC = 1 << lcc, NG = Sx >> lcc;
-  const int pair0 = (int)(blockIdx.x - A.blk_first[c]) * np;
-  const int half = Px / 2 + 1;
-  const int nrb = 2 * np, lnrb = lnp + 1;
-  const int ngu = (half + CC - 1) / CC;
-  const C *S = A.S + ch.s_off;
-  C *tws = raw + il_padded(E);               // pass twiddle tables (at most Px entries)
-  il_twiddles<C, V>(tws, A.tw, lx);
-  // Each sequence is z = a + i b for the half spectra a, b of two real rows:
-  // z[k] = a[k] + i b[k] and z[Px - k] = conj(a[k]) + i conj(b[k]), real parts only
-  // at k = 0 and Px/2 (where the spectra of real rows are real).  Sequence
-  // (h, qq) pairs x and y of row 2 qq + h, sequence (2, qq) the z of rows 2 qq and
-  // 2 qq + 1; a work item (kx, row) reads its values and writes z directly.
-  auto put = [&](int sb, int kx, C a, C b) {
-    if (kx == 0 || 2 * kx == Px) {
-      C z;
-      z.x = a.x; z.y = b.x;
-      buf[sb + kx * np] = z;
-    } else {
-      C zk, zm;
-      zk.x = a.x - b.y; zk.y = a.y + b.x;
-      zm.x = a.x + b.y; zm.y = b.x - a.y;
-      buf[sb + kx * np] = zk;
-      buf[sb + (Px - kx) * np] = zm;
-    }
-  };
-  const int tot = ngu * nrb * CC;
-#pragma unroll 8
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int cc = idx & (CC - 1), rr = (idx >> lcc) & (nrb - 1), g = idx >> (lcc + lnrb);
-    const int kx = g * CC + cc;
-    if (kx >= half) continue;
-    const int r = 2 * pair0 + rr;
-    const int qq = rr >> 1, h = rr & 1;
-    C ax, ay, z0, z1;
-    ax.x = ax.y = ay.x = ay.y = z0.x = z0.y = z1.x = z1.y = 0;
-    if (r < ny) {
-      ax = S[tiled(0, r, kx, ny, NG, lcc)];
-      ay = S[tiled(1, r, kx, ny, NG, lcc)];
-      if (h == 0) {
-        z0 = S[tiled(2, r, kx, ny, NG, lcc)];
-        if (r + 1 < ny) z1 = S[tiled(2, r + 1, kx, ny, NG, lcc)];
-      }
-    }
-    put(h * gs + qq, kx, ax, ay);
-    if (h == 0) put(2 * gs + qq, kx, z0, z1);
-  }
-  __syncthreads();
-  fft_il<C, V, true, false, true>(buf, lx, IlMap{lnp, 3, gs}, tws);
-  const R scale = (R)1 / ((R)Px * (R)ch.Py * (R)ch.Pz);
-  const long long Sl = (long long)ny * ch.hx;
-  const bool percell = ch.t_off >= 0;
-  const float mu0f = (float)mu0;
-  const int totpairs = (ny + 1) / 2;
-  for (int idx = threadIdx.x; idx < np * nx; idx += blockDim.x) {
-    const int qq = (int)divq((unsigned)idx, ch.nx_m, ch.nx_l), x = idx - qq * nx;
-    const int pr = pair0 + qq;
-    if (pr >= totpairs) continue;
-    const C z0 = buf[x * np + qq], z1 = buf[gs + x * np + qq], z2 = buf[2 * gs + x * np + qq];
-    for (int h = 0; h < 2; ++h) {
-      const int r = 2 * pr + h;
-      if (r >= ny) break;
-      const R Hx = (h == 0 ? z0.x : z1.x) * scale;
-      const R Hy = (h == 0 ? z0.y : z1.y) * scale;
-      const R Hz = (h == 0 ? z2.x : z2.y) * scale;
-      const int colr = (x + r) & 1;
-      const long long li = (long long)colr * Sl + (long long)r * ch.hx + (x >> 1);
-      if (A.heff) {
-        const float zee = percell ? A.tab[ch.t_off + 2 * Sl + li].x : ch.zee;
-        A.heff[ch.h_off + li] = make_float4(zee * (ch.Bx + mu0f * (float)Hx), zee * (ch.By + mu0f * (float)Hy),
-                                            zee * (ch.Bz + mu0f * (float)Hz), 0.f);
-      }
-      if (A.Hd && c == A.Hd_chain) {
-        const long long nat = x + (long long)nx * r;
-        A.Hd[3 * nat + 0] = (double)Hx;
-        A.Hd[3 * nat + 1] = (double)Hy;
-        A.Hd[3 * nat + 2] = (double)Hz;
-      }
-    }
-  }
-}
-
-template <typename CFG>
-void launch_il(const Launch &L, const DemagLaunch &P, DemagArgs<typename CFG::R> A) {
-  using C = typename Cx<typename CFG::R>::T;
-  constexpr int T = CFG::E / CFG::V;
-  A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
-  if (P.ev) cudaEventRecord(P.ev[0], L.stream);
-  k_rows_fwd2<CFG><<<P.rows_blocks, T, P.rows_smem, L.stream>>>(A);
-  if (P.ev) cudaEventRecord(P.ev[1], L.stream);
-  A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
-  k_cols2d<CFG><<<P.cols_blocks, T, P.cols_smem, L.stream>>>(A);
-  if (P.ev) cudaEventRecord(P.ev[2], L.stream);
-  A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
-  k_rows_inv2<CFG><<<P.rows_blocks, T, P.inv_smem, L.stream>>>(A);
-  if (P.ev) cudaEventRecord(P.ev[3], L.stream);
-  *L.counter += 3;
-}
-
 template <typename R>
 void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
   using C = typename Cx<R>::T;
@@ -605,17 +295,10 @@ cudaError_t demag_set_smem_limits() {
   e = cudaFuncSetAttribute(k_rows_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e != cudaSuccess) return e;
   const int lil = 200 * 1024;
-  const void *fns[12] = {(const void *)k_rows_fwd2<CfgF16>, (const void *)k_rows_fwd2<CfgF32>,
-                         (const void *)k_rows_fwd2<CfgD16>, (const void *)k_rows_fwd2<CfgF16h>,
-                         (const void *)k_cols2d<CfgF16>, (const void *)k_cols2d<CfgF32>,
-                         (const void *)k_cols2d<CfgD16>, (const void *)k_cols2d<CfgF16h>,
-                         (const void *)k_rows_inv2<CfgF16>, (const void *)k_rows_inv2<CfgF32>,
-                         (const void *)k_rows_inv2<CfgD16>, (const void *)k_rows_inv2<CfgF16h>};
-  for (const void *f : fns) {
-    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lil);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  if ((e = il_set_smem<CfgF16>(lil)) != cudaSuccess) return e;
+  if ((e = il_set_smem<CfgF32>(lil)) != cudaSuccess) return e;
+  if ((e = il_set_smem<CfgD16>(lil)) != cudaSuccess) return e;
+  return il_set_smem<CfgF16h>(lil);
 }
 
 int il_elements(bool fp64) { return fp64 ? CfgD16::E : CfgF16::E; }

@@ -66,6 +66,7 @@ struct __align__(16) ChainDev {
   int Px, Py, Pz;     // padded FFT sizes
   int Sx;             // row stride (complex elements) of the spectrum buffer
   int lx, ly, lz;     // log2 of the padded sizes
+  int circ;           // bit a: axis a periodic for demag with P_a = n_a (circular transform, no padding)
   double Ms0d;        // Ms0 in FP64 (convolution input of the FP64 path)
 };
 
@@ -143,19 +144,24 @@ void demag_tensor(const double h[3], const double R[3], double out[6]);
 // images == 0 (or no periodic axis) the convolution has open boundaries.  The
 // zero-padded convolution with this kernel on offsets -(n-1)..n-1 is the
 // circular convolution exactly.
+// A periodic axis whose extent is a power of two (>= kCircMin) is transformed
+// circularly (circ[a]: transform length n_a, no zero padding); the kernel's
+// half-period offset then reaches mesh cells and is kept in the spectrum.
 struct DemagPeriodic {
   int n[3] = {1, 1, 1};
   int per[3] = {0, 0, 0};
+  int circ[3] = {0, 0, 0};
   int images = 0;
   bool any() const { return images > 0 && (per[0] || per[1] || per[2]); }
   bool operator==(const DemagPeriodic &o) const {
     if (any() != o.any()) return false;
     if (!any()) return true;
     for (int a = 0; a < 3; ++a)
-      if (per[a] != o.per[a] || (per[a] && n[a] != o.n[a])) return false;
+      if (per[a] != o.per[a] || circ[a] != o.circ[a] || (per[a] && n[a] != o.n[a])) return false;
     return images == o.images;
   }
 };
+constexpr int kCircMin = 8;          // smallest periodic extent transformed circularly
 void demag_spectra(const double h[3], int Px, int Py, int Pz, std::vector<double> &out,
                    const DemagPeriodic &pd = DemagPeriodic());
 void demag_octant(const double h[3], int ox, int oy, int oz, std::vector<double> &oct,

@@ -2,7 +2,9 @@
 Sec. III-IV) against the oracle's truncated image sum, through the C ABI.
 
 - FP64 field: 1e-9 relative on 2D (interleaved kernels) and 3D (generic
-  kernels) meshes, periodic along x, y, both, or all three axes.
+  kernels) meshes, periodic along x, y, both, or all three axes; periodic
+  extents that are powers of two (>= 8) take the circular transforms, the
+  others the zero-padded ones with the periodized kernel.
 - The GPU field of a cosine mode equals the thin-film closed form.
 - Sublattice passes and whole iterations with the FP32 / FP64 / cuFFT field:
   decisions within the FP32 bound of the open-boundary tests.
@@ -82,13 +84,14 @@ def test_pass_with_periodic_demag(P):
     m4 = W.smooth_state(spec["mesh"], 3, 0.86)
     o = O.Oracle(spec)
     H = o.demag_field(m4[:, :3].astype(np.float64), "fft")
-    for fp64, cufft in ((0, 0), (1, 0), (0, 1)):
-        g = P.MMC(spec, demag=1, demag_fp64=fp64, demag_cufft=cufft)
+    # every FP32 kernel variant, the FP64 kernels and the cuFFT comparison path
+    for fp64, cufft, variant in ((0, 0, 1), (0, 0, 2), (0, 0, 3), (1, 0, 0), (0, 1, 0)):
+        g = P.MMC(spec, demag=1, demag_fp64=fp64, demag_cufft=cufft, fft_variant=variant)
         for color in (0, 1):
             g.set_m(m4)
             dec_g, acc_g = g.pass_debug(0, color, 5, 3, 25.0)
             _, acc_o, dec_o, band_o = oracle_pass(spec, m4, color, 5, 0, 3, 25.0, H=H, o=o)
-            print("periodic film64 fp64=%d cufft=%d" % (fp64, cufft), color,
+            print("periodic film64 fp64=%d cufft=%d variant=%d" % (fp64, cufft, variant), color,
                   compare_pass(dec_g, acc_g, dec_o, acc_o, band_o))
 
 
@@ -154,7 +157,7 @@ def test_serial_form_periodic(P, self_term):
 
 def test_energy_and_gradient_periodic(P):
     import torch
-    spec = pfilm((24, 20, 2), (4e-9, 4e-9, 4e-9), (1, 1, 0), 3, A0=1e-11, D0=1.5e-3, K1=8e5,
+    spec = pfilm((32, 20, 2), (4e-9, 4e-9, 4e-9), (1, 1, 0), 3, A0=1e-11, D0=1.5e-3, K1=8e5,
                  Tc=600.0, T=300.0, B=(0.01, -0.02, 0.03))
     n = int(np.prod(spec["mesh"]))
     me = O.me(spec["T"], spec["Tc"])
