@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--fft-variant", type=int, default=0, choices=(0, 1, 2, 3),
                     help="FP32 2D demag kernels: 0 timed pick at create, 1 radix 16, 2 radix 32, "
                          "3 radix 16 two blocks per SM")
+    ap.add_argument("--stream-groups", type=int, default=0,
+                    help="chain groups iterating on concurrent streams: 0 auto (2), 1 one stream")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the cuFFT demag timing and the one-chain-per-launch comparison")
     ap.add_argument("--chains", type=int, default=0, help="use only the first N chains of the workload")
@@ -149,6 +151,18 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def nvtx_range(name):
+    """Open (name) or close (None) an NVTX range, where torch provides NVTX."""
+    import torch
+    try:
+        if name is None:
+            torch.cuda.nvtx.range_pop()
+        else:
+            torch.cuda.nvtx.range_push(name)
+    except (AttributeError, RuntimeError):
+        pass
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("k_sweep.cu", "k_demag.cu", "k_demag_il.cuh", "demag_il.h", "demag_args.cuh", "fft.cuh", "fft_il.cuh",
@@ -171,15 +185,29 @@ def recorded_traffic(kernel, workload_name, src_hash):
 
 
 # algorithmic bytes per cell per launch: what each kernel must read and write
-def algorithmic_bytes(kind, demag, percell):
+def spectrum_bytes_per_cell(specs):
+    """Bytes per cell of the FP32 half spectrum (3 components, complex): 24 for rows
+    zero padded to >= 2 nx, 12 for rows transformed circularly (periodic demag
+    along x with a power-of-two extent >= 8: half as many kx)."""
+    tot = cells = 0.0
+    for sp in specs:
+        nx = sp["mesh"][0]
+        circ = (sp.get("demag_images", 0) > 0 and sp["pbc"][0] and nx >= 8 and (nx & (nx - 1)) == 0)
+        n = float(np.prod(sp["mesh"]))
+        tot += n * (12.0 if circ else 24.0)
+        cells += n
+    return tot / cells
+
+
+def algorithmic_bytes(kind, demag, percell, spec=24.0):
     if kind == "sweep_pass":     # per pass: half the cells updated; 48 B/cell-update (+48 per-cell table)
         return 0.5 * (48.0 if demag else 32.0) + (0.5 * 48.0 if percell else 0.0)
-    if kind == "demag_rows_fwd":  # m read 16 B, three half-spectrum rows written 24 B
-        return 40.0
-    if kind == "demag_cols":      # spectrum read and written, 2 x 24 B
-        return 48.0
-    if kind == "demag_rows_inv":  # spectrum read 24 B, h_eff written 16 B
-        return 40.0
+    if kind == "demag_rows_fwd":  # m read 16 B, three half-spectrum rows written (spec B)
+        return 16.0 + spec
+    if kind == "demag_cols":      # spectrum read and written, 2 x spec B
+        return 2.0 * spec
+    if kind == "demag_rows_inv":  # spectrum read (spec B), h_eff written 16 B
+        return spec + 16.0
     return 0.0
 
 
@@ -315,7 +343,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         print("profile run ok", gp.launches, flush=True)
         return
-    g = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=args.fft_variant, stream=stream)
+    g = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=args.fft_variant,
+            stream_groups=args.stream_groups, stream=stream)
     seed = replica_seed(rank)
     g.init_random(seed)
     ncell = sum(g.ncell)
@@ -336,11 +365,13 @@ def run_ours(args):
     l0 = g.launches
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    nvtx_range("timed_steps")            # lets a profiler select the timed launches
     e0.record(stream)
     for _ in range(args.steps):
         g.sweep(SWEEPS_PER_STEP, seed)
     e1.record(stream)
     torch.cuda.synchronize()
+    nvtx_range(None)
     barrier()
     ms = e0.elapsed_time(e1)
     launches = g.launches - l0
@@ -356,7 +387,8 @@ def run_ours(args):
             best = kind
     tms, cnt = phases[best]
     avg_s = tms / cnt * 1e-3
-    bytes_per_launch = algorithmic_bytes(best, demag, percell) * ncell
+    spec_b = spectrum_bytes_per_cell(specs)
+    bytes_per_launch = algorithmic_bytes(best, demag, percell, spec_b) * ncell
     achieved = bytes_per_launch / avg_s / 1e9
     src = kernel_source_hash()
     roofline = {"bound": "hbm", "kernel": best, "achieved": achieved, "peak": peak,
