@@ -177,3 +177,53 @@ def test_energy_and_gradient_periodic(P):
     Ee = o.energy(m4[:, :3].astype(np.float64))
     for k in range(7):
         assert Eg[k] == pytest.approx(Ee[k], abs=1e-9 * np.abs(Ee[1:]).sum()), (k, Eg, Ee)
+
+
+def test_images_argument_is_validated(P):
+    for bad in (-1, 65):
+        with pytest.raises(P.MmcError):
+            P.MMC(pfilm((16, 16, 1), (2e-9, 2e-9, 2e-9), (1, 1, 0), bad), demag=1)
+    # images without a periodic axis leave the convolution open
+    spec = pfilm((16, 12, 1), (2e-9, 2e-9, 2e-9), (0, 0, 0), 5)
+    m4 = W.random_state(16 * 12, 2, 0.5, 1.0)
+    g = P.MMC(spec, demag=1)
+    g.set_m(m4)
+    Ho = O.Oracle(spec | {"demag_images": 0}).demag_field(m4[:, :3].astype(np.float64))
+    assert np.abs(g.demag_field(0) - Ho).max() < 1e-9 * np.abs(Ho).max()
+
+
+def test_granular_periodic_chain(P):
+    """Per-cell Ms0 (grains) with the periodic field, circular transforms."""
+    spec = W.granular_chain(32, 6) | {"pbc": (True, True, False), "demag_images": 3}
+    n = 32 * 32
+    m4 = W.random_state(n, 17, 0.6, 0.9)
+    g = P.MMC(spec, demag=1)
+    g.set_m(m4)
+    o = O.Oracle(spec)
+    Ho = o.demag_field(m4[:, :3].astype(np.float64), "direct")
+    # per-cell Ms0 is stored in FP32 on the device (relative rounding 2^-24 per source)
+    assert np.abs(g.demag_field(0) - Ho).max() < 1e-7 * np.abs(Ho).max()
+    for color in (0, 1):
+        g.set_m(m4)
+        dec_g, acc_g = g.pass_debug(0, color, 3, 9, 30.0)
+        _, acc_o, dec_o, band_o = oracle_pass(spec, m4, color, 3, 0, 9, 30.0, H=Ho, o=o)
+        # per-cell m_e^2 is stored in FP32 (no float-float pair): wider absolute bound
+        compare_pass(dec_g, acc_g, dec_o, acc_o, band_o, absolute=5e-4)
+
+
+def test_minimizer_with_periodic_demag(P):
+    """SDesc (Sec. III) on a film periodic in the plane: same minimum as the
+    oracle's minimizer with the periodic kernel."""
+    s = pfilm((16, 8, 1), (3e-9, 3e-9, 2e-9), (1, 1, 0), 2, A0=1.2e-11, D0=1e-3, K1=3e5, Tc=650.0,
+              T=300.0, B=(0.02, 0.01, 0.05))
+    m4 = W.smooth_state(s["mesh"], 3, 0.8)
+    g = P.MMC(s, demag=1)
+    g.set_m(m4)
+    r = g.minimize(0, maxit=20000, tol=1e-7)
+    assert r["converged"], r
+    o = O.Oracle(s)
+    mo, ok, it, tq = o.sdesc(m4[:, :3].astype(np.float64), maxit=20000, tol=1e-7)
+    assert ok
+    mg = g.get_m()[:, :3].astype(np.float64)
+    assert np.abs(mg - mo).max() < 2e-5
+    assert r["energy"][0] == pytest.approx(o.energy(mo)[0], rel=1e-9)
