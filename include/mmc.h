@@ -9,7 +9,8 @@
  * Eq. 10), D0 (interfacial DMI, Eq. 15), K1/K2 with easy axis e_A (uniaxial
  * Eq. 11, or cubic Eq. 12), Curie temperature Tc and atomic moment mu (Eqs. 8-9),
  * a temperature field T, an applied field, and the demagnetizing interaction by
- * zero-padded FFT convolution with the Newell tensor (Sec. III, Eq. 14).
+ * FFT convolution with the Newell tensor (Sec. III, Eq. 14), open (zero padded)
+ * or periodic in the plane (mmc_mesh.demag_images).
  * mmc_sweep runs MMC iterations: each cell, one checkerboard sublattice at a
  * time, proposes a rotation in a cone plus a multiplicative length change
  * (Sec. II) and accepts it with Eq. 5.

@@ -1,5 +1,10 @@
-// Demagnetizing field by zero-padded FFT convolution with the Newell tensor
-// (Sec. III, Eq. 14): H_d = -IFFT( N^ . FFT(Ms0 m) ), for every chain of a batch.
+// Demagnetizing field by FFT convolution with the Newell tensor (Sec. III,
+// Eq. 14): H_d = -IFFT( N^ . FFT(Ms0 m) ), for every chain of a batch.  Open
+// axes are zero padded to Px >= 2 nx; periodic demag axes either use the
+// periodic kernel on the padded grid or, for power-of-two extents, a circular
+// transform of length nx (ChainDev::circ).  This file holds the generic kernels
+// (any nz, used for 3D meshes) and the dispatch; the interleaved 2D kernels are
+// in k_demag_il.cuh.
 //
 // Three kernels per update, each batched over chains:
 //  rows_fwd  two rows per sequence pair: the real rows Mx, My of row r, of row
