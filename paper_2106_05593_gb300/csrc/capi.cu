@@ -8,6 +8,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mmc.h"
 #include "mmc_internal.h"
 #include "angles.h"
@@ -22,6 +24,15 @@ mmc_status fail(mmc_status s, const std::string &msg) {
   g_err = msg;
   return s;
 }
+
+// NVTX range for profilers (nsys, ncu --nvtx): every public call, and in eager
+// execution every phase of an iteration; a no-op when no tool is attached
+struct Trace {
+  explicit Trace(const char *name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+  Trace(const Trace &) = delete;
+  Trace &operator=(const Trace &) = delete;
+};
 
 }  // namespace
 
@@ -804,14 +815,29 @@ void issue_block(mmc_ctx *c, int k, unsigned key0, unsigned key1, int sample_eve
     return;
   }
   for (int off = 0; off < k; ++off) {
-    if (c->any_demag) issue_demag(c, pt);
-    timed(c, pt, 3, [&] { launch_sweep_pass(L, sweep_launch(c, 0, (unsigned)off, key0, key1)); });
-    if (c->any_demag && c->opt.demag_per_pass) issue_demag(c, pt);
-    timed(c, pt, 3, [&] { launch_sweep_pass(L, sweep_launch(c, 1, (unsigned)off, key0, key1)); });
-    if (sample_every > 0 && (start + off + 1) % (uint64_t)sample_every == 0)
+    if (c->any_demag) {
+      Trace t("demag");
+      issue_demag(c, pt);
+    }
+    {
+      Trace t("pass red");
+      timed(c, pt, 3, [&] { launch_sweep_pass(L, sweep_launch(c, 0, (unsigned)off, key0, key1)); });
+    }
+    if (c->any_demag && c->opt.demag_per_pass) {
+      Trace t("demag");
+      issue_demag(c, pt);
+    }
+    {
+      Trace t("pass black");
+      timed(c, pt, 3, [&] { launch_sweep_pass(L, sweep_launch(c, 1, (unsigned)off, key0, key1)); });
+    }
+    if (sample_every > 0 && (start + off + 1) % (uint64_t)sample_every == 0) {
+      Trace t("observables");
       timed(c, pt, 4, [&] { launch_obs(L, obs_launch(c, 1)); });
+    }
   }
   const int adapt_now = ((start + k) % 100 == 0) ? 1 : 0;
+  Trace t("advance");
   timed(c, pt, 5, [&] {
     launch_advance(L, c->d_st, c->nchains, (unsigned)k, c->d_sweep_base, adapt_now, c->opt.adapt, 1.f, 180.f);
   });
@@ -852,7 +878,10 @@ mmc_status sweep_impl(mmc_ctx *c, int64_t n, uint64_t seed, int sample_every) {
         c->graphs.push_back(e);
         g = &c->graphs.back();
       }
-      CUDA_TRY(cudaGraphLaunch(g->exec, c->stream));
+      {
+        Trace t("graph: 100 iterations");
+        CUDA_TRY(cudaGraphLaunch(g->exec, c->stream));
+      }
       c->launches += g->launches;
     } else {
       issue_block(c, k, key0, key1, sample_every, c->host_sweep);
@@ -963,6 +992,7 @@ void mmc_destroy(mmc_ctx *c) {
 
 mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_options *opt,
                       void *stream, mmc_ctx **out) {
+  Trace trace("mmc_create");
   if (!out) return fail(MMC_ERR_ARG, "null output pointer");
   *out = nullptr;
   if (!chains || nchains < 1) return fail(MMC_ERR_ARG, "need at least one chain");
@@ -1353,6 +1383,7 @@ mmc_status mmc_set_temperature(mmc_ctx *c, int chain, double T, const double *T_
 }
 
 mmc_status mmc_demag_update(mmc_ctx *c) {
+  Trace trace("mmc_demag_update");
   if (!c) return fail(MMC_ERR_ARG, "null context");
   if (!c->any_demag) return MMC_OK;
   issue_demag(c);
@@ -1428,17 +1459,20 @@ mmc_status mmc_init_random(mmc_ctx *c, uint64_t seed, double len) {
 }
 
 mmc_status mmc_sweep(mmc_ctx *c, int64_t n, uint64_t seed) {
+  Trace trace("mmc_sweep");
   MMC_TRY(sweep_impl(c, n, seed, 0));
   return MMC_OK;
 }
 
 mmc_status mmc_sweep_sampled(mmc_ctx *c, int64_t n, uint64_t seed, int sample_every) {
+  Trace trace("mmc_sweep_sampled");
   if (sample_every < 1) return fail(MMC_ERR_ARG, "sample_every must be >= 1");
   MMC_TRY(sweep_impl(c, n, seed, sample_every));
   return MMC_OK;
 }
 
 mmc_status mmc_sweep_serial(mmc_ctx *c, int64_t n, uint64_t seed) {
+  Trace trace("mmc_sweep_serial");
   if (!c) return fail(MMC_ERR_ARG, "null context");
   if (n < 0) return fail(MMC_ERR_ARG, "negative sweep count");
   MMC_TRY(serial_prepare(c));
@@ -1491,6 +1525,7 @@ mmc_status mmc_pass_debug(mmc_ctx *c, int chain, int color, uint32_t sweep, uint
 }
 
 mmc_status mmc_observables(mmc_ctx *c, int chain, mmc_obs *out, int reset) {
+  Trace trace("mmc_observables");
   MMC_TRY(check_chain(c, chain));
   if (!out) return fail(MMC_ERR_ARG, "null output");
   ChainState s;
@@ -1603,6 +1638,7 @@ mmc_status mmc_demag_field(mmc_ctx *c, int chain, double *H) {
 }
 
 mmc_status mmc_energy(mmc_ctx *c, int chain, double out[7]) {
+  Trace trace("mmc_energy");
   MMC_TRY(check_chain(c, chain));
   if (!out) return fail(MMC_ERR_ARG, "null output");
   const ChainHost &H = c->hc[chain];
@@ -1637,6 +1673,7 @@ mmc_status mmc_tables(mmc_ctx *c, int chain, double *me, double *chi, double *si
 
 mmc_status mmc_energy_grad(mmc_ctx *c, int chain, const void *m, int fp64, const double params[5],
                            double E[7], void *dEdm, double dEdp[5]) {
+  Trace trace("mmc_energy_grad");
   MMC_TRY(check_chain(c, chain));
   if (!m || !E) return fail(MMC_ERR_ARG, "null m or E");
   const ChainHost &H = c->hc[chain];
@@ -1719,6 +1756,7 @@ mmc_status mmc_energy_grad(mmc_ctx *c, int chain, const void *m, int fp64, const
 
 mmc_status mmc_minimize(mmc_ctx *c, int chain, int64_t maxit, double tol, int64_t *iters, double *torque,
                         double E[7]) {
+  Trace trace("mmc_minimize");
   MMC_TRY(check_chain(c, chain));
   if (!(tol > 0) || maxit < 0) return fail(MMC_ERR_ARG, "tol must be > 0 and maxit >= 0");
   const ChainHost &H = c->hc[chain];
