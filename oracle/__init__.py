@@ -119,6 +119,7 @@ def lib():
         L.orc_pass.restype = C.c_int64
         L.orc_pass.argtypes = [C.c_void_p, dp, dp, C.c_int, C.c_uint32, C.c_uint32, C.c_uint64,
                                C.c_double, C.POINTER(C.c_int8), dp, dp]
+        L.orc_trial_terms.argtypes = [C.c_void_p, dp, dp, C.c_uint32, C.c_uint32, C.c_uint64, C.c_double, dp]
         L.orc_angle_hist.argtypes = [C.c_void_p, dp, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_int64), dp]
         L.orc_sdesc.restype = C.c_int
         L.orc_sdesc.argtypes = [C.c_void_p, dp, C.c_int, C.c_double, C.POINTER(C.c_int), dp]
@@ -356,6 +357,19 @@ class Oracle:
         nacc = lib().orc_serial_sweep(self._ctx, _dp(mm), _dp(Hh), int(sweep), int(chain),
                                       int(seed), float(theta_deg))
         return mm.reshape(self.n, 3), Hh.reshape(self.n, 3), nacc
+
+    def trial_terms(self, m, H, sweep, chain, seed, theta_deg):
+        """App. B (Fig. 11): mean |dF_term| / kT over the trial moves of every cell
+        at state m (frozen field H, or None for the field of m):
+        [ex, dmi, an, zee, long, demag]."""
+        mm = self._m(m)
+        if H is None:
+            H = self.demag_field(mm.reshape(-1, 3), "direct" if self.n <= 4096 else "fft")
+        Hf = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(-1))
+        out = np.zeros(6)
+        lib().orc_trial_terms(self._ctx, _dp(mm), _dp(Hf), int(sweep), int(chain), int(seed),
+                              float(theta_deg), _dp(out))
+        return out
 
     def angle_hist(self, m, bins=100, lo=0.0, hi=np.pi):
         """Histogram of the polar angle to the mean direction (Sec. II, Fig. 1d-f):

@@ -944,6 +944,27 @@ int64_t orc_pass(orc_ctx *c, double *m, const double *H, int color, uint32_t swe
     return nacc;
 }
 
+/* App. B (Fig. 11): the size of each free-energy term of the trial moves.  For
+ * every cell of the mesh (both sublattices, each against the same state m and
+ * frozen field H) the trial move the sweep would propose at iteration `sweep`
+ * (same random numbers, cone half-angle theta_deg) is drawn, its energy change
+ * split into the terms of orc_local_dF, and |term| / kT of the cell averaged
+ * over the cells: out = [ex, dmi, an, zee, long, demag]. */
+void orc_trial_terms(orc_ctx *c, const double *m, const double *H, uint32_t sweep, uint32_t chain,
+                     uint64_t seed, double theta_deg, double out[6])
+{
+    double cos_tc = cos(theta_deg * PI / 180.0);
+    for (int k = 0; k < 6; ++k) out[k] = 0.0;
+    for (int q = 0; q < c->n; ++q) {
+        double u[4], mn[3], t[7];
+        draw4((uint32_t)q + c->p.cell_base, sweep, chain, 0u, seed, u);
+        propose(m + 3 * q, cos_tc, c->sigma[q], u, mn);
+        orc_local_dF(c, m, H, q, mn, t);
+        for (int k = 0; k < 6; ++k) out[k] += fabs(t[k + 1]) / c->kT[q];
+    }
+    for (int k = 0; k < 6; ++k) out[k] /= (double)c->n;
+}
+
 /* App. B: serial MMC, cells in index order, the demag field updated after
  * every accepted move so that every move's Eq. 14 term uses the field of the
  * current state (plus the self term when demag_self is set). */

@@ -22,7 +22,8 @@
  *   Eq. 15    interfacial DMI                                (Sec. IV)
  *   Sec. II   MMC iteration: cone rotation + length change, red-black passes,
  *             cone angle adapted every 100 iterations by +-1 deg outside 0.5+-0.05
- *   App. B    serial MMC with the demag field updated after every accepted move
+ *   App. B    serial MMC with the demag field updated after every accepted move;
+ *             the per-term size of the trial moves' free-energy changes (Fig. 11)
  *
  * Parity status of each function (what pins it) is listed in the header
  * comment of mmc_oracle.c.
@@ -142,6 +143,12 @@ int64_t orc_pass(orc_ctx *c, double *m, const double *H, int color, uint32_t swe
  * problem's demag_self is set; H is updated in place. */
 int64_t orc_serial_sweep(orc_ctx *c, double *m, double *H, uint32_t sweep,
                          uint32_t chain, uint64_t seed, double theta_deg);
+
+/* App. B (Fig. 11): mean |dF_term| / kT of the trial moves of every cell at state
+ * m with frozen field H (both sublattices against the same state; the moves the
+ * sweep draws at iteration `sweep`): out = [ex, dmi, an, zee, long, demag]. */
+void orc_trial_terms(orc_ctx *c, const double *m, const double *H, uint32_t sweep, uint32_t chain,
+                     uint64_t seed, double theta_deg, double out[6]);
 
 /* Sec. II transverse check (Fig. 1d-f): histogram of the polar angle of every
  * cell to the mean direction of m, `bins` equal bins on [lo, hi), outside
