@@ -272,6 +272,20 @@ mmc_status mmc_observables(mmc_ctx *ctx, int chain, mmc_obs *out, int reset);
 mmc_status mmc_angle_hist(mmc_ctx *ctx, int chain, int bins, double theta_lo, double theta_hi, int64_t *hist,
                           double mean_dir[3]);
 
+/* Size of the free-energy terms of the trial moves (App. B, Fig. 11): for every
+ * cell of one chain, both sublattices evaluated against the current state and
+ * its frozen demag field (Eq. 14), the trial move the sweep would draw at
+ * iteration `sweep` with `seed` (Philox counter (cell, sweep, chain, 0), cone
+ * half-angle theta_deg, or the chain's current angle when theta_deg < 0, and the
+ * length move of Eq. 13) is formed and its free-energy change split by term.
+ * out[6] (HOST) receives the means over the cells of |dF| / kT of the cell:
+ * exchange (Eq. 10), DMI (Eq. 15), anisotropy (Eqs. 11-12), Zeeman, longitudinal
+ * (Eq. 7), demag (Eq. 14).  The state is not changed; averaging the result over
+ * the states of a run gives the paper's per-term averages.  MMC_ERR_ARG:
+ * theta_deg > 180 or a null output. */
+mmc_status mmc_trial_terms(mmc_ctx *ctx, int chain, uint32_t sweep, uint64_t seed, double theta_deg,
+                           double out[6]);
+
 /* Energy terms of one chain, in J: out[7] = {total, exchange, dmi, anisotropy,
  * zeeman, longitudinal (Eq. 7), demag (E_d = -(mu0 V/2) sum Ms0 m.H_d)}.
  * Sums accumulate in FP64; the demag field of the current state is recomputed

@@ -20,7 +20,7 @@ EXPORTS = [
     "mmc_default_options", "mmc_create", "mmc_create_single", "mmc_destroy", "mmc_set_field",
     "mmc_set_m", "mmc_get_m", "mmc_init_random", "mmc_sweep", "mmc_sweep_sampled",
     "mmc_demag_update", "mmc_pass_debug", "mmc_observables", "mmc_energy", "mmc_demag_field",
-    "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_fft_tuning", "mmc_sweep_serial", "mmc_minimize", "mmc_set_temperature", "mmc_angle_hist", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell",
+    "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_fft_tuning", "mmc_sweep_serial", "mmc_minimize", "mmc_set_temperature", "mmc_angle_hist", "mmc_trial_terms", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell",
     "mmc_checkpoint", "mmc_restore", "mmc_observables_noalloc", "mmc_status_str", "mmc_last_error",
 ]
 
@@ -120,6 +120,8 @@ def load():
     L.mmc_phase_times.argtypes = [vp, C.c_int64, C.c_uint64, dp, C.POINTER(C.c_int64)]
     L.mmc_angle_hist.restype = st
     L.mmc_angle_hist.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(C.c_int64), dp]
+    L.mmc_trial_terms.restype = st
+    L.mmc_trial_terms.argtypes = [vp, C.c_int, C.c_uint32, C.c_uint64, C.c_double, dp]
     L.mmc_set_temperature.restype = st
     L.mmc_set_temperature.argtypes = [vp, C.c_int, C.c_double, dp]
     L.mmc_minimize.restype = st

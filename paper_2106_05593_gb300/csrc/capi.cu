@@ -13,6 +13,7 @@
 #include "../../include/mmc.h"
 #include "mmc_internal.h"
 #include "angles.h"
+#include "terms.h"
 
 using namespace mmc;
 
@@ -208,6 +209,7 @@ struct mmc_ctx {
   bool obs_fresh = false;               // current-state observables of all chains are up to date
   int *d_flag = nullptr;                // device scratch int (input checks)
   unsigned long long *d_ang = nullptr;  // angular histogram counters (kHistMax + 1)
+  double *d_terms = nullptr;            // trial-term partials (blocks x 6) and sums (6)
   std::vector<GraphEntry> graphs;
   std::vector<void *> allocs;
 
@@ -1620,6 +1622,30 @@ mmc_status mmc_angle_hist(mmc_ctx *c, int chain, int bins, double theta_lo, doub
   CUDA_TRY(cudaMemcpyAsync(h.data(), d_h, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   for (int b = 0; b <= bins; ++b) hist[b] = (int64_t)h[(size_t)b];
+  return MMC_OK;
+}
+
+mmc_status mmc_trial_terms(mmc_ctx *c, int chain, uint32_t sweep, uint64_t seed, double theta_deg,
+                           double out[6]) {
+  Trace trace("mmc_trial_terms");
+  MMC_TRY(check_chain(c, chain));
+  if (!out) return fail(MMC_ERR_ARG, "null output");
+  if (!(theta_deg <= 180)) return fail(MMC_ERR_ARG, "theta_deg must be <= 180 (negative: the chain's angle)");
+  if (c->any_demag && c->heff_stale) MMC_TRY(mmc_demag_update(c));
+  const long long slots = c->hc[chain].slots;       // per colour
+  const int nb = trial_terms_blocks(slots);
+  if (!c->d_terms) MMC_TRY(dalloc_t(c, &c->d_terms, (size_t)6 * (trial_terms_blocks(c->max_slots) + 1)));
+  const float omc = theta_deg >= 0 ? (float)(1.0 - std::cos(theta_deg * kPi / 180.0)) : -1.f;
+  Launch L = c->L();
+  launch_trial_terms(L, c->d_ch, c->d_st, chain, slots, c->ch[chain].t_off >= 0, c->d_m, c->d_heff, c->d_tab,
+                     sweep, (unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32), omc, c->d_terms,
+                     c->d_terms + 6 * (size_t)nb);
+  MMC_TRY(check_launch());
+  double sums[6];
+  CUDA_TRY(cudaMemcpyAsync(sums, c->d_terms + 6 * (size_t)nb, sizeof(sums), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const double n = (double)c->hc[chain].ncell;
+  for (int k = 0; k < 6; ++k) out[k] = sums[k] / n;
   return MMC_OK;
 }
 

@@ -99,3 +99,21 @@ def angular_histogram(engine, chain, nsnap, every, seed, bins=100, lo=0.0, hi=np
     centres = lo + (np.arange(bins) + 0.5) * width
     total = acc.sum()
     return centres, (acc / (total * width) if total > 0 else acc)
+
+
+TERM_NAMES = ("exchange", "dmi", "anisotropy", "zeeman", "longitudinal", "demag")
+
+
+def trial_term_averages(engine, chain, nsnap, every, seed):
+    """The per-term free-energy changes of the trial moves (App. B, Fig. 11):
+    after every `every` iterations the mean |dF| / kT of each term over the
+    trial moves of all cells of the chain (the moves of the next iteration, at
+    the chain's current cone angle) is taken; returns a dict of the averages
+    over nsnap configurations."""
+    acc = np.zeros(6)
+    for _ in range(nsnap):
+        engine.sweep(every, seed)
+        sweep = int(engine.observables(chain)["sweeps"])
+        acc += engine.trial_terms(chain, sweep, seed, -1.0)
+    acc /= max(nsnap, 1)
+    return dict(zip(TERM_NAMES, acc))

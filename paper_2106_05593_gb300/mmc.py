@@ -219,6 +219,16 @@ class MMC:
                                     h.ctypes.data_as(C.POINTER(C.c_int64)), _dptr(d)), "mmc_angle_hist")
         return h, d
 
+    def trial_terms(self, chain=0, sweep=0, seed=1, theta_deg=-1.0):
+        """App. B (Fig. 11): mean |dF| / kT per term of the trial moves of every cell
+        at the current state -- [exchange, DMI, anisotropy, Zeeman, longitudinal,
+        demag] -- for the moves of iteration `sweep` with `seed` (theta_deg < 0:
+        the chain's current cone angle)."""
+        out = np.zeros(6)
+        check(load().mmc_trial_terms(self._ctx, int(chain), int(sweep), int(seed), float(theta_deg), _dptr(out)),
+              "mmc_trial_terms")
+        return out
+
     def tables(self, chain=0):
         n = self.ncell[chain]
         me, chi, sg = np.zeros(n), np.zeros(n), np.zeros(n)
