@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -163,12 +164,29 @@ def nvtx_range(name):
         pass
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = ("k_sweep.cu", "k_demag.cu", "k_demag_il.cuh", "demag_il.h", "demag_args.cuh", "fft.cuh",
+                  "fft_il.cuh", "trial.cuh", "philox.cuh", "mmc_internal.h")
+
+
+def strip_comments(src):
+    """C/C++ source without its comments and trailing blanks (the kernel sources
+    hold no string literal with comment markers)."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())
+
+
+def kernel_source_hash(read=None):
+    """Hash of the code (comments excluded) of the timed kernels' sources: a
+    recorded ncu figure is used only when it was taken on the same code."""
     h = hashlib.sha256()
-    for f in ("k_sweep.cu", "k_demag.cu", "k_demag_il.cuh", "demag_il.h", "demag_args.cuh", "fft.cuh", "fft_il.cuh",
-              "trial.cuh", "philox.cuh", "mmc_internal.h"):
-        with open(os.path.join(ROOT, "paper_2106_05593_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for f in KERNEL_SOURCES:
+        if read is None:
+            with open(os.path.join(ROOT, "paper_2106_05593_gb300", "csrc", f)) as fh:
+                txt = fh.read()
+        else:
+            txt = read(f)
+        h.update(strip_comments(txt).encode())
     return h.hexdigest()[:16]
 
 
