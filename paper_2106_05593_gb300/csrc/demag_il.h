@@ -15,9 +15,10 @@ namespace mmc {
 // column kernel block reads and writes contiguous ny * CC runs.
 
 // kernel configurations: E elements per block, V values per thread (E / V
-// threads), MINB blocks per SM for the register budget.  Two FP32 variants
-// (radix 16 with 384 threads, radix 32 with 192 threads) are timed against each
-// other on the actual batch; FP64 uses radix 16.
+// threads), MINB blocks per SM for the register budget.  The three FP32
+// configurations (radix 16 with 768 threads; radix 32 with 384 threads; radix
+// 16 with 384 threads, two blocks per SM) are timed against each other on the
+// actual batch at create; FP64 uses radix 16 with 384 threads.
 struct CfgF16 { using R = float; static constexpr int E = 12288, V = 16, MINB = 1; };
 struct CfgF32 { using R = float; static constexpr int E = 12288, V = 32, MINB = 1; };
 struct CfgD16 { using R = double; static constexpr int E = 6144, V = 16, MINB = 1; };
