@@ -73,7 +73,7 @@ class RunState(C.Structure):
     _fields_ = [
         ("seed", C.c_uint64), ("chain", C.c_uint32), ("sweep", C.c_uint32),
         ("theta_deg", C.c_double), ("win_acc", C.c_int64), ("win_att", C.c_int64),
-        ("adapt", C.c_int), ("demag_mode", C.c_int),
+        ("adapt", C.c_int), ("demag_mode", C.c_int), ("stripes", C.c_int),
     ]
 
 
@@ -419,7 +419,7 @@ class Oracle:
         return mm.reshape(self.n, 3), nacc, obs
 
 
-def new_state(seed=1, chain=0, theta_deg=30.0, adapt=True, demag_mode=1, sweep=0):
+def new_state(seed=1, chain=0, theta_deg=30.0, adapt=True, demag_mode=1, sweep=0, stripes=1):
     st = RunState()
     st.seed = seed
     st.chain = chain
@@ -429,4 +429,5 @@ def new_state(seed=1, chain=0, theta_deg=30.0, adapt=True, demag_mode=1, sweep=0
     st.win_att = 0
     st.adapt = int(bool(adapt))
     st.demag_mode = demag_mode
+    st.stripes = int(stripes)
     return st

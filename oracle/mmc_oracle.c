@@ -924,13 +924,14 @@ static int trial(orc_ctx *c, double *m, const double *H, int q, uint32_t sweep, 
     return 0;
 }
 
-int64_t orc_pass(orc_ctx *c, double *m, const double *H, int color, uint32_t sweep,
-                 uint32_t chain, uint64_t seed, double theta_deg,
-                 int8_t *acc, double *dec, double *band)
+/* the cells of one colour in rows r0 <= j + ny k < r1 (a whole pass: 0, ny nz) */
+static int64_t pass_rows(orc_ctx *c, double *m, const double *H, int color, int r0, int r1, uint32_t sweep,
+                         uint32_t chain, uint64_t seed, double theta_deg,
+                         int8_t *acc, double *dec, double *band)
 {
     double cos_tc = cos(theta_deg * PI / 180.0);
     int64_t nacc = 0;
-    for (int q = 0; q < c->n; ++q) {
+    for (int q = r0 * c->p.nx; q < r1 * c->p.nx; ++q) {
         if (cell_color(c, q) != color) {
             if (acc) acc[q] = -1;
             if (dec) dec[q] = 0.0;
@@ -942,6 +943,16 @@ int64_t orc_pass(orc_ctx *c, double *m, const double *H, int color, uint32_t swe
         nacc += a;
     }
     return nacc;
+}
+
+int64_t orc_pass(orc_ctx *c, double *m, const double *H, int color, uint32_t sweep,
+                 uint32_t chain, uint64_t seed, double theta_deg,
+                 int8_t *acc, double *dec, double *band)
+{
+    if (acc) for (int q = 0; q < c->n; ++q) acc[q] = -1;
+    if (dec) for (int q = 0; q < c->n; ++q) dec[q] = 0.0;
+    if (band) for (int q = 0; q < c->n; ++q) band[q] = 0.0;
+    return pass_rows(c, m, H, color, 0, c->p.ny * c->p.nz, sweep, chain, seed, theta_deg, acc, dec, band);
 }
 
 /* App. B (Fig. 11): the size of each free-energy term of the trial moves.  For
@@ -1053,6 +1064,18 @@ int64_t orc_run(orc_ctx *c, double *m, int64_t n, orc_run_state *st, orc_obs *ob
                serial Metropolis sweep */
             if (H) orc_demag_field(c, m, H, method);
             acc = orc_serial_sweep(c, m, H, st->sweep, st->chain, st->seed, st->theta_deg);
+        } else if (st->demag_mode == 2 && st->stripes > 1) {
+            /* finer than per pass: each pass in `stripes` bands of rows, the
+               demag field recomputed before every band */
+            int nrows = c->p.ny * c->p.nz;
+            for (int color = 0; color < 2; ++color)
+                for (int k = 0; k < st->stripes; ++k) {
+                    int r0 = (int)((int64_t)k * nrows / st->stripes);
+                    int r1 = (int)((int64_t)(k + 1) * nrows / st->stripes);
+                    if (H) orc_demag_field(c, m, H, method);
+                    acc += pass_rows(c, m, H, color, r0, r1, st->sweep, st->chain, st->seed, st->theta_deg,
+                                     NULL, NULL, NULL);
+                }
         } else {
             if (H) orc_demag_field(c, m, H, method);
             acc += orc_pass(c, m, H, 0, st->sweep, st->chain, st->seed, st->theta_deg, NULL, NULL, NULL);

@@ -171,6 +171,8 @@ typedef struct {
     int64_t win_acc, win_att;   /* acceptance window counters */
     int adapt;                  /* adapt the cone angle every 100 sweeps */
     int demag_mode;             /* 0 off, 1 once per sweep, 2 before each pass, 3 serial (App. B) */
+    int stripes;                /* demag_mode 2: each pass in this many bands of rows
+                                   (j + ny k), the field recomputed before every band */
 } orc_run_state;
 
 /* n full sweeps; obs (may be NULL) accumulates a snapshot every obs_every sweeps */
