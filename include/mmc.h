@@ -119,6 +119,12 @@ typedef struct {
                                  batch at create and keep the fastest, 1 radix 16
                                  (768 threads), 2 radix 32 (384 threads), 3 radix
                                  16 (384 threads, two blocks per SM)            [0] */
+    int demag_stripes;        /* S > 1: each sublattice pass runs in S bands of rows
+                                 (j + ny k in [floor(b nrows / S), floor((b+1)
+                                 nrows / S))), the demag field recomputed before
+                                 every band: a schedule between demag before each
+                                 pass and the serial form (App. B).  0 or 1: whole
+                                 passes (demag_per_pass decides).                [1] */
 } mmc_options;
 
 /* One chain of a batch. T_cell (optional, HOST) gives a per-cell temperature;

@@ -712,8 +712,13 @@ SweepLaunch sweep_launch(mmc_ctx *c, int color, unsigned off, unsigned key0, uns
   P.omc_override = -1.f;
   P.dec_dbg = nullptr;
   P.acc_dbg = nullptr;
+  P.nstripes = 1;
+  P.stripe = 0;
   return P;
 }
+
+// bands of rows per sublattice pass (the demag field recomputed before each)
+int pass_bands(const mmc_ctx *c) { return c->any_demag && c->opt.demag_stripes > 1 ? c->opt.demag_stripes : 1; }
 
 ObsLaunch obs_launch(mmc_ctx *c, int accumulate) {
   ObsLaunch P;
@@ -799,14 +804,19 @@ void issue_block(mmc_ctx *c, int k, unsigned key0, unsigned key1, int sample_eve
       cudaStreamWaitEvent(g.stream, c->ev_fork, 0);
       Launch Lg{g.stream, &c->launches};
       const int b0 = (int)c->sw_first[(size_t)g.c0], nb = (int)(c->sw_first[(size_t)g.c1] - b0);
+      const int nbands = pass_bands(c);
       for (int off = 0; off < k; ++off) {
         for (int color = 0; color < 2; ++color) {
-          if (c->any_demag && (color == 0 || c->opt.demag_per_pass))
-            launch_demag(Lg, make_demag_launch(c, g.plan, c->d_heff, nullptr, -1), g.plan.fp64);
-          SweepLaunch P = sweep_launch(c, color, (unsigned)off, key0, key1);
-          P.blk_base = b0;
-          P.nblocks = nb;
-          launch_sweep_pass(Lg, P);
+          for (int band = 0; band < nbands; ++band) {
+            if (c->any_demag && ((color == 0 && band == 0) || c->opt.demag_per_pass || nbands > 1))
+              launch_demag(Lg, make_demag_launch(c, g.plan, c->d_heff, nullptr, -1), g.plan.fp64);
+            SweepLaunch P = sweep_launch(c, color, (unsigned)off, key0, key1);
+            P.blk_base = b0;
+            P.nblocks = nb;
+            P.nstripes = nbands;
+            P.stripe = band;
+            launch_sweep_pass(Lg, P);
+          }
         }
       }
       cudaEventRecord(g.done, g.stream);
@@ -816,22 +826,20 @@ void issue_block(mmc_ctx *c, int k, unsigned key0, unsigned key1, int sample_eve
     launch_advance(L, c->d_st, c->nchains, (unsigned)k, c->d_sweep_base, adapt_now, c->opt.adapt, 1.f, 180.f);
     return;
   }
+  const int nbands = pass_bands(c);
   for (int off = 0; off < k; ++off) {
-    if (c->any_demag) {
-      Trace t("demag");
-      issue_demag(c, pt);
-    }
-    {
-      Trace t("pass red");
-      timed(c, pt, 3, [&] { launch_sweep_pass(L, sweep_launch(c, 0, (unsigned)off, key0, key1)); });
-    }
-    if (c->any_demag && c->opt.demag_per_pass) {
-      Trace t("demag");
-      issue_demag(c, pt);
-    }
-    {
-      Trace t("pass black");
-      timed(c, pt, 3, [&] { launch_sweep_pass(L, sweep_launch(c, 1, (unsigned)off, key0, key1)); });
+    for (int color = 0; color < 2; ++color) {
+      for (int band = 0; band < nbands; ++band) {
+        if (c->any_demag && ((color == 0 && band == 0) || c->opt.demag_per_pass || nbands > 1)) {
+          Trace t("demag");
+          issue_demag(c, pt);
+        }
+        Trace t(color == 0 ? "pass red" : "pass black");
+        SweepLaunch P = sweep_launch(c, color, (unsigned)off, key0, key1);
+        P.nstripes = nbands;
+        P.stripe = band;
+        timed(c, pt, 3, [&] { launch_sweep_pass(L, P); });
+      }
     }
     if (sample_every > 0 && (start + off + 1) % (uint64_t)sample_every == 0) {
       Trace t("observables");
@@ -974,6 +982,7 @@ mmc_status mmc_default_options(mmc_options *o) {
   o->stream_groups = 0;
   o->demag_self = 0;
   o->fft_variant = 0;
+  o->demag_stripes = 1;
   return MMC_OK;
 }
 
@@ -1004,6 +1013,7 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
   if (!(o.hist_max > 0)) return fail(MMC_ERR_ARG, "hist_max must be > 0");
   if (!(o.sigma_cap > 0 && o.sigma_cap < 1)) return fail(MMC_ERR_ARG, "sigma_cap must be in (0, 1)");
   if (!(o.theta0_deg >= 1 && o.theta0_deg <= 180)) return fail(MMC_ERR_ARG, "theta0_deg must be in [1, 180]");
+  if (o.demag_stripes < 0 || o.demag_stripes > 64) return fail(MMC_ERR_ARG, "demag_stripes must be in [0, 64]");
   for (int i = 0; i < nchains; ++i) MMC_TRY(validate(chains[i], o, i));
   {
     bool any_pc = false, any_cubic = false;

@@ -39,6 +39,7 @@ struct SweepArgs {
   float omc_override;       // >= 0: use this 1 - cos(theta) (diagnostic pass)
   float *dec_dbg;
   signed char *acc_dbg;
+  int nstripes, stripe;     // nstripes > 1: the band of rows [r0, r1) of the stripe only
 };
 
 // A thread handles kSweepCells cells of its block's 256 slots (slot t + j 128):
@@ -64,6 +65,17 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 6) k_sweep_pass(S
   const float4 *mo = A.m + K.m_off + (long long)(1 - color) * S;
   const float omc = A.omc_override >= 0.f ? A.omc_override : A.st[c].omc;
   const unsigned sweep = *A.sweep_base + A.sweep_off;
+  // the slots of the pass: all, or the rows [r0, r1) of one band (the demag
+  // field is then recomputed between bands); a block outside the band leaves
+  // before any barrier
+  unsigned lo = 0, hi = S32;
+  if (A.nstripes > 1) {
+    const unsigned long long nr = (unsigned long long)K.nrows;
+    lo = (unsigned)((unsigned long long)A.stripe * nr / (unsigned)A.nstripes) * (unsigned)hx;
+    hi = (unsigned)((unsigned long long)(A.stripe + 1) * nr / (unsigned)A.nstripes) * (unsigned)hx;
+    const unsigned b0 = (unsigned)bd.y * (unsigned)kSweepBlock;
+    if (b0 >= hi || b0 + (unsigned)kSweepBlock <= lo) return;
+  }
 
   // 1. indices and loads of every cell of this thread
   bool valid[kSweepCells];
@@ -75,7 +87,7 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 6) k_sweep_pass(S
 #pragma unroll
   for (int e = 0; e < kSweepCells; ++e) {
     const unsigned q32 = q0 + (unsigned)(e * kSweepThreads);
-    bool ok = q32 < S32;
+    bool ok = q32 >= lo && q32 < hi;
     const int row = ok ? (int)divq(q32, K.hx_m, K.hx_l) : 0;
     const int s = (int)(q32 - (unsigned)row * (unsigned)hx);
     const int k = (int)divq((unsigned)row, K.ny_m, K.ny_l), j = row - k * ny;
@@ -157,6 +169,7 @@ void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
   A.m = P.m; A.heff = P.heff; A.tab = P.tab; A.sweep_base = P.sweep_base;
   A.sweep_off = P.sweep_off; A.key0 = P.key0; A.key1 = P.key1; A.color = P.color;
   A.omc_override = P.omc_override; A.dec_dbg = P.dec_dbg; A.acc_dbg = P.acc_dbg;
+  A.nstripes = P.nstripes; A.stripe = P.stripe;
   const bool dbg = P.dec_dbg != nullptr;
   if (P.percell) {
     if (dbg) k_sweep_pass<true, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A);

@@ -191,6 +191,7 @@ struct SweepLaunch {
   float omc_override;
   float *dec_dbg;
   signed char *acc_dbg;
+  int nstripes, stripe;         // nstripes > 1: only the band `stripe` of rows of every chain
 };
 void launch_sweep_pass(const Launch &L, const SweepLaunch &P);
 void launch_advance(const Launch &L, ChainState *st, int nchains, unsigned by, unsigned *sweep_base,

@@ -33,6 +33,8 @@ def test_hash_ignores_comments_only():
 
 def test_recorded_traffic_keyed_by_hash():
     b = _bench()
-    h = b.kernel_source_hash()
-    assert b.recorded_traffic("demag_cols", "chiral512", h) is not None
-    assert b.recorded_traffic("demag_cols", "chiral512", "0" * 16) is None
+    rows = [ln.split() for ln in open(os.path.join(ROOT, "profiles", "dram_traffic_per_launch.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    kernel, workload, h, value = rows[0][:4]
+    assert b.recorded_traffic(kernel, workload, h) == float(value)
+    assert b.recorded_traffic(kernel, workload, "0" * 16) is None
