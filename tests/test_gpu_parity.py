@@ -232,3 +232,27 @@ def test_angle_hist_matches_oracle(P, mesh, bins, lo, hi):
     assert np.allclose(d, do, rtol=0, atol=1e-14)
     assert h.sum() == n
     assert np.array_equal(h, ho)
+
+
+@pytest.mark.parametrize("mesh", [(2048, 6, 1), (6, 2048, 1), (2048, 4, 2)])
+def test_longest_transforms(P, mesh):
+    """Meshes whose padded length is the largest supported (4096) along x, along
+    y, and in 3D: FP64 field against the oracle, and one pass with each FP32
+    kernel variant (a variant that cannot hold a 4096-point row falls back)."""
+    n = int(np.prod(mesh))
+    spec = W._base(mesh, (2e-9, 2e-9, 2e-9), demag=True, Ms0=6e5, A0=1e-11, B=(0.01, 0.0, 0.0))
+    m4 = W.smooth_state(mesh, 2, 0.85)
+    o = O.Oracle(spec)
+    Ho = o.demag_field(m4[:, :3].astype(np.float64), "fft")
+    g = P.MMC(spec, demag=1)
+    g.set_m(m4)
+    err = np.abs(g.demag_field(0) - Ho).max() / np.abs(Ho).max()
+    print("longest transforms", mesh, err)
+    assert err < 1e-9
+    for variant in (1, 2, 3):
+        gv = P.MMC(spec, demag=1, fft_variant=variant)
+        for color in (0, 1):
+            gv.set_m(m4)
+            dec_g, acc_g = gv.pass_debug(0, color, 1, 4, 20.0)
+            _, acc_o, dec_o, band_o = oracle_pass(spec, m4, color, 1, 0, 4, 20.0, H=Ho, o=o)
+            compare_pass(dec_g, acc_g, dec_o, acc_o, band_o)

@@ -227,3 +227,4 @@ def test_minimizer_with_periodic_demag(P):
     mg = g.get_m()[:, :3].astype(np.float64)
     assert np.abs(mg - mo).max() < 2e-5
     assert r["energy"][0] == pytest.approx(o.energy(mo)[0], rel=1e-9)
+
