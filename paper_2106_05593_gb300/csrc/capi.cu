@@ -203,6 +203,7 @@ struct mmc_ctx {
   float *d_dec = nullptr;
   signed char *d_acc = nullptr;
   long long max_ncell = 0, max_slots = 0;
+  bool all_flat = true;                 // every chain one cell thick (nz == 1)
   long long launches = 0;
   uint64_t host_sweep = 0;
   bool heff_stale = true;               // state or field changed since the last demag update
@@ -714,6 +715,7 @@ SweepLaunch sweep_launch(mmc_ctx *c, int color, unsigned off, unsigned key0, uns
   P.acc_dbg = nullptr;
   P.nstripes = 1;
   P.stripe = 0;
+  P.flat = c->all_flat;
   return P;
 }
 
@@ -1049,6 +1051,7 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     c->any_percell |= c->hc[i].percell;
     c->max_ncell = std::max(c->max_ncell, c->hc[i].ncell);
     c->max_slots = std::max(c->max_slots, c->hc[i].slots);
+    c->all_flat = c->all_flat && chains[i].mesh.nz == 1;
   }
   // arenas
   long long moff = 0, toff = 0, msoff = 0, soff = 0;

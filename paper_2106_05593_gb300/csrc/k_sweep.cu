@@ -49,12 +49,18 @@ struct SweepArgs {
 constexpr int kSweepCells = 2;
 constexpr int kSweepThreads = kSweepBlock / kSweepCells;
 
-template <bool PERCELL, bool DEBUG>
-__global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 6) k_sweep_pass(SweepArgs A) {
+// FLAT: every chain of the launch is one cell thick (nz = 1), so the z
+// neighbours, their loads and registers drop out at compile time.  Seven
+// blocks per SM for uniform chains (72 registers): the pass waits on its cell
+// and neighbour loads, and the extra warps hide that latency better than six
+// blocks (80 registers) or eight (64 registers, more spills) did on GB300.
+template <bool PERCELL, bool DEBUG, bool FLAT>
+__global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 7) k_sweep_pass(SweepArgs A) {
   const int2 bd = A.blk_desc[A.blk_base + (int)blockIdx.x];
   const int c = bd.x;
   const ChainK K = load_chain(A.chains + c);
-  const int nx = K.nx, ny = K.ny, nz = K.nz, hx = K.hx;
+  const int nx = K.nx, ny = K.ny, nz = FLAT ? 1 : K.nz, hx = K.hx;
+  const int pbc = FLAT ? (K.pbc & 3) : K.pbc;
   // a chain has fewer than 2^31 cells: 32-bit slot arithmetic
   const unsigned S32 = (unsigned)K.nrows * (unsigned)hx;
   const long long S = (long long)S32;
@@ -90,7 +96,7 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 6) k_sweep_pass(S
     bool ok = q32 >= lo && q32 < hi;
     const int row = ok ? (int)divq(q32, K.hx_m, K.hx_l) : 0;
     const int s = (int)(q32 - (unsigned)row * (unsigned)hx);
-    const int k = (int)divq((unsigned)row, K.ny_m, K.ny_l), j = row - k * ny;
+    const int k = FLAT ? 0 : (int)divq((unsigned)row, K.ny_m, K.ny_l), j = row - k * ny;
     const int p = (j + k + color) & 1;
     const int i = 2 * s + p;
     ok = ok && (i < nx);
@@ -99,7 +105,7 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 6) k_sweep_pass(S
     cellid[e] = (unsigned)i + (unsigned)nx * (unsigned)row;
     if (ok) {
       a[e] = mc[q32];
-      load_neighbours(K.pbc, (flags & F_GRAIN) != 0, K.gscale, nx, ny, nz, hx, mo, a[e], i, j, k, row, s, p, nb[e], w[e]);
+      load_neighbours(pbc, (flags & F_GRAIN) != 0, K.gscale, nx, ny, nz, hx, mo, a[e], i, j, k, row, s, p, nb[e], w[e]);
       M[e] = cell_material<PERCELL>(K, A.tab, S, (long long)color * S + q32);
       if (flags & F_DEMAG) h[e] = A.heff[K.h_off + (long long)color * S + q32];
       else h[e] = make_float4(M[e].zee * K.Bx, M[e].zee * K.By, M[e].zee * K.Bz, 0.f);
@@ -118,7 +124,7 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 6) k_sweep_pass(S
     const float u0 = uniform01(r.x), u1 = uniform01(r.y), u2 = uniform01(r.z), u3 = uniform01(r.w);
     Move v = move_length(a[e], M[e].me2h, M[e].me2l);
     move_direction(v, a[e], M[e].sigma, omc, u0, u1, u2);
-    const float fex = exchange_change(v, a[e], nb[e], w[e], wx, wy, wz, nz > 1);
+    const float fex = exchange_change(v, a[e], nb[e], w[e], wx, wy, wz, !FLAT && nz > 1);
     const float flin = linear_change(v, nb[e], w[e], cdx, cdy, (flags & F_DMI) != 0, h[e].x, h[e].y, h[e].z);
     const float flong = longitudinal_change(v, M[e].p2, M[e].p4);
     const float fan = anisotropy_change(v, flags, M[e].k1, M[e].k2, M[e].ex, M[e].ey, M[e].ez);
@@ -170,13 +176,16 @@ void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
   A.sweep_off = P.sweep_off; A.key0 = P.key0; A.key1 = P.key1; A.color = P.color;
   A.omc_override = P.omc_override; A.dec_dbg = P.dec_dbg; A.acc_dbg = P.acc_dbg;
   A.nstripes = P.nstripes; A.stripe = P.stripe;
-  const bool dbg = P.dec_dbg != nullptr;
-  if (P.percell) {
-    if (dbg) k_sweep_pass<true, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A);
-    else k_sweep_pass<true, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A);
-  } else {
-    if (dbg) k_sweep_pass<false, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A);
-    else k_sweep_pass<false, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A);
+  const int v = (P.percell ? 4 : 0) | (P.dec_dbg != nullptr ? 2 : 0) | (P.flat ? 1 : 0);
+  switch (v) {
+    case 0: k_sweep_pass<false, false, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    case 1: k_sweep_pass<false, false, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    case 2: k_sweep_pass<false, true, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    case 3: k_sweep_pass<false, true, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    case 4: k_sweep_pass<true, false, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    case 5: k_sweep_pass<true, false, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    case 6: k_sweep_pass<true, true, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    default: k_sweep_pass<true, true, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
   }
   ++*L.counter;
 }

@@ -192,6 +192,7 @@ struct SweepLaunch {
   float *dec_dbg;
   signed char *acc_dbg;
   int nstripes, stripe;         // nstripes > 1: only the band `stripe` of rows of every chain
+  bool flat;                    // every chain has nz == 1
 };
 void launch_sweep_pass(const Launch &L, const SweepLaunch &P);
 void launch_advance(const Launch &L, ChainState *st, int nchains, unsigned by, unsigned *sweep_base,
