@@ -24,6 +24,8 @@ MUB = 9.2740100783e-24
 
 
 def default_options(**kw) -> Options:
+    """mmc_options with the library's defaults, overridden by keyword (field names
+    of mmc_options in include/mmc.h, e.g. demag=1, demag_images via the problem)."""
     o = Options()
     check(load().mmc_default_options(C.byref(o)), "mmc_default_options")
     for k, v in kw.items():
@@ -106,6 +108,7 @@ class MMC:
         self.ncell = [int(L.mmc_ncell(self._ctx, k)) for k in range(self.nchains)]
 
     def close(self):
+        """Release the context's device memory (mmc_destroy); idempotent."""
         if getattr(self, "_ctx", None):
             load().mmc_destroy(self._ctx)
             self._ctx = None
@@ -118,6 +121,7 @@ class MMC:
 
     # ------------------------------------------------------------------ state
     def set_field(self, B, chain=-1):
+        """Applied field B = mu0 H (tesla, 3 components) of one chain (chain < 0: all)."""
         b = np.asarray(B, dtype=np.float64).reshape(3)
         check(load().mmc_set_field(self._ctx, int(chain), _dptr(b)), "mmc_set_field")
 
@@ -142,6 +146,8 @@ class MMC:
         check(load().mmc_set_m(self._ctx, int(chain), a.ctypes.data_as(C.c_void_p), 0), "mmc_set_m")
 
     def get_m(self, chain=0, out=None):
+        """m of one chain as float32 (ncell, 4) in natural order (w: grain id); into
+        `out` when given (a host array or a CUDA torch tensor)."""
         if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
             check(load().mmc_get_m(self._ctx, int(chain), C.c_void_p(out.data_ptr()), 1), "mmc_get_m")
             return out
@@ -150,10 +156,14 @@ class MMC:
         return a
 
     def init_random(self, seed, length=0.0):
+        """Random directions for every chain (Philox counter (cell, 0, chain, 1));
+        |m| = length, or m_e (the Eq. 7 rms length where m_e = 0) when length <= 0."""
         check(load().mmc_init_random(self._ctx, int(seed), float(length)), "mmc_init_random")
 
     # ------------------------------------------------------------------ MC
     def sweep(self, n, seed):
+        """n MMC iterations of every chain (Sec. II): demag update, red pass, black
+        pass (per the options), cone adaptation every 100 iterations."""
         check(load().mmc_sweep(self._ctx, int(n), int(seed)), "mmc_sweep")
 
     def sweep_serial(self, n, seed):
@@ -175,12 +185,17 @@ class MMC:
                 "energy": E.copy()}
 
     def sweep_sampled(self, n, seed, every):
+        """Like sweep, accumulating an observables snapshot every `every` iterations."""
         check(load().mmc_sweep_sampled(self._ctx, int(n), int(seed), int(every)), "mmc_sweep_sampled")
 
     def demag_update(self):
+        """Recompute the demag field (Eq. 14) of every chain from the current state."""
         check(load().mmc_demag_update(self._ctx), "mmc_demag_update")
 
     def pass_debug(self, chain, color, sweep, seed, theta_deg):
+        """One sublattice pass of one chain with explicit iteration index and cone
+        angle; returns the FP32 decision values and accept flags per cell (natural
+        order; -1 for cells of the other colour).  The state is updated."""
         n = self.ncell[chain]
         dec = np.zeros(n, dtype=np.float32)
         acc = np.zeros(n, dtype=np.int8)
@@ -191,6 +206,9 @@ class MMC:
 
     # ------------------------------------------------------------------ measurements
     def observables(self, chain=0, reset=False):
+        """Averages over the accumulated snapshots, or over the current state when
+        there are none: <m>, <|m|>, <|m|^2>, |m| histogram, acceptance rate of the
+        last window, cone angle, iteration count, non-finite count."""
         bins = self.options.hist_bins
         hist = np.zeros(bins + 1, dtype=np.int64)
         o = Obs()
@@ -201,11 +219,14 @@ class MMC:
                 "theta_deg": o.theta_deg, "sweeps": o.sweeps, "hist": hist}
 
     def energy(self, chain=0):
+        """Energy terms of the current state (J): total, exchange, DMI, anisotropy,
+        Zeeman, longitudinal, demag (FP64 convolution)."""
         out = np.zeros(7)
         check(load().mmc_energy(self._ctx, int(chain), _dptr(out)), "mmc_energy")
         return out
 
     def demag_field(self, chain=0):
+        """Demag field H_d (A/m) of the current state, FP64 convolution, (ncell, 3)."""
         H = np.zeros(3 * self.ncell[chain])
         check(load().mmc_demag_field(self._ctx, int(chain), _dptr(H)), "mmc_demag_field")
         return H.reshape(-1, 3)
@@ -230,6 +251,7 @@ class MMC:
         return out
 
     def tables(self, chain=0):
+        """Per-cell m_e(T), chi(T) (Eqs. 8-9) and the length-move width sigma (Eq. 13)."""
         n = self.ncell[chain]
         me, chi, sg = np.zeros(n), np.zeros(n), np.zeros(n)
         check(load().mmc_tables(self._ctx, int(chain), _dptr(me), _dptr(chi), _dptr(sg)), "mmc_tables")
@@ -275,9 +297,13 @@ class MMC:
 
     @property
     def launches(self) -> int:
+        """Kernels the context has launched (graph replays counted per kernel)."""
         return int(load().mmc_kernel_launches(self._ctx))
 
     def checkpoint(self) -> bytes:
+        """The whole mutable state (moments, per-chain counters, cone angles, sweep
+        counter) as bytes; restore() on a context of the same problem resumes it
+        bit for bit."""
         L = load()
         n = C.c_size_t(0)
         check(L.mmc_checkpoint(self._ctx, None, C.byref(n)), "mmc_checkpoint")
@@ -286,5 +312,6 @@ class MMC:
         return bytes(buf)
 
     def restore(self, data: bytes):
+        """Resume a checkpoint taken on a context of the same problem."""
         buf = C.create_string_buffer(data, len(data))
         check(load().mmc_restore(self._ctx, buf, len(data)), "mmc_restore")
