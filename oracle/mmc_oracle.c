@@ -27,6 +27,17 @@
  *                        field of a cosine magnetization in a film infinite in
  *                        the plane (closed form of the charge sheets, summed over
  *                        the cell aliases); half-period offsets by hand
+ *   serial form (App. B) per-move field updates equal the direct sum of the final
+ *                        state; without demag equal to pass-by-pass application
+ *   row bands            one band = demag before each pass; without demag any
+ *                        banding equals the plain iteration
+ *   trial-term sizes     exchange and Zeeman means of a uniform state equal their
+ *                        closed forms over the proposal (App. B, Fig. 11)
+ *   SDesc (Sec. III)     Stoner-Wohlfarth angle of a single cell; torque criterion
+ *   angle histogram      cap and sphere densities (Fig. 1d-f)
+ *
+ * Parity unpinned: equilibria of interacting chains (only GPU-oracle agreement
+ * within standard errors is available).
  */
 #include "mmc_oracle.h"
 
