@@ -487,7 +487,8 @@ void fill_percell_tables(const ChainHost &H, const ChainDev &D, float4 *tab, flo
       tab[si] = make_float4((float)(et[0] / kT), (float)(et[1] / kT), (float)et[2], (float)H.sigma[(size_t)nat]);
       tab[2 * S + si] =
           make_float4((float)(H.V * et[3] / kT), (float)(H.V * et[4] / kT), (float)(H.V * et[5] / kT), bs);
-      tab[4 * S + si] = make_float4((float)et[6], (float)et[7], (float)et[8], 0.f);
+      // m_e^2 as a float-float pair (high part in the first table, low part here)
+      tab[4 * S + si] = make_float4((float)et[6], (float)et[7], (float)et[8], (float)(et[2] - (double)(float)et[2]));
       ms[si] = (float)et[3];
     }
 }

@@ -54,14 +54,15 @@ struct CellMat {
   float p2, p4, me2h, me2l, sigma, zee, k1, k2, ex, ey, ez, bs;
 };
 
-// off = colour * S + slot; per-cell tables are 3 float4 arrays of 2 S entries
+// off = colour * S + slot; per-cell tables are 3 float4 arrays of 2 S entries:
+// {p2, p4, m_e^2 (high part), sigma}, {zee, k1, k2, bond scale}, {e_A, m_e^2 low part}
 template <bool PERCELL, typename CH>
 __device__ __forceinline__ CellMat cell_material(const CH &ch, const float4 *tab, long long S, long long off) {
   CellMat M;
   if (PERCELL) {
     const float4 *tb = tab + ch.t_off;
     const float4 t0 = tb[off], t1 = tb[2 * S + off], t2 = tb[4 * S + off];
-    M.p2 = t0.x; M.p4 = t0.y; M.me2h = t0.z; M.me2l = 0.f; M.sigma = t0.w;
+    M.p2 = t0.x; M.p4 = t0.y; M.me2h = t0.z; M.me2l = t2.w; M.sigma = t0.w;
     M.zee = t1.x; M.k1 = t1.y; M.k2 = t1.z; M.bs = t1.w;
     M.ex = t2.x; M.ey = t2.y; M.ez = t2.z;
   } else {

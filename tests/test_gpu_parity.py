@@ -157,8 +157,7 @@ def test_granular_per_cell_chain(P):
         g.set_m(m4)
         dec_g, acc_g = g.pass_debug(0, color, 2, 5, 30.0)
         _, acc_o, dec_o, band_o = oracle_pass(spec, m4, color, 2, 0, 5, 30.0)
-        # per-cell m_e^2 is stored in FP32 (no float-float pair): wider absolute bound
-        print("granular", color, compare_pass(dec_g, acc_g, dec_o, acc_o, band_o, absolute=5e-4))
+        print("granular", color, compare_pass(dec_g, acc_g, dec_o, acc_o, band_o))
 
 
 def test_mixed_batch_of_uniform_and_per_cell_chains(P):
@@ -174,8 +173,7 @@ def test_mixed_batch_of_uniform_and_per_cell_chains(P):
             g.set_m(m4, k)
             dec_g, acc_g = g.pass_debug(k, color, 4, 77, 35.0)
             _, acc_o, dec_o, band_o = oracle_pass(sp, m4, color, 4, k, 77, 35.0)
-            # per-cell m_e^2 is stored in FP32 (no float-float pair): wider absolute bound
-            compare_pass(dec_g, acc_g, dec_o, acc_o, band_o, absolute=5e-4)
+            compare_pass(dec_g, acc_g, dec_o, acc_o, band_o)
 
 
 def test_pass_updates_exactly_the_accepted_cells(P):

@@ -207,8 +207,7 @@ def test_granular_periodic_chain(P):
         g.set_m(m4)
         dec_g, acc_g = g.pass_debug(0, color, 3, 9, 30.0)
         _, acc_o, dec_o, band_o = oracle_pass(spec, m4, color, 3, 0, 9, 30.0, H=Ho, o=o)
-        # per-cell m_e^2 is stored in FP32 (no float-float pair): wider absolute bound
-        compare_pass(dec_g, acc_g, dec_o, acc_o, band_o, absolute=5e-4)
+        compare_pass(dec_g, acc_g, dec_o, acc_o, band_o)
 
 
 def test_minimizer_with_periodic_demag(P):

@@ -1,7 +1,6 @@
 """GPU parity of the per-term size of the trial moves (App. B, Fig. 11) against
 the oracle: the same state, random numbers, cone angle and frozen field give the
-same mean |dF| / kT per term (FP32 terms against FP64: 2e-4 relative per term,
-2e-3 for per-cell chains whose m_e^2 is stored in FP32)."""
+same mean |dF| / kT per term (FP32 terms against FP64: 2e-4 relative per term)."""
 import numpy as np
 import pytest
 
@@ -27,7 +26,7 @@ CASES = {
     "film3d": (full_spec((12, 10, 4), demag=True), 2e-4),
     "periodic": (full_spec((32, 32, 1), demag=True, pbc=(True, True, False)) | {"demag_images": 3}, 2e-4),
     "cubic": (full_spec((20, 16, 2)) | {"aniso": "cubic", "K1": 4.8e5, "K2": -1e5}, 2e-4),
-    "granular": (W.granular_chain(40, 3), 2e-3),
+    "granular": (W.granular_chain(40, 3), 2e-4),
 }
 
 
