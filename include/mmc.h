@@ -366,6 +366,28 @@ int64_t mmc_kernel_launches(const mmc_ctx *ctx);
 int mmc_nchains(const mmc_ctx *ctx);
 int64_t mmc_ncell(const mmc_ctx *ctx, int chain);
 
+/* The demag kernel the library convolves with (Sec. III, Eq. 14), computed on the
+ * host in FP64 without a context or a GPU: the Newell tensor of cells of size h
+ * (m) at cell offsets (x, y, z), 0 <= x < ox, 0 <= y < oy, 0 <= z < oz, or, along
+ * the axes with periodic[a] != 0 and images > 0, its sum over `images` periodic
+ * images of extent n[a] on each side (mmc_mesh.demag_images).  out (HOST,
+ * 6 ox oy oz doubles) receives xx yy zz xy xz yz of offset (x, y, z) at
+ * out[6 (x + ox (y + oy z)) + c].  MMC_ERR_ARG: null pointers, non-positive
+ * sizes, extents or counts, images outside [0, 64], more than 2^24 offsets. */
+mmc_status mmc_demag_kernel(const double h[3], const int n[3], const int periodic[3], int images, int ox, int oy,
+                            int oz, double *out);
+
+/* The thermodynamic tables the library builds (Sec. II), computed on the host in
+ * FP64 without a context or a GPU: for each of n temperatures T[i] (K), m_e
+ * (Eq. 9), chi (Eq. 8, 1/T), the length-move width sigma (Eq. 13, capped at
+ * sigma_cap, the cap at and above Tc) and the coefficients c2, c4 of the Eq. 7
+ * free energy F = c2 m^2 + c4 m^4 + const (J) of a cell of volume V (m^3) with
+ * Ms0 (A/m), Curie temperature Tc and atomic moment mu (J/T; <= 0: one Bohr
+ * magneton).  Output arrays (HOST, n values) may be NULL.  MMC_ERR_ARG: T <= 0,
+ * Tc, V or Ms0 <= 0, sigma_cap outside (0, 1), n < 0, a null T with n > 0. */
+mmc_status mmc_thermo(const double *T, int n, double Tc, double mu, double V, double Ms0, double sigma_cap,
+                      double *me, double *chi, double *sigma, double *c2, double *c4);
+
 /* Checkpoint: serialize the full chain state (m of all chains, sweep counter,
  * cone angle, window counters, applied fields) into buf.  With buf == NULL only
  * *len is set to the required size.  mmc_restore accepts a buffer from a context

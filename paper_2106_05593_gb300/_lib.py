@@ -20,7 +20,7 @@ EXPORTS = [
     "mmc_default_options", "mmc_create", "mmc_create_single", "mmc_destroy", "mmc_set_field",
     "mmc_set_m", "mmc_get_m", "mmc_init_random", "mmc_sweep", "mmc_sweep_sampled",
     "mmc_demag_update", "mmc_pass_debug", "mmc_observables", "mmc_energy", "mmc_demag_field",
-    "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_fft_tuning", "mmc_sweep_serial", "mmc_minimize", "mmc_set_temperature", "mmc_angle_hist", "mmc_trial_terms", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell",
+    "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_fft_tuning", "mmc_sweep_serial", "mmc_minimize", "mmc_set_temperature", "mmc_angle_hist", "mmc_trial_terms", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell", "mmc_demag_kernel", "mmc_thermo",
     "mmc_checkpoint", "mmc_restore", "mmc_observables_noalloc", "mmc_status_str", "mmc_last_error",
 ]
 
@@ -135,6 +135,11 @@ def load():
     L.mmc_kernel_launches.argtypes = [vp]
     L.mmc_nchains.restype = C.c_int
     L.mmc_nchains.argtypes = [vp]
+    ip = C.POINTER(C.c_int)
+    L.mmc_demag_kernel.restype = st
+    L.mmc_demag_kernel.argtypes = [dp, ip, ip, C.c_int, C.c_int, C.c_int, C.c_int, dp]
+    L.mmc_thermo.restype = st
+    L.mmc_thermo.argtypes = [dp, C.c_int] + [C.c_double] * 5 + [dp] * 5
     L.mmc_ncell.restype = C.c_int64
     L.mmc_ncell.argtypes = [vp, C.c_int]
     L.mmc_checkpoint.restype = st

@@ -1882,6 +1882,48 @@ mmc_status mmc_fft_tuning(const mmc_ctx *c, int *variant, double ms[3]) {
   return MMC_OK;
 }
 int mmc_nchains(const mmc_ctx *c) { return c ? c->nchains : 0; }
+
+mmc_status mmc_demag_kernel(const double h[3], const int n[3], const int periodic[3], int images, int ox, int oy,
+                            int oz, double *out) {
+  if (!h || !n || !periodic || !out) return fail(MMC_ERR_ARG, "null argument");
+  for (int a = 0; a < 3; ++a) {
+    if (!(h[a] > 0.0)) return fail(MMC_ERR_ARG, "cell size must be > 0");
+    if (n[a] < 1) return fail(MMC_ERR_ARG, "extents must be >= 1");
+  }
+  if (images < 0 || images > kMaxDemagImages) return fail(MMC_ERR_ARG, "images must be in [0, 64]");
+  if (ox < 1 || oy < 1 || oz < 1) return fail(MMC_ERR_ARG, "offset counts must be >= 1");
+  if (1LL * ox * oy * oz > (1LL << 24)) return fail(MMC_ERR_ARG, "more than 2^24 offsets");
+  DemagPeriodic pd;
+  for (int a = 0; a < 3; ++a) {
+    pd.n[a] = n[a];
+    pd.per[a] = periodic[a] ? 1 : 0;
+  }
+  pd.images = images;
+  std::vector<double> oct;
+  demag_octant(h, ox, oy, oz, oct, pd);
+  std::memcpy(out, oct.data(), oct.size() * sizeof(double));
+  return MMC_OK;
+}
+
+mmc_status mmc_thermo(const double *T, int n, double Tc, double mu, double V, double Ms0, double sigma_cap,
+                      double *me, double *chi, double *sigma, double *c2, double *c4) {
+  if (n < 0 || (n > 0 && !T)) return fail(MMC_ERR_ARG, "need n >= 0 temperatures");
+  if (!(Tc > 0.0) || !(V > 0.0) || !(Ms0 > 0.0)) return fail(MMC_ERR_ARG, "Tc, V and Ms0 must be > 0");
+  if (!(sigma_cap > 0.0 && sigma_cap < 1.0)) return fail(MMC_ERR_ARG, "sigma_cap must be in (0, 1)");
+  for (int i = 0; i < n; ++i)
+    if (!(T[i] > 0.0)) return fail(MMC_ERR_ARG, "T must be > 0");
+  const double m = mu > 0.0 ? mu : muB;
+  for (int i = 0; i < n; ++i) {
+    if (me) me[i] = me_of_T(T[i], Tc);
+    if (chi) chi[i] = chi_of_T(T[i], Tc, m);
+    if (sigma) sigma[i] = sigma_of_T(T[i], Tc, m, V, Ms0, sigma_cap);
+    double a = 0.0, b = 0.0;
+    long_coeffs(T[i], Tc, m, V, Ms0, &a, &b);
+    if (c2) c2[i] = a;
+    if (c4) c4[i] = b;
+  }
+  return MMC_OK;
+}
 int64_t mmc_ncell(const mmc_ctx *c, int chain) {
   if (!c || chain < 0 || chain >= c->nchains) return 0;
   return c->hc[chain].ncell;

@@ -39,6 +39,33 @@ def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def thermo(T, Tc, V, Ms0, mu=MUB, sigma_cap=0.03):
+    """The library's thermodynamic tables on the host, no GPU (Sec. II): dict of
+    arrays m_e (Eq. 9), chi (Eq. 8), sigma (Eq. 13) and the Eq. 7 coefficients
+    c2, c4 (F = c2 m^2 + c4 m^4 + const, J) at the temperatures T."""
+    t = np.ascontiguousarray(np.atleast_1d(T), dtype=np.float64)
+    n = t.size
+    out = {k: np.zeros(n) for k in ("me", "chi", "sigma", "c2", "c4")}
+    check(load().mmc_thermo(_dptr(t), n, float(Tc), float(mu), float(V), float(Ms0), float(sigma_cap),
+                            *[_dptr(out[k]) for k in ("me", "chi", "sigma", "c2", "c4")]), "mmc_thermo")
+    return out
+
+
+def demag_kernel(h, n, periodic=(0, 0, 0), images=0, offsets=None):
+    """The library's demag kernel (Sec. III, Eq. 14) on the host, no GPU: an array
+    (oz, oy, ox, 6) of xx yy zz xy xz yz at cell offsets 0 <= x < ox, ...
+    (offsets = (ox, oy, oz), default n), periodic along the flagged axes with
+    `images` images per side."""
+    ox, oy, oz = n if offsets is None else offsets
+    out = np.zeros(6 * ox * oy * oz)
+    nn = (C.c_int * 3)(*[int(v) for v in n])
+    pp = (C.c_int * 3)(*[int(bool(v)) for v in periodic])
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    check(load().mmc_demag_kernel(_dptr(hh), nn, pp, int(images), int(ox), int(oy), int(oz), _dptr(out)),
+          "mmc_demag_kernel")
+    return out.reshape(oz, oy, ox, 6)
+
+
 def _percell(v, n, width=1):
     a = np.asarray(v, dtype=np.float64)
     if a.size == width:
