@@ -258,6 +258,25 @@ def crop_spec(spec, side=CPU_SAMPLE_SIDE):
     return out, note + "corner block of chain 0"
 
 
+def host_description():
+    """Host cores (nproc) and CPU model name (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model and os.path.exists("/proc/cpuinfo"):
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    return {"host_cores": os.cpu_count(), "cpu_model": model}
+
+
 def cpu_baseline(specs, demag, nsweeps=3):
     """FP64 oracle, one thread, one chain of the workload (its corner block
     when larger than 512 x 512 in-plane) for a few iterations."""
@@ -271,7 +290,7 @@ def cpu_baseline(specs, demag, nsweeps=3):
     t0 = time.perf_counter()
     o.run(m, nsweeps, st)
     dt = time.perf_counter() - t0
-    return {"value": n * nsweeps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": n * nsweeps / dt, "unit": UNIT, "cores": 1, "kind": "oracle", **host_description(),
             "sample": f"{what} of the workload "
                       f"({spec['mesh'][0]}x{spec['mesh'][1]}x{spec['mesh'][2]}), "
                       f"{nsweeps} iterations after 1 warm-up, demag {'FFT FP64' if demag else 'off'}"}
@@ -327,12 +346,66 @@ def run_reference(args):
                        "sample": f"{what} "
                                  f"({spec['mesh'][0]}x{spec['mesh'][1]}x{spec['mesh'][2]}), "
                                  "one MMC iteration per step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", **host_description(),
                              "sample": f"{what} of {args.workload} "
                                        f"({spec['mesh'][0]}x{spec['mesh'][1]}x{spec['mesh'][2]}), "
                                        f"{per} iteration per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def fp64_demag_compare(MMC, specs, seed, stream, cells_per_step, steps=2):
+    """The FP64-demag form of the workload (demag FFT convolution in FP64, the
+    sweep in FP32): whole-batch rate over `steps` steps, the demag update time,
+    and the largest difference of the Eq. 5 decision values (kT) of one pass of
+    chain 0 between the FP32 and the FP64 convolution on the same state (the FP64
+    convolution equals the oracle's to 1e-9 relative in the parity tests)."""
+    import torch
+    g64 = MMC(specs, demag=1, demag_fp64=1, stream=stream)
+    g64.init_random(seed)
+    g64.sweep(SWEEPS_PER_STEP, seed)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        g64.sweep(SWEEPS_PER_STEP, seed)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    ph = g64.phase_times(10, seed)
+    upd = sum(ph[k][0] for k in ("demag_rows_fwd", "demag_cols", "demag_rows_inv")) / max(ph["demag_cols"][1], 1)
+    m4 = g64.get_m(0)
+    g32 = MMC(specs[:1], demag=1, stream=stream)
+    g1 = MMC(specs[:1], demag=1, demag_fp64=1, stream=stream)
+    dd = 0.0
+    for color in (0, 1):
+        decs = []
+        for gg in (g32, g1):
+            gg.set_m(m4)
+            decs.append(gg.pass_debug(0, color, 7, seed, 20.0)[0])
+        dd = max(dd, float(np.abs(decs[0].astype(np.float64) - decs[1]).max()))
+    return {"value": cells_per_step * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "demag_update_ms": upd, "decision_value_max_diff_fp32_vs_fp64_kT": dd}
+
+
+def batched_plain_identity(MMC, specs, demag, args, variant, seed, stream, iters=100):
+    """Batched and plain forms at equal accuracy: one-chain contexts given
+    chain_base = k run chain k's Markov chain; after `iters` iterations from the
+    same random start every chain's state equals the batch's bit for bit."""
+    b = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=variant, stream=stream)
+    b.init_random(seed)
+    b.sweep(iters, seed)
+    same = 0
+    for k, sp in enumerate(specs):
+        p = MMC([sp], demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=variant, chain_base=k,
+                stream=stream)
+        p.init_random(seed)
+        p.sweep(iters, seed)
+        same += int(np.array_equal(p.get_m(0), b.get_m(k)))
+        p.close()
+    return {"identical_chains": same, "chains": len(specs), "iterations": iters,
+            "note": "plain context k with chain_base = k is chain k of the batch (same random numbers)"}
 
 
 def run_ours(args):
@@ -433,6 +506,9 @@ def run_ours(args):
             # padded-size group, so divide by the updates, not by the marks
             cfm = sum(ph[k][0] for k in kinds) / 20.0
             compare["demag_update_ms"] = {"own": own, "cufft": cfm}
+            if not args.fp64_demag:
+                compare["fp64_demag"] = fp64_demag_compare(MMC, specs, seed, stream, cells_per_step)
+                compare["demag_update_ms"]["own_fp64"] = compare["fp64_demag"]["demag_update_ms"]
             v, tms = g.fft_tuning()
             compare["fft_variant"] = {"picked": {0: None, 1: "radix16", 2: "radix32", 3: "radix16x2"}[v],
                                       "create_time_ms": {"radix16": tms[0], "radix32": tms[1],
@@ -457,7 +533,8 @@ def run_ours(args):
             pms = p0.elapsed_time(p1e)
             compare["plain_one_chain_per_launch"] = {
                 "value": cells_per_step * steps_p / (pms * 1e-3), "unit": UNIT, "steps": steps_p,
-                "batched_over_plain": value / world / (cells_per_step * steps_p / (pms * 1e-3))}
+                "batched_over_plain": value / world / (cells_per_step * steps_p / (pms * 1e-3)),
+                "agreement": batched_plain_identity(MMC, specs, demag, args, g.fft_tuning()[0], seed, stream)}
             del plain
 
     # end to end through the public API: state from pinned host memory, observables back

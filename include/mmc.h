@@ -32,7 +32,8 @@
  *    stream).  Calls that return results to host memory synchronize that stream.
  *  - A context holds nchains independent Markov chains ("batch"); a plain
  *    single-chain context is a batch of one.  Chains advance in lockstep: one
- *    sweep counter, one seed; Philox counter word 2 carries the chain index.
+ *    sweep counter, one seed; Philox counter word 2 carries the chain index
+ *    (plus mmc_options.chain_base).
  */
 #ifndef MMC_H
 #define MMC_H
@@ -125,6 +126,12 @@ typedef struct {
                                  every band: a schedule between demag before each
                                  pass and the serial form (App. B).  0 or 1: whole
                                  passes (demag_per_pass decides).                [1] */
+    int chain_base;           /* Philox counter word 2 of chain c is chain_base + c
+                                 (>= 0, chain_base + nchains < 2^31): a one-chain
+                                 context with chain_base = c draws the random
+                                 numbers of chain c of a batch, so the plain and
+                                 batched forms of the same chain are the same
+                                 Markov chain, bit for bit.                      [0] */
 } mmc_options;
 
 /* One chain of a batch. T_cell (optional, HOST) gives a per-cell temperature;
@@ -408,12 +415,17 @@ mmc_status mmc_restore(mmc_ctx *ctx, const void *buf, size_t len);
  *        cells, the number of non-finite cells, the number of finite cells, 0;
  *   hist DEVICE, hist_bins + 1 counters of |m| on [0, hist_max) (last =
  *        overflow), cleared by the call.
- * Work is queued on cuda_stream (a cudaStream_t, or NULL for the legacy
- * stream); the call does not synchronize.  Scratch for the per-block partial
+ * m must be 16-byte aligned and out, hist 8-byte aligned (MMC_ERR_ARG
+ * otherwise, with nothing launched).
+ * Work is queued on cuda_stream (a cudaStream_t of the current device, or NULL
+ * for the legacy stream; a stream of another device is MMC_ERR_ARG); the call
+ * does not synchronize.  Scratch for the per-block partial
  * sums is a fixed 128 KiB __device__ array inside the library, so n is limited
  * to 2,097,152 cells (MMC_ERR_ARG beyond that, with nothing launched).  The
  * first call on each device looks up that array's device address with the
- * device current; make that first call before any stream capture.  All calls
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not use this entry point after a
+ * reset of the device (cudaDeviceReset), which invalidates the kept address.  All calls
  * on a device share the array: calls whose kernels may overlap on the GPU
  * (different streams without ordering) race and give wrong results.  Every
  * call overwrites the partials it reads, so no clearing is needed between

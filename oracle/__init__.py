@@ -128,7 +128,7 @@ def lib():
         L.orc_run.restype = C.c_int64
         L.orc_run.argtypes = [C.c_void_p, dp, C.c_int64, C.POINTER(RunState), C.POINTER(_Obs), C.c_int]
         L.orc_obs_accumulate.argtypes = [C.c_void_p, dp, C.POINTER(_Obs)]
-        L.orc_hist_f32.argtypes = [C.POINTER(C.c_float), C.c_int64, C.c_int, C.c_float, C.POINTER(C.c_int64)]
+        L.orc_hist.argtypes = [dp, C.c_int64, C.c_int, C.c_double, C.POINTER(C.c_int64)]
         L.orc_adapt_theta.restype = C.c_double
         L.orc_adapt_theta.argtypes = [C.c_double, C.c_int64, C.c_int64]
         L.orc_init_state.argtypes = [C.c_void_p, dp, C.c_int, dp, C.c_double, C.c_uint32, C.c_uint64]
@@ -208,12 +208,13 @@ def adapt_theta(theta, acc, att):
     return lib().orc_adapt_theta(float(theta), int(acc), int(att))
 
 
-def hist_f32(m4, bins=200, hmax=1.0):
-    m4 = np.ascontiguousarray(m4, dtype=np.float32).reshape(-1, 4)
-    hist = np.zeros(bins + 1, dtype=np.int64)
-    lib().orc_hist_f32(m4.ctypes.data_as(C.POINTER(C.c_float)), m4.shape[0], int(bins),
-                       float(hmax), hist.ctypes.data_as(C.POINTER(C.c_int64)))
-    return hist
+def hist(m, bins=200, hmax=1.0):
+    """|m| histogram of a state (Sec. II, Figs. 1-2), FP64: `bins` equal bins on
+    [0, hmax) and the lengths at or beyond hmax in the last of bins + 1 entries."""
+    mm = np.ascontiguousarray(np.asarray(m, dtype=np.float64)[..., :3]).reshape(-1)
+    h = np.zeros(bins + 1, dtype=np.int64)
+    lib().orc_hist(_dp(mm), mm.size // 3, int(bins), float(hmax), h.ctypes.data_as(C.POINTER(C.c_int64)))
+    return h
 
 
 # --------------------------------------------------------------------------- #

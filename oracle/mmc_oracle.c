@@ -1047,17 +1047,17 @@ void orc_obs_accumulate(const orc_ctx *c, const double *m, orc_obs *obs)
     obs->nsnap += 1;
 }
 
-/* |m| in FP32 as r = sqrt(fma(z,z,fma(y,y,x*x))), bin = (int)(r * (bins/hmax)) */
-void orc_hist_f32(const float *m4, int64_t n, int bins, float hmax, int64_t *hist)
+/* Sec. II (Figs. 1-2): histogram of the vector lengths |m| of a state, in bins
+ * equal bins on [0, hmax), lengths at or beyond hmax counted in hist[bins].
+ * FP64: |m| = sqrt(x^2 + y^2 + z^2), bin = floor(|m| bins / hmax). */
+void orc_hist(const double *m, int64_t n, int bins, double hmax, int64_t *hist)
 {
-    float scale = (float)bins / hmax;
+    for (int b = 0; b <= bins; ++b) hist[b] = 0;
     for (int64_t q = 0; q < n; ++q) {
-        float x = m4[4 * q], y = m4[4 * q + 1], z = m4[4 * q + 2];
-        float xx = x * x;
-        float r2 = fmaf(z, z, fmaf(y, y, xx));
-        float r = sqrtf(r2);
-        float t = r * scale;
-        int b = (t >= (float)bins) ? bins : (int)t;
+        const double *v = m + 3 * q;
+        double len = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        double t = len / hmax * bins;
+        int b = t >= (double)bins ? bins : (int)t;
         hist[b] += 1;
     }
 }

@@ -178,8 +178,8 @@ typedef struct {
 /* n full sweeps; obs (may be NULL) accumulates a snapshot every obs_every sweeps */
 int64_t orc_run(orc_ctx *c, double *m, int64_t n, orc_run_state *st, orc_obs *obs, int obs_every);
 void    orc_obs_accumulate(const orc_ctx *c, const double *m, orc_obs *obs);
-/* |m| histogram of an FP32 state with the same FP32 operation order as the product */
-void    orc_hist_f32(const float *m4, int64_t n, int bins, float hmax, int64_t *hist);
+/* |m| histogram of a state in FP64: bins equal bins on [0, hmax), overflow last */
+void    orc_hist(const double *m, int64_t n, int bins, double hmax, int64_t *hist);
 /* cone angle adaptation rule (Sec. II) */
 double  orc_adapt_theta(double theta_deg, int64_t acc, int64_t att);
 /* initial state: uniform direction dir with length len, or random directions

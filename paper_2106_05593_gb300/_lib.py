@@ -53,7 +53,7 @@ class Options(C.Structure):
         ("demag_cufft", C.c_int), ("adapt", C.c_int), ("theta0_deg", C.c_double),
         ("sigma_cap", C.c_double), ("hist_bins", C.c_int), ("hist_max", C.c_double),
         ("use_graphs", C.c_int), ("stream_groups", C.c_int), ("demag_self", C.c_int), ("fft_variant", C.c_int),
-        ("demag_stripes", C.c_int),
+        ("demag_stripes", C.c_int), ("chain_base", C.c_int),
     ]
 
 

@@ -418,7 +418,7 @@ void build_chain(ChainHost &H, ChainDev &D, const mmc_chain_desc &d, const mmc_o
   std::memset(&D, 0, sizeof(D));
   D.nx = nx; D.ny = ny; D.nz = nz; D.hx = hx; D.nrows = ny * nz;
   D.pbc = (d.mesh.periodic[0] ? 1 : 0) | (d.mesh.periodic[1] ? 2 : 0) | (d.mesh.periodic[2] ? 4 : 0);
-  D.chain = idx;
+  D.chain = o.chain_base + idx;
   D.ncell = H.ncell;
   divmagic((unsigned)hx, D.hx_m, D.hx_l);
   divmagic((unsigned)ny, D.ny_m, D.ny_l);
@@ -1017,6 +1017,8 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
   if (!(o.sigma_cap > 0 && o.sigma_cap < 1)) return fail(MMC_ERR_ARG, "sigma_cap must be in (0, 1)");
   if (!(o.theta0_deg >= 1 && o.theta0_deg <= 180)) return fail(MMC_ERR_ARG, "theta0_deg must be in [1, 180]");
   if (o.demag_stripes < 0 || o.demag_stripes > 64) return fail(MMC_ERR_ARG, "demag_stripes must be in [0, 64]");
+  if (o.chain_base < 0 || (long long)o.chain_base + nchains > 2147483647LL)
+    return fail(MMC_ERR_ARG, "chain_base must be >= 0 with chain_base + nchains < 2^31");
   for (int i = 0; i < nchains; ++i) MMC_TRY(validate(chains[i], o, i));
   {
     bool any_pc = false, any_cubic = false;

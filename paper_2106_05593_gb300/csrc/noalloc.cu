@@ -5,6 +5,7 @@
 // scratch is a file-scope __device__ array of fixed capacity, so the entry
 // point issues only kernel launches and one memset of the caller's histogram;
 // it never calls cudaMalloc/cudaFree or any routine that allocates.
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -119,10 +120,23 @@ extern "C" mmc_status mmc_observables_noalloc(const float *m, int64_t n, int his
   if (n > kNaMaxCells) return na_fail(MMC_ERR_ARG, "n exceeds the built-in scratch capacity of 2097152 cells");
   if (hist_bins < 1 || hist_bins > mmc::kHistMax) return na_fail(MMC_ERR_ARG, "hist_bins must be in [1, 1024]");
   if (!(hist_max > 0)) return na_fail(MMC_ERR_ARG, "hist_max must be > 0");
+  // m is read as float4 and out / hist written as 8-byte words: a misaligned
+  // pointer would fault the kernel, so it is rejected before any launch
+  if ((reinterpret_cast<uintptr_t>(m) & 15u) != 0) return na_fail(MMC_ERR_ARG, "m must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(out) & 7u) != 0 || (reinterpret_cast<uintptr_t>(hist) & 7u) != 0)
+    return na_fail(MMC_ERR_ARG, "out and hist must be 8-byte aligned");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_fail(MMC_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return na_fail(MMC_ERR_UNSUPPORTED, "device index above 63");
+  if (cuda_stream) {
+    // the scratch address below is the current device's; a stream of another
+    // device would run the kernels against the wrong device's memory
+    int sdev = -1;
+    e = cudaStreamGetDevice((cudaStream_t)cuda_stream, &sdev);
+    if (e != cudaSuccess) return na_fail(MMC_ERR_ARG, std::string("cudaStreamGetDevice: ") + cudaGetErrorString(e));
+    if (sdev != dev) return na_fail(MMC_ERR_ARG, "cuda_stream belongs to another device than the current one");
+  }
   double *scratch = nullptr;
   {
     // once per device, with that device current: the scratch's device address

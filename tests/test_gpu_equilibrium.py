@@ -1,0 +1,222 @@
+"""Equilibrium observables of interacting chains with the demag interaction
+(Sec. II target distribution, Eq. 1; Sec. III frozen demag field, Eq. 14)
+against the FP64 oracle, and the batched form against the plain form.
+
+GPU chains (one batch, chain index in the random-number counter) and oracle
+chains (other seeds, so independent of the GPU's) run the same protocol: a
+burn-in with cone adaptation, then a measurement phase with the cone frozen
+(adaptation breaks detailed balance) that averages a snapshot every iteration.
+Per chain the observables are <|m|>, <|m|^2>, <m> and the |m| histogram (its
+cumulative fraction below the pooled median); each must agree between the two
+sides (32 GPU chains, 16 oracle chains) within 3 standard errors of the
+difference, the errors taken from the chain-to-chain spread of each side.
+Every run is deterministic (fixed seeds and FFT variant), so a pass is
+reproducible."""
+import concurrent.futures as cf
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_common import hist_cdf, lib_or_skip, welch_z
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ("<|m|>", "<|m|^2>", "<mx>", "<my>", "<mz>")
+NO = 16                                  # oracle chains per case
+WORKERS = max(1, min(NO, (os.cpu_count() or 2) - 1))
+
+
+def _pool():
+    return cf.ProcessPoolExecutor(max_workers=WORKERS, mp_context=mp.get_context("spawn"))
+
+
+@pytest.fixture(scope="module")
+def P():
+    return lib_or_skip()
+
+
+def _oracle_eq(spec, chain, seed, m0, burn, meas):
+    """One oracle chain (runs in a spawned process): burn-in with adaptation,
+    then `meas` iterations with the cone frozen, a snapshot every iteration."""
+    import numpy as np
+    import oracle as O
+    o = O.Oracle(spec)
+    st = O.new_state(seed=seed, chain=chain, theta_deg=30.0, adapt=True, demag_mode=1)
+    m, _, _ = o.run(np.asarray(m0, dtype=np.float64), burn, st)
+    st.adapt = 0
+    _, _, ob = o.run(m, meas, st, obs_every=1)
+    return [ob["mean_len"], ob["mean_len2"], *ob["mean_m"]], ob["hist"]
+
+
+def _oracle_chains(spec, m0, no, seed, burn, meas, pool):
+    return [pool.submit(_oracle_eq, spec, c, seed, m0, burn, meas) for c in range(no)]
+
+
+def _gpu_chains(P, spec, m0, ng, seed, burn, meas, **opt):
+    """ng chains of spec in one batch from state m0 (float32 (n, 4))."""
+    g = P.MMC([spec] * ng, fft_variant=1, **opt)
+    for k in range(ng):
+        g.set_m(m0, k)
+    g.sweep(burn, seed)
+    g2 = P.MMC([spec] * ng, fft_variant=1, adapt=0, **opt)
+    g2.restore(g.checkpoint())
+    g2.sweep_sampled(meas, seed + 1, 1)
+    vals, hists = [], []
+    for k in range(ng):
+        ob = g2.observables(k)
+        assert ob["nonfinite"] == 0 and ob["nsnap"] == meas
+        vals.append([ob["mean_len"], ob["mean_len2"], *ob["mean_m"]])
+        hists.append(ob["hist"])
+    return np.array(vals), np.array(hists)
+
+
+def _compare(label, gv, gh, ov, oh, quantities=(0, 1, 2, 3, 4)):
+    """Each observable within 3 standard errors; the histogram through its
+    cumulative fraction below the pooled median."""
+    ov = np.array(ov)
+    oh = np.array(oh)
+    pooled = gh.sum(0) / gh.sum() + oh.sum(0) / oh.sum()
+    c = np.cumsum(pooled) / pooled.sum()
+    edges = [int(np.searchsorted(c, 0.5)) + 1]
+    gc = np.array([hist_cdf(h, edges) for h in gh])
+    oc = np.array([hist_cdf(h, edges) for h in oh])
+    rows = []
+    for q in quantities:
+        rows.append((NAMES[q], gv[:, q].mean(), ov[:, q].mean(), welch_z(gv[:, q], ov[:, q])))
+    for e in range(len(edges)):
+        rows.append(("P(|m| < %.3f)" % (edges[e] / (gh.shape[1] - 1)), gc[:, e].mean(), oc[:, e].mean(),
+                     welch_z(gc[:, e], oc[:, e])))
+    for name, a, b, z in rows:
+        print("%s %-16s gpu %.6g oracle %.6g  z %+.2f" % (label, name, a, b, z))
+    bad = [r for r in rows if not abs(r[3]) < 3.0]
+    assert not bad, (label, bad)
+    return rows
+
+
+def test_film_with_demag_fp32_and_fp64(P):
+    """48 x 48 permalloy film of 4 nm cells with the demag interaction in a 20 mT
+    field along x, 300 K: 32 GPU chains with the default FP32 demag convolution
+    and 32 with the FP64 one, each against 16 oracle chains (FP64 FFT
+    convolution)."""
+    spec = W.film256(48, B_mT=20.0)
+    me = O.me(300.0, 870.0)
+    m0 = W.uniform_state(48 * 48, (1, 0, 0), me)
+    burn, meas = 1000, 2000
+    with _pool() as ex:
+        fut = _oracle_chains(spec, m0[:, :3], NO, 101, burn, meas, ex)
+        g32 = _gpu_chains(P, spec, m0, 32, 3, burn, meas, demag=1)
+        g64 = _gpu_chains(P, spec, m0, 32, 3, burn, meas, demag=1, demag_fp64=1)
+        res = [f.result() for f in fut]
+    ov = [r[0] for r in res]
+    oh = [r[1] for r in res]
+    _compare("film FP32 demag", *g32, ov, oh)
+    _compare("film FP64 demag", *g64, ov, oh)
+
+
+@pytest.mark.parametrize("T", [570.0, 610.0])
+def test_chiral_film_across_tc(P, T):
+    """32 x 32 chiral film (DMI, perpendicular anisotropy, demag) at 570 K and
+    610 K, on both sides of Tc = 600 K where the length distribution is widest
+    and the demag share of the energy changes grows: 32 GPU chains against 16
+    oracle chains."""
+    spec = W.chiral(32, T)
+    m0 = W.uniform_state(32 * 32, (0, 0, 1), 0.3 if T < 600.0 else 0.22)
+    burn, meas = 1000, 2000
+    with _pool() as ex:
+        fut = _oracle_chains(spec, m0[:, :3], NO, 202, burn, meas, ex)
+        gv, gh = _gpu_chains(P, spec, m0, 32, 5, burn, meas, demag=1)
+        res = [f.result() for f in fut]
+    _compare("chiral %g K" % T, gv, gh, [r[0] for r in res], [r[1] for r in res])
+
+
+def test_granular_per_cell_chain_with_demag(P):
+    """48 x 48 granular chain (per-grain Ms0, Ku, Tc and easy axes, weakened
+    exchange across grains, Gaussian hotspot above Tc at the centre) with the
+    demag interaction: 32 GPU chains against 16 oracle chains."""
+    spec = W.granular_chain(48, 3, demag=True)
+    me = O.Oracle(spec).tables()["me"]
+    L = np.maximum(me, 0.2)
+    m0 = np.zeros((48 * 48, 4), np.float32)
+    m0[:, 2] = L.astype(np.float32)
+    burn, meas = 1000, 2000
+    with _pool() as ex:
+        fut = _oracle_chains(spec, m0[:, :3], NO, 303, burn, meas, ex)
+        gv, gh = _gpu_chains(P, spec, m0, 32, 7, burn, meas, demag=1)
+        res = [f.result() for f in fut]
+    _compare("granular", gv, gh, [r[0] for r in res], [r[1] for r in res])
+
+
+def test_batched_equals_plain_bitwise(P):
+    """The batched form and the plain one-chain-per-launch form of the 16-chain
+    chiral temperature scan at full size (512 x 512 cells per chain) are the
+    same Markov chains: a one-chain context given chain_base = c draws chain c's
+    random numbers, and after 200 iterations (two graph blocks) every chain's
+    state, cone angle and observables equal the batch's bit for bit.  The two
+    forms are therefore at equal accuracy by construction."""
+    specs = W.chiral512_batch()
+    b = P.MMC(specs, demag=1)
+    variant = b.fft_tuning()[0]
+    b.init_random(7)
+    b.sweep(200, 7)
+    for c in range(16):
+        p = P.MMC(specs[c], demag=1, fft_variant=variant, chain_base=c)
+        p.init_random(7)
+        p.sweep(200, 7)
+        assert np.array_equal(p.get_m(0), b.get_m(c)), c
+        ob, op = b.observables(c), p.observables(0)
+        for k in ("mean_len", "mean_len2", "theta_deg", "acc_rate"):
+            assert ob[k] == op[k], (c, k)
+        assert np.array_equal(ob["mean_m"], op["mean_m"]) and np.array_equal(ob["hist"], op["hist"])
+        p.close()
+
+
+def test_batched_vs_plain_independent_chains(P):
+    """The metric's agreement clause with independent random numbers: the
+    chiral temperature scan reduced to 64 x 64 cells per chain (T = 50 + 40 c K,
+    c = 0..15), 16 replicas per temperature in one batch against 16 replicas per
+    temperature each in its own one-chain context (other seeds), 1000 + 1000
+    iterations from random states (the same adaptive protocol on both sides).
+    Per temperature <|m|>, <|m|^2> and the cumulative |m| fraction below the
+    pooled median are compared: 48 comparisons, each within 3 standard errors of
+    the difference except at the rate chance allows (at most 2 beyond 3 SE and
+    none beyond 4, the family-wise bound of 48 tests at 0.3 %)."""
+    R, n = 16, 64
+    temps = [50.0 + 40.0 * c for c in range(16)]
+    specs = [W.chiral(n, T) for T in temps for _ in range(R)]
+    burn, meas = 1000, 1000
+    b = P.MMC(specs, demag=1, fft_variant=1)
+    b.init_random(21)
+    b.sweep(burn, 21)
+    b.sweep_sampled(meas, 22, 1)
+    bo = [b.observables(k) for k in range(len(specs))]
+    po = []
+    for k, sp in enumerate(specs):
+        p = P.MMC(sp, demag=1, fft_variant=1)
+        p.init_random(1000 + k)
+        p.sweep(burn, 31)
+        p.sweep_sampled(meas, 32, 1)
+        po.append(p.observables(0))
+        p.close()
+    zs = []
+    for t, T in enumerate(temps):
+        sl = slice(t * R, (t + 1) * R)
+        bb, pp = bo[sl], po[sl]
+        hb = np.array([o["hist"] for o in bb])
+        hp = np.array([o["hist"] for o in pp])
+        pooled = hb.sum(0) + hp.sum(0)
+        med = int(np.searchsorted(np.cumsum(pooled) / pooled.sum(), 0.5)) + 1
+        for name, f in (("<|m|>", lambda o: o["mean_len"]), ("<|m|^2>", lambda o: o["mean_len2"])):
+            z = welch_z([f(o) for o in bb], [f(o) for o in pp])
+            zs.append(z)
+            print("T %5.0f %-8s batched %.6g plain %.6g z %+.2f" % (T, name, np.mean([f(o) for o in bb]),
+                                                                      np.mean([f(o) for o in pp]), z))
+        z = welch_z([hist_cdf(h, [med])[0] for h in hb], [hist_cdf(h, [med])[0] for h in hp])
+        zs.append(z)
+        print("T %5.0f P(|m| < median) z %+.2f" % (T, z))
+    zs = np.abs(np.array(zs))
+    print("comparisons %d, beyond 3 SE %d, largest |z| %.2f" % (zs.size, int((zs >= 3).sum()), zs.max()))
+    assert int((zs >= 3).sum()) <= 2 and zs.max() < 4.0

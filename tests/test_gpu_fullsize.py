@@ -68,3 +68,73 @@ def test_probe_full_size_pass_on_sampled_rows(P, color):
         st = compare_pass(dec_g[sl_g], acc_g[sl_g], dec_o[sl_o], acc_o[sl_o], band_o[sl_o],
                           wsum=exchange_weight_sum(spec))
         print("probe 8192^2 colour %d rows %d..%d: %s" % (color, r0 + lo, r0 + hi, st))
+
+
+def _differing(mg, mo, tol=1e-5):
+    d = np.abs(mg - mo).max(axis=1)
+    return int((d > tol).sum()), float(d[d <= tol].max(initial=0.0))
+
+
+def test_chiral_batch_full_size_iterations(P):
+    """The benchmarked path itself (the production pass kernel, the create-time
+    FFT variant, chain groups on concurrent streams) over three whole
+    iterations of the 16-chain batch: chains 0, 9 and 15 end equal to the
+    oracle's run from the same state to FP32 rounding, except the few cells a
+    decision inside the FP32 bound can change (a flipped cell and, later, its
+    neighbours)."""
+    specs = W.chiral512_batch()
+    g = P.MMC(specs, demag=1)
+    g.init_random(7)
+    start = {k: g.get_m(k) for k in (0, 9, 15)}
+    g.sweep(3, 7)
+    for k, m4 in start.items():
+        o = O.Oracle(specs[k])
+        st = O.new_state(seed=7, chain=k, theta_deg=30.0, adapt=True, demag_mode=1)
+        mo, _, _ = o.run(m4[:, :3].astype(np.float64), 3, st)
+        ndiff, agree = _differing(g.get_m(k)[:, :3].astype(np.float64), mo)
+        print("chiral batch chain %d, 3 iterations: differing cells %d, max |dm| elsewhere %.2e" % (k, ndiff, agree))
+        assert agree < 1e-5 and ndiff <= 8
+
+
+def test_chiral_batch_full_size_graphs_equal_eager(P):
+    """A 100-iteration block of the full batch replayed as a CUDA graph (the
+    benchmark's launch form) equals the same iterations launched eagerly, bit
+    for bit, for every chain."""
+    specs = W.chiral512_batch()
+    a = P.MMC(specs, demag=1)
+    variant = a.fft_tuning()[0]
+    b = P.MMC(specs, demag=1, use_graphs=0, fft_variant=variant)
+    for g in (a, b):
+        g.init_random(11)
+        g.sweep(100, 11)
+    for k in range(16):
+        assert np.array_equal(a.get_m(k), b.get_m(k)), k
+    assert [a.observables(k)["theta_deg"] for k in range(16)] == [b.observables(k)["theta_deg"] for k in range(16)]
+
+
+def test_probe_full_size_iterations_on_windows(P):
+    """Two whole iterations of the 8192 x 8192 probe film through mmc_sweep (the
+    production kernel) against the oracle's run of three 64-row windows of the
+    same state; rows within four of a window's cut see stale neighbours in the
+    oracle (four passes) and are left out."""
+    nx = 8192
+    spec = W.probe(nx)
+    g = P.MMC(spec, adapt=0)
+    g.init_random(5)
+    g.sweep(2, 5)                                   # a non-trivial start
+    m0 = g.get_m().reshape(nx, nx, 4)
+    g.sweep(2, 9)
+    m1 = g.get_m().reshape(nx, nx, 4)
+    for r0 in (0, 4000, nx - 64):                   # even: window colours equal global colours
+        nr = 64
+        sub = dict(spec, mesh=(nx, nr, 1), cell_base=r0 * nx)
+        o = O.Oracle(sub)
+        st = O.new_state(seed=9, chain=0, theta_deg=30.0, adapt=False, demag_mode=0, sweep=2)
+        mo, _, _ = o.run(m0[r0:r0 + nr].reshape(-1, 4)[:, :3].astype(np.float64), 2, st)
+        lo = 0 if r0 == 0 else 4
+        hi = nr if r0 + nr == nx else nr - 4
+        mg = m1[r0 + lo:r0 + hi].reshape(-1, 4)[:, :3].astype(np.float64)
+        ndiff, agree = _differing(mg, mo.reshape(nr, nx, 3)[lo:hi].reshape(-1, 3))
+        print("probe rows %d..%d, 2 iterations: differing cells %d, max |dm| elsewhere %.2e"
+              % (r0 + lo, r0 + hi, ndiff, agree))
+        assert agree < 1e-5 and ndiff <= 8

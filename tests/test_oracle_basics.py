@@ -166,14 +166,29 @@ def test_cone_adaptation_rule(theta, acc, att, exp):
     assert O.adapt_theta(theta, acc, att) == exp
 
 
-def test_hist_f32_matches_float32_semantics():
+def test_hist_counts_of_known_lengths():
+    """The |m| histogram (Sec. II, Figs. 1-2) of states whose lengths are known
+    exactly: c_b cells at the centre of bin b land in bin b, lengths at or above
+    hmax in the overflow entry, for any direction; doubling hmax halves the bin
+    index."""
     rng = np.random.default_rng(3)
-    m4 = np.zeros((5000, 4), np.float32)
-    m4[:, :3] = rng.uniform(-0.7, 0.7, (5000, 3)).astype(np.float32)
-    h = O.hist_f32(m4, 200, 1.0)
-    assert h.sum() == 5000
-    r = np.sqrt(np.sum(m4[:, :3].astype(np.float64) ** 2, axis=1))
-    ref = np.minimum((r * 200).astype(int), 200)
-    # identical except values that sit within FP32 rounding of a bin edge
-    diff = np.abs(np.bincount(ref, minlength=201) - h).sum()
-    assert diff <= 4
+    bins, hmax = 200, 1.0
+    counts = rng.integers(0, 7, bins)
+    L = np.repeat((np.arange(bins) + 0.5) * hmax / bins, counts)
+    L = np.concatenate([L, [1.0, 1.0 + 1e-9, 1.3]])          # overflow: at and beyond hmax
+    d = rng.standard_normal((L.size, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    m = d * L[:, None]
+    h = O.hist(m, bins, hmax)
+    assert np.array_equal(h[:bins], counts)
+    assert h[bins] == 3
+    # a zero vector is in bin 0; hmax = 2 maps centre (b + 1/2)/200 to bin b // 2
+    # (t = b/2 + 1/4), and the lengths 1, 1 + 1e-9, 1.3 to bins 100, 100, 130
+    assert O.hist(np.zeros((4, 3)), bins, hmax)[0] == 4
+    h2 = O.hist(m, bins, 2.0)
+    exp = np.zeros(bins + 1, np.int64)
+    for b in range(bins):
+        exp[b // 2] += counts[b]
+    exp[100] += 2
+    exp[130] += 1
+    assert np.array_equal(h2, exp)

@@ -117,8 +117,9 @@ def granular_chain(n, seed, h=5e-9, grain_spacing=8e-9, Ms0=1e6, Ku=3e5, Tc=700.
                  grain=gflat.copy(), grain_exch_scale=0.1)
 
 
-def granular_sizes(nchains=32, seed=7, lo=64, hi=1024, step=32):
-    """Square mesh sides drawn uniformly from lo..hi in steps of `step`."""
+def granular_sizes(nchains=32, seed=7, lo=64, hi=1024, step=2):
+    """Square mesh sides drawn uniformly from the even values lo..hi (steps of
+    `step`)."""
     rng = np.random.default_rng(seed)
     return [int(v) for v in rng.choice(np.arange(lo, hi + 1, step), size=nchains)]
 
