@@ -195,10 +195,12 @@ def test_batched_vs_plain_independent_chains(P):
     bo = [b.observables(k) for k in range(len(specs))]
     po = []
     for k, sp in enumerate(specs):
+        # every replica its own key: one-chain contexts all carry chain index 0,
+        # so a shared seed would give every replica the same random numbers
         p = P.MMC(sp, demag=1, fft_variant=1)
         p.init_random(1000 + k)
-        p.sweep(burn, 31)
-        p.sweep_sampled(meas, 32, 1)
+        p.sweep(burn, 5000 + k)
+        p.sweep_sampled(meas, 9000 + k, 1)
         po.append(p.observables(0))
         p.close()
     zs = []
