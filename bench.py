@@ -55,9 +55,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-demag", action="store_true")
-    ap.add_argument("--fft-variant", type=int, default=0, choices=(0, 1, 2, 3),
+    ap.add_argument("--fft-variant", type=int, default=0, choices=(0, 1, 2, 3, 4),
                     help="FP32 2D demag kernels: 0 timed pick at create, 1 radix 16, 2 radix 32, "
-                         "3 radix 16 two blocks per SM")
+                         "3 radix 16 two blocks per SM, 4 warp 32x32 transforms (1024-point grids)")
     ap.add_argument("--stream-groups", type=int, default=0,
                     help="chain groups iterating on concurrent streams: 0 auto (2), 1 one stream")
     ap.add_argument("--no-compare", action="store_true",
@@ -165,7 +165,7 @@ def nvtx_range(name):
 
 
 KERNEL_SOURCES = ("k_sweep.cu", "k_demag.cu", "k_demag_il.cuh", "demag_il.h", "demag_args.cuh", "fft.cuh",
-                  "fft_il.cuh", "trial.cuh", "philox.cuh", "mmc_internal.h")
+                  "fft_il.cuh", "trial.cuh", "philox.cuh", "mmc_internal.h", "k_demag_w32.cu", "fft_w32.cuh")
 
 
 def strip_comments(src):
@@ -510,9 +510,9 @@ def run_ours(args):
                 compare["fp64_demag"] = fp64_demag_compare(MMC, specs, seed, stream, cells_per_step)
                 compare["demag_update_ms"]["own_fp64"] = compare["fp64_demag"]["demag_update_ms"]
             v, tms = g.fft_tuning()
-            compare["fft_variant"] = {"picked": {0: None, 1: "radix16", 2: "radix32", 3: "radix16x2"}[v],
+            compare["fft_variant"] = {"picked": {0: None, 1: "radix16", 2: "radix32", 3: "radix16x2", 4: "warp32x32"}[v],
                                       "create_time_ms": {"radix16": tms[0], "radix32": tms[1],
-                                                         "radix16x2": tms[2]}}
+                                                         "radix16x2": tms[2], "warp32x32": tms[3]}}
             del cf
         if len(specs) > 1:
             plain = [MMC([sp], demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=args.fft_variant,

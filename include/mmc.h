@@ -119,7 +119,10 @@ typedef struct {
     int fft_variant;          /* FP32 2D demag kernels: 0 time the variants on the
                                  batch at create and keep the fastest, 1 radix 16
                                  (768 threads), 2 radix 32 (384 threads), 3 radix
-                                 16 (384 threads, two blocks per SM)            [0] */
+                                 16 (384 threads, two blocks per SM), 4 one warp
+                                 per 1024-point sequence as a 32 x 32 split (only
+                                 when every chain's padded grid is 1024 x 1024 and
+                                 open; otherwise 1)                              [0] */
     int demag_stripes;        /* S > 1: each sublattice pass runs in S bands of rows
                                  (j + ny k in [floor(b nrows / S), floor((b+1)
                                  nrows / S))), the demag field recomputed before
@@ -309,6 +312,14 @@ mmc_status mmc_energy(mmc_ctx *ctx, int chain, double out[7]);
  * natural order (HOST), from the FP64 convolution. */
 mmc_status mmc_demag_field(mmc_ctx *ctx, int chain, double *H);
 
+/* The demag field H_d (A/m) the sweep itself uses for one chain (Sec. III,
+ * Eq. 14): the context's own convolution of the current state, with the FFT
+ * kernels and precision the sweep runs (FP32 unless demag_fp64, the FFT variant
+ * of mmc_fft_tuning), 3 doubles per cell in natural order (HOST).  A diagnostic
+ * of the precision of the sweep's frozen field; MMC_ERR_UNSUPPORTED on the cuFFT
+ * comparison path (demag_cufft). */
+mmc_status mmc_sweep_field(mmc_ctx *ctx, int chain, double *H);
+
 /* Thermodynamic tables of one chain (HOST, ncell doubles each, any may be NULL):
  * m_e (Eq. 9), chi (Eq. 8, 1/T), sigma (Eq. 13 capped). */
 mmc_status mmc_tables(mmc_ctx *ctx, int chain, double *me, double *chi, double *sigma);
@@ -356,15 +367,16 @@ mmc_status mmc_phase_times(mmc_ctx *ctx, int64_t n, uint64_t seed, double ms[6],
 
 /* FFT variant of the batch's FP32 2D demag kernels (1 radix 16 with 768-thread
  * blocks, 2 radix 32 with 384-thread blocks, 3 radix 16 with 384-thread blocks,
- * two per SM; 0 when the batch does not use them) and, when
+ * two per SM, 4 warp-resident 32 x 32 transforms for batches whose padded grids
+ * are all 1024 x 1024; 0 when the batch does not use them) and, when
  * mmc_options.fft_variant was 0, the per-update times in ms that the
- * create-time timing measured for the three variants (0 for a variant that was
- * not timed).  The variants compute the same convolution with FP32 rounding in
+ * create-time timing measured for the four variants (ms has 4 entries; 0 for a
+ * variant that was not timed).  The variants compute the same convolution with FP32 rounding in
  * a different order, so the demag field, and through it the chain, can differ
  * between them at rounding level; set the variant explicitly where runs must
  * repeat bit for bit across contexts.  (HOST outputs.)  Not a paper quantity: a
  * tuning record of this implementation. */
-mmc_status mmc_fft_tuning(const mmc_ctx *ctx, int *variant, double ms[3]);
+mmc_status mmc_fft_tuning(const mmc_ctx *ctx, int *variant, double ms[4]);
 
 /* Number of kernels the library launched since create (all kinds). */
 int64_t mmc_kernel_launches(const mmc_ctx *ctx);

@@ -20,7 +20,7 @@ EXPORTS = [
     "mmc_default_options", "mmc_create", "mmc_create_single", "mmc_destroy", "mmc_set_field",
     "mmc_set_m", "mmc_get_m", "mmc_init_random", "mmc_sweep", "mmc_sweep_sampled",
     "mmc_demag_update", "mmc_pass_debug", "mmc_observables", "mmc_energy", "mmc_demag_field",
-    "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_fft_tuning", "mmc_sweep_serial", "mmc_minimize", "mmc_set_temperature", "mmc_angle_hist", "mmc_trial_terms", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell", "mmc_demag_kernel", "mmc_thermo",
+    "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_fft_tuning", "mmc_sweep_field", "mmc_sweep_serial", "mmc_minimize", "mmc_set_temperature", "mmc_angle_hist", "mmc_trial_terms", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell", "mmc_demag_kernel", "mmc_thermo",
     "mmc_checkpoint", "mmc_restore", "mmc_observables_noalloc", "mmc_status_str", "mmc_last_error",
 ]
 
@@ -113,6 +113,8 @@ def load():
     L.mmc_energy.argtypes = [vp, C.c_int, dp]
     L.mmc_demag_field.restype = st
     L.mmc_demag_field.argtypes = [vp, C.c_int, dp]
+    L.mmc_sweep_field.restype = st
+    L.mmc_sweep_field.argtypes = [vp, C.c_int, dp]
     L.mmc_tables.restype = st
     L.mmc_tables.argtypes = [vp, C.c_int, dp, dp, dp]
     L.mmc_energy_grad.restype = st

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cu", "k_sweep.cu", "k_demag.cu", "k_demag_il_f16.cu", "k_demag_il_f32.cu", "k_demag_il_f16h.cu",
-           "k_demag_il_d16.cu", "k_reduce.cu", "k_grad.cu", "noalloc.cu", "k_serial.cu", "k_sdesc.cu", "k_angles.cu", "k_terms.cu",
+           "k_demag_il_d16.cu", "k_demag_w32.cu", "k_reduce.cu", "k_grad.cu", "noalloc.cu", "k_serial.cu", "k_sdesc.cu", "k_angles.cu", "k_terms.cu",
            "k_cufft.cu", "host_physics.cpp"]
 
 

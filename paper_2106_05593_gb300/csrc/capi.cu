@@ -112,6 +112,7 @@ struct IlTables {
 
 struct DemagPlan {
   IlTables small;                       // FP32 variant 3: E = 6144 (2 blocks per SM)
+  IlTables w32;                         // FP32 variant 4: warp transforms, 1024 x 1024 grids only
   bool fp64 = false;
   ChainDev *d_ch = nullptr;             // chain table the plan indexes
   int *rows_chain = nullptr;
@@ -134,6 +135,7 @@ struct SpecSet {
   int Px, Py, Pz;
   DemagPeriodic pd;                     // periodic axes of the convolution
   void *d32 = nullptr, *d64 = nullptr;
+  void *d32t = nullptr;                 // FP32 [comp][kx][kyq] copy for the warp-transform path
 };
 
 struct GraphEntry {
@@ -160,8 +162,8 @@ struct mmc_ctx {
   float *d_ms = nullptr;
   long long m_total = 0, tab_total = 0, ms_total = 0;
   std::vector<SpecSet> specs;
-  void **d_nhat32 = nullptr, **d_nhat64 = nullptr;
-  void *d_tw32 = nullptr, *d_tw64 = nullptr;
+  void **d_nhat32 = nullptr, **d_nhat64 = nullptr, **d_nhat32t = nullptr;
+  void *d_tw32 = nullptr, *d_tw64 = nullptr, *d_tw1024 = nullptr;
   int *d_sw_chain = nullptr;
   long long *d_sw_first = nullptr;
   int2 *d_sw_desc = nullptr;
@@ -186,7 +188,7 @@ struct mmc_ctx {
   std::vector<ChainGroup> groups;
   cudaEvent_t ev_fork = nullptr;
   int tuned_variant = 0;                // FFT variant picked at create (0: not tuned)
-  double tune_ms[3] = {0.0, 0.0, 0.0};  // per-update time of the variants when tuned
+  double tune_ms[4] = {0.0, 0.0, 0.0, 0.0};  // per-update time of the variants when tuned
   std::vector<DemagPlan> single[2];     // per chain and precision (0 FP32, 1 FP64), built lazily
   // serial exact-demag sweep: real-space tensors per set, proposals scratch
   bool serial_ready = false;
@@ -549,7 +551,7 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
     if (single) {
       D.s_off = spec_elems;
     }
-    spec_elems += 3LL * D.nrows * D.Sx;
+    spec_elems += 3LL * spectrum_rows(D) * D.Sx;
     table.push_back(D);
     maxPx = std::max(maxPx, D.Px);
     maxPyPz = std::max(maxPyPz, D.Py * D.Pz);
@@ -633,10 +635,35 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
   P.cols_smem = csmem;
   P.fp64 = fp64;
   if (il && !fp64) MMC_TRY(build_il_tables(c, P.small, table, ids, nid, il_elements_small(), false));
+  if (il && !fp64 && !single) {
+    // warp-transform path: every chain on a 1024 x 1024 padded grid; one row block
+    // per tile of four rows, one column block per kx = 0..512
+    bool ok = !table.empty();
+    for (const ChainDev &D : table) ok = ok && w32_chain(D) && c->specs[(size_t)D.spec].d32t != nullptr;
+    if (ok) {
+      std::vector<int> rc2, cc2;
+      std::vector<long long> rf2((size_t)nid + 1, 0), cf2((size_t)nid + 1, 0);
+      for (size_t t = 0; t < table.size(); ++t) {
+        const ChainDev &D = table[t];
+        rf2[(size_t)ids[t]] = (long long)rc2.size();
+        for (long long b = 0; b < spectrum_rows(D) / 4; ++b) rc2.push_back(ids[t]);
+        cf2[(size_t)ids[t]] = (long long)cc2.size();
+        for (int b = 0; b < D.Px / 2 + 1; ++b) cc2.push_back(ids[t]);
+      }
+      MMC_TRY(upload(c, &P.w32.rows_chain, rc2));
+      MMC_TRY(upload(c, &P.w32.rows_first, rf2));
+      MMC_TRY(upload(c, &P.w32.cols_chain, cc2));
+      MMC_TRY(upload(c, &P.w32.cols_first, cf2));
+      P.w32.rows_blocks = (int)rc2.size();
+      P.w32.cols_blocks = (int)cc2.size();
+      P.w32.ok = true;
+    }
+  }
   {
-    int v = c->opt.fft_variant >= 1 && c->opt.fft_variant <= 3 ? c->opt.fft_variant
+    int v = c->opt.fft_variant >= 1 && c->opt.fft_variant <= 4 ? c->opt.fft_variant
             : (c->tuned_variant ? c->tuned_variant : 1);
     if (v == 3 && !P.small.ok) v = 1;
+    if (v == 4 && !P.w32.ok) v = 1;
     P.fft_variant = v;
   }
   if (shared_spec) {
@@ -678,6 +705,14 @@ DemagLaunch make_demag_launch(mmc_ctx *c, const DemagPlan &P, float4 *heff, doub
   D.il2d = P.il2d;
   D.fft_variant = P.fft_variant;
   D.inv_smem = P.inv_smem;
+  D.w32 = false;
+  D.nhatT = (const void *const *)c->d_nhat32t;
+  D.tw1024 = c->d_tw1024;
+  if (P.il2d && P.fft_variant == 4 && P.w32.ok && !P.fp64) {
+    D.w32 = true;
+    D.rows_chain = P.w32.rows_chain; D.rows_first = P.w32.rows_first; D.rows_blocks = P.w32.rows_blocks;
+    D.cols_chain = P.w32.cols_chain; D.cols_first = P.w32.cols_first; D.cols_blocks = P.w32.cols_blocks;
+  }
   if (P.il2d && P.fft_variant == 3 && P.small.ok) {
     D.rows_chain = P.small.rows_chain; D.rows_first = P.small.rows_first; D.rows_blocks = P.small.rows_blocks;
     D.cols_chain = P.small.cols_chain; D.cols_first = P.small.cols_first; D.cols_blocks = P.small.cols_blocks;
@@ -1098,7 +1133,7 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
         D.Sx = (D.Px / 2 + 1 + g - 1) / g * g;
       }
       D.s_off = soff;
-      soff += 3LL * D.nrows * D.Sx;
+      soff += 3LL * spectrum_rows(D) * D.Sx;
       int found = -1;
       for (size_t s = 0; s < c->specs.size(); ++s) {
         const SpecSet &ss = c->specs[s];
@@ -1147,7 +1182,7 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
   }
   // tensor spectra and twiddles
   if (o.demag) {
-    std::vector<void *> p32, p64;
+    std::vector<void *> p32, p64, p32t;
     for (auto &ss : c->specs) {
       std::vector<double> sp;
       demag_spectra(ss.h, ss.Px, ss.Py, ss.Pz, sp, ss.pd);
@@ -1160,9 +1195,36 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
       ss.d64 = d64;
       p32.push_back(d32);
       p64.push_back(d64);
+      void *d32t = nullptr;
+      if (ss.Px == 1024 && ss.Py == 1024 && ss.Pz == 1 && !ss.pd.circ[0] && !ss.pd.circ[1]) {
+        // [comp][kyq][kx] -> [comp][kx][kyq] for the column blocks of the warp-transform path
+        const size_t q = 513;
+        std::vector<float> tr(4 * q * q);
+        for (size_t cp = 0; cp < 4; ++cp)
+          for (size_t ky = 0; ky < q; ++ky)
+            for (size_t kx = 0; kx < q; ++kx) tr[(cp * q + kx) * q + ky] = (float)sp[(cp * q + ky) * q + kx];
+        float *dt = nullptr;
+        MMC_TRY_OR(upload(c, &dt, tr));
+        d32t = dt;
+      }
+      ss.d32t = d32t;
+      p32t.push_back(d32t);
     }
     MMC_TRY_OR(upload(c, &c->d_nhat32, p32));
     MMC_TRY_OR(upload(c, &c->d_nhat64, p64));
+    MMC_TRY_OR(upload(c, &c->d_nhat32t, p32t));
+    {
+      // 32 x 32 twiddles of the warp transforms: entry k1 * 32 + t = exp(-2 pi i t k1 / 1024)
+      std::vector<float2> t1024(1024);
+      for (int k1 = 0; k1 < 32; ++k1)
+        for (int t = 0; t < 32; ++t) {
+          const double a = -2.0 * kPi * (double)(t * k1) / 1024.0;
+          t1024[(size_t)(k1 * 32 + t)] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+      float2 *d = nullptr;
+      MMC_TRY_OR(upload(c, &d, t1024));
+      c->d_tw1024 = d;
+    }
     std::vector<float2> tw32(kMaxFFT);
     std::vector<double2> tw64(kMaxFFT);
     for (int t = 0; t < kMaxFFT; ++t) {
@@ -1246,8 +1308,9 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     cudaEvent_t e0, e1;
     CUDA_TRY_OR(cudaEventCreate(&e0));
     CUDA_TRY_OR(cudaEventCreate(&e1));
-    for (int v = 1; v <= 3; ++v) {
+    for (int v = 1; v <= 4; ++v) {
       if (v == 3 && !c->batch_plan.small.ok) continue;
+      if (v == 4 && !c->batch_plan.w32.ok) continue;
       c->batch_plan.fft_variant = v;
       issue_demag(c);
       CUDA_TRY_OR(cudaEventRecord(e0, c->stream));
@@ -1679,6 +1742,27 @@ mmc_status mmc_demag_field(mmc_ctx *c, int chain, double *H) {
   return MMC_OK;
 }
 
+mmc_status mmc_sweep_field(mmc_ctx *c, int chain, double *H) {
+  Trace trace("mmc_sweep_field");
+  MMC_TRY(check_chain(c, chain));
+  if (!H) return fail(MMC_ERR_ARG, "null output");
+  const long long n = c->hc[chain].ncell;
+  if (!c->any_demag) {
+    std::memset(H, 0, (size_t)n * 3 * sizeof(double));
+    return MMC_OK;
+  }
+  if (!c->cf.empty()) return fail(MMC_ERR_UNSUPPORTED, "the cuFFT comparison path does not report its field");
+  // the batch plan with the kernels and precision the sweep uses; the chain's
+  // field is also written out in natural order (h_eff gets the values the next
+  // iteration would compute anyway)
+  DemagLaunch D = make_demag_launch(c, c->batch_plan, c->d_heff, c->d_Hd, chain);
+  launch_demag(c->L(), D, c->batch_plan.fp64);
+  MMC_TRY(check_launch());
+  CUDA_TRY(cudaMemcpyAsync(H, c->d_Hd, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MMC_OK;
+}
+
 mmc_status mmc_energy(mmc_ctx *c, int chain, double out[7]) {
   Trace trace("mmc_energy");
   MMC_TRY(check_chain(c, chain));
@@ -1877,10 +1961,10 @@ mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[6], i
 
 int64_t mmc_kernel_launches(const mmc_ctx *c) { return c ? c->launches : 0; }
 
-mmc_status mmc_fft_tuning(const mmc_ctx *c, int *variant, double ms[3]) {
+mmc_status mmc_fft_tuning(const mmc_ctx *c, int *variant, double ms[4]) {
   if (!c || !variant || !ms) return fail(MMC_ERR_ARG, "null argument");
   *variant = c->batch_plan.ready && c->batch_plan.il2d ? c->batch_plan.fft_variant : 0;
-  for (int k = 0; k < 3; ++k) ms[k] = c->tune_ms[k];
+  for (int k = 0; k < 4; ++k) ms[k] = c->tune_ms[k];
   return MMC_OK;
 }
 int mmc_nchains(const mmc_ctx *c) { return c ? c->nchains : 0; }

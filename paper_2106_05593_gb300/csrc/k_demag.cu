@@ -281,6 +281,7 @@ void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
 
 void launch_demag(const Launch &L, const DemagLaunch &P, bool fp64) {
   if (fp64) launch_demag_impl<double>(L, P);
+  else if (P.w32) launch_w32(L, P);
   else launch_demag_impl<float>(L, P);
 }
 
@@ -303,6 +304,7 @@ cudaError_t demag_set_smem_limits() {
   if ((e = il_set_smem<CfgF16>(lil)) != cudaSuccess) return e;
   if ((e = il_set_smem<CfgF32>(lil)) != cudaSuccess) return e;
   if ((e = il_set_smem<CfgD16>(lil)) != cudaSuccess) return e;
+  if ((e = w32_set_smem()) != cudaSuccess) return e;
   return il_set_smem<CfgF16h>(lil);
 }
 

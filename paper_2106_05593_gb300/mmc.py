@@ -258,6 +258,13 @@ class MMC:
         check(load().mmc_demag_field(self._ctx, int(chain), _dptr(H)), "mmc_demag_field")
         return H.reshape(-1, 3)
 
+    def sweep_field(self, chain=0):
+        """Demag field H_d (A/m) the sweep uses (the context's own convolution:
+        FP32 unless demag_fp64, the picked FFT variant), (ncell, 3)."""
+        H = np.zeros(3 * self.ncell[chain])
+        check(load().mmc_sweep_field(self._ctx, int(chain), _dptr(H)), "mmc_sweep_field")
+        return H.reshape(-1, 3)
+
     def angle_hist(self, chain=0, bins=100, lo=0.0, hi=np.pi):
         """Angular-deviation histogram of the current state (Sec. II, Fig. 1d-f):
         (counts, bins + 1 entries with the out-of-range angles last; mean direction)."""
@@ -316,9 +323,9 @@ class MMC:
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(kinds)}
 
     def fft_tuning(self):
-        """(variant, create-time ms of variants 1, 2, 3) of the FP32 2D demag kernels."""
+        """(variant, create-time ms of variants 1, 2, 3, 4) of the FP32 2D demag kernels."""
         v = C.c_int(0)
-        ms = np.zeros(3)
+        ms = np.zeros(4)
         check(load().mmc_fft_tuning(self._ctx, C.byref(v), _dptr(ms)), "mmc_fft_tuning")
         return int(v.value), tuple(float(x) for x in ms)
 
