@@ -40,6 +40,7 @@ struct SweepArgs {
   float *dec_dbg;
   signed char *acc_dbg;
   int nstripes, stripe;     // nstripes > 1: the band of rows [r0, r1) of the stripe only
+  unsigned rk[20];          // Philox round keys of (key0, key1), see philox4x32_10_rk
 };
 
 // A thread handles kSweepCells cells of its block's 256 slots (slot t + j 128):
@@ -168,6 +169,146 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 7) k_sweep_pass(S
   }
 }
 
+// One-cell-thick chains (every chain of the launch has nz = 1): the same pass
+// with the work per cell cut down.  The chain constants are read once per block
+// into shared memory; the Philox round keys come precomputed in the kernel
+// parameters; the four in-plane neighbours are found by offsets from the cell's
+// slot in the other colour (s - 1 + p, s + p in the row, s in the rows j -+ 1,
+// with the periodic wrap at the edges); exchange, DMI and the field act through
+// one local vector (local_change_flat).
+template <bool PERCELL, bool DEBUG>
+__global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 8) k_sweep_flat(SweepArgs A) {
+  __shared__ float4 skv[kChainKVec];
+  __shared__ unsigned wacc[kSweepThreads / 32], watt[kSweepThreads / 32];
+  const int2 bd = A.blk_desc[A.blk_base + (int)blockIdx.x];
+  const int c = bd.x;
+  if (threadIdx.x < kChainKVec) skv[threadIdx.x] = __ldg(reinterpret_cast<const float4 *>(A.chains + c) + threadIdx.x);
+  __syncthreads();
+  const ChainK K = load_chain_vec(skv);
+  const int nx = K.nx, ny = K.ny, hx = K.hx;
+  const int pbc = K.pbc & 3;
+  const unsigned S32 = (unsigned)K.nrows * (unsigned)hx;
+  const long long S = (long long)S32;
+  const unsigned q0 = (unsigned)bd.y * (unsigned)kSweepBlock + threadIdx.x;
+  const int color = A.color;
+  const int flags = K.flags;
+  float4 *mc = A.m + K.m_off + (long long)color * S;
+  const float4 *mo = A.m + K.m_off + (long long)(1 - color) * S;
+  const float omc = A.omc_override >= 0.f ? A.omc_override : A.st[c].omc;
+  const unsigned sweep = *A.sweep_base + A.sweep_off;
+  unsigned lo = 0, hi = S32;
+  if (A.nstripes > 1) {
+    const unsigned long long nr = (unsigned long long)K.nrows;
+    lo = (unsigned)((unsigned long long)A.stripe * nr / (unsigned)A.nstripes) * (unsigned)hx;
+    hi = (unsigned)((unsigned long long)(A.stripe + 1) * nr / (unsigned)A.nstripes) * (unsigned)hx;
+    const unsigned b0 = (unsigned)bd.y * (unsigned)kSweepBlock;
+    if (b0 >= hi || b0 + (unsigned)kSweepBlock <= lo) return;     // the whole block, before the next barrier
+  }
+  const bool grain = (flags & F_GRAIN) != 0;
+
+  // 1. indices and loads of every cell of this thread
+  bool valid[kSweepCells];
+  unsigned qq[kSweepCells], cellid[kSweepCells];
+  float4 a[kSweepCells], h[kSweepCells];
+  float4 nb[kSweepCells][4];
+  float pres[kSweepCells][4];
+  CellMat M[kSweepCells];
+#pragma unroll
+  for (int e = 0; e < kSweepCells; ++e) {
+    const unsigned q32 = q0 + (unsigned)(e * kSweepThreads);
+    bool ok = q32 >= lo && q32 < hi;
+    const int j = ok ? (int)divq(q32, K.hx_m, K.hx_l) : 0;     // row (one cell thick: j)
+    const int s = (int)(q32 - (unsigned)j * (unsigned)hx);
+    const int p = (j + color) & 1;
+    const int i = 2 * s + p;
+    ok = ok && (i < nx);
+    valid[e] = ok;
+    qq[e] = q32;
+    cellid[e] = (unsigned)i + (unsigned)nx * (unsigned)j;
+    if (ok) {
+      a[e] = mc[q32];
+      // the other colour's slots of the -x, +x, -y, +y neighbours, relative to
+      // slot s of row j (periodic axes have even extents)
+      const float4 *P = mo + (long long)j * hx + s;
+      const bool hl = i > 0 || (pbc & 1), hr = i < nx - 1 || (pbc & 1);
+      const bool hu = j > 0 || (pbc & 2), hd = j < ny - 1 || (pbc & 2);
+      const int ol = i > 0 ? p - 1 : hx - 1;
+      const int orr = i < nx - 1 ? p : 1 - hx;
+      const int ou = j > 0 ? -hx : (ny - 1) * hx;
+      const int od = j < ny - 1 ? hx : -(ny - 1) * hx;
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      nb[e][0] = hl ? P[ol] : z4;
+      nb[e][1] = hr ? P[orr] : z4;
+      nb[e][2] = hu ? P[ou] : z4;
+      nb[e][3] = hd ? P[od] : z4;
+      pres[e][0] = hl ? 1.f : 0.f;
+      pres[e][1] = hr ? 1.f : 0.f;
+      pres[e][2] = hu ? 1.f : 0.f;
+      pres[e][3] = hd ? 1.f : 0.f;
+      if (grain) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (nb[e][b].w != a[e].w) pres[e][b] *= K.gscale;
+      }
+      M[e] = cell_material<PERCELL>(K, A.tab, S, (long long)color * S + q32);
+      if (flags & F_DEMAG) h[e] = A.heff[K.h_off + (long long)color * S + q32];
+      else h[e] = make_float4(M[e].zee * K.Bx, M[e].zee * K.By, M[e].zee * K.Bz, 0.f);
+    }
+  }
+
+  // 2. the trials
+  int accepted[kSweepCells];
+#pragma unroll
+  for (int e = 0; e < kSweepCells; ++e) {
+    accepted[e] = 0;
+    if (!valid[e]) continue;
+    const float wx = K.wx * M[e].bs, wy = K.wy * M[e].bs;
+    const float w[4] = {wx * pres[e][0], wx * pres[e][1], wy * pres[e][2], wy * pres[e][3]};
+    const uint4 r = philox4x32_10_rk(make_uint4(cellid[e], sweep, (unsigned)K.chain, 0u), A.rk);
+    const float u0 = uniform01(r.x), u1 = uniform01(r.y), u2 = uniform01(r.z), u3 = uniform01(r.w);
+    Move v = move_length(a[e], M[e].me2h, M[e].me2l);
+    move_direction(v, a[e], M[e].sigma, omc, u0, u1, u2);
+    const float floc = local_change_flat(v, a[e], nb[e], w, pres[e], K.cdx * M[e].bs, K.cdy * M[e].bs,
+                                         (flags & F_DMI) != 0, h[e].x, h[e].y, h[e].z);
+    const float flong = longitudinal_change(v, M[e].p2, M[e].p4);
+    const float fan = anisotropy_change(v, flags, M[e].k1, M[e].k2, M[e].ex, M[e].ey, M[e].ez);
+    const float dF = floc + flong + fan;
+    const float lg = log1p_move(v.tt);
+    const float dl = dF - 4.f * lg;
+    float dec;
+    if (DEBUG || dl > 0.f) dec = dl + __logf(u3);
+    else dec = dl;
+    accepted[e] = dec < 0.f;
+    if (accepted[e]) mc[qq[e]] = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
+    if (DEBUG) {
+      A.dec_dbg[cellid[e]] = dec;
+      A.acc_dbg[cellid[e]] = (signed char)accepted[e];
+    }
+  }
+
+  unsigned na = 0, nv = 0;
+#pragma unroll
+  for (int e = 0; e < kSweepCells; ++e) {
+    na += __popc(__ballot_sync(0xffffffffu, accepted[e]));
+    nv += __popc(__ballot_sync(0xffffffffu, valid[e]));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    wacc[warp] = na;
+    watt[warp] = nv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned sa = 0, sv = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < kSweepThreads / 32; ++w2) { sa += wacc[w2]; sv += watt[w2]; }
+    if (sv) {
+      atomicAdd(&A.st[c].win_acc, (unsigned long long)sa);
+      atomicAdd(&A.st[c].win_att, (unsigned long long)sv);
+    }
+  }
+}
+
 void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
   SweepArgs A;
   A.chains = P.chains; A.st = P.st; A.blk_desc = P.blk_desc;
@@ -176,16 +317,25 @@ void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
   A.sweep_off = P.sweep_off; A.key0 = P.key0; A.key1 = P.key1; A.color = P.color;
   A.omc_override = P.omc_override; A.dec_dbg = P.dec_dbg; A.acc_dbg = P.acc_dbg;
   A.nstripes = P.nstripes; A.stripe = P.stripe;
+  {
+    unsigned k0 = P.key0, k1 = P.key1;
+    for (int r = 0; r < 10; ++r) {
+      A.rk[2 * r] = k0;
+      A.rk[2 * r + 1] = k1;
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+  }
   const int v = (P.percell ? 4 : 0) | (P.dec_dbg != nullptr ? 2 : 0) | (P.flat ? 1 : 0);
   switch (v) {
     case 0: k_sweep_pass<false, false, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
-    case 1: k_sweep_pass<false, false, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    case 1: k_sweep_flat<false, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
     case 2: k_sweep_pass<false, true, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
-    case 3: k_sweep_pass<false, true, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    case 3: k_sweep_flat<false, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
     case 4: k_sweep_pass<true, false, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
-    case 5: k_sweep_pass<true, false, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    case 5: k_sweep_flat<true, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
     case 6: k_sweep_pass<true, true, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
-    default: k_sweep_pass<true, true, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    default: k_sweep_flat<true, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
   }
   ++*L.counter;
 }

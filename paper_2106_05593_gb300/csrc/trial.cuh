@@ -28,6 +28,8 @@ struct ChainK {
   long long m_off, h_off, t_off, ms_off;
 };
 
+constexpr int kChainKVec = 11;     // 16-byte vectors of ChainDev that ChainK unpacks
+
 __device__ __forceinline__ ChainK load_chain(const ChainDev *cd) {
   const int4 *iv = reinterpret_cast<const int4 *>(cd);
   const float4 *fv = reinterpret_cast<const float4 *>(cd);
@@ -47,6 +49,11 @@ __device__ __forceinline__ ChainK load_chain(const ChainDev *cd) {
   K.Bx = f4.x; K.By = f4.y; K.Bz = f4.z; K.Ms0 = f4.w;
   K.m_off = o0.x; K.h_off = o0.y; K.t_off = o1.x; K.ms_off = o1.y;
   return K;
+}
+
+// a chain's constants from a copy of its first kChainKVec vectors (shared memory)
+__device__ __forceinline__ ChainK load_chain_vec(const float4 *v) {
+  return load_chain(reinterpret_cast<const ChainDev *>(v));
 }
 
 // material constants of one cell
@@ -218,6 +225,32 @@ __device__ __forceinline__ float linear_change(const Move &v, const float4 nb[6]
     gz = -cdx * (w[1] * nb[1].x - w[0] * nb[0].x) - cdy * (w[3] * nb[3].y - w[2] * nb[2].y);
   }
   return v.dmx * (gx - hxs) + v.dmy * (gy - hys) + v.dmz * (gz - hzs);
+}
+
+// exchange (pair form of Eq. 10), interfacial DMI (pair form of Eq. 15) and the
+// Zeeman + frozen demag field (Eq. 14) of a cell of a one-cell-thick chain, as
+// one product dm . u: the exchange change sum_b w_b (|m' - m_b|^2 - |m - m_b|^2)
+// is sum_b w_b dm . (m' + m - 2 m_b); nb[0..3] are the -x, +x, -y, +y
+// neighbours, w[b] their full bond weights (0 for an absent bond), d[b] their
+// DMI presence weights, h the field term (kT per unit m).
+__device__ __forceinline__ float local_change_flat(const Move &v, float4 a, const float4 nb[4], const float w[4],
+                                                   const float d[4], float cdx, float cdy, bool dmi, float hx,
+                                                   float hy, float hz) {
+  const float sx = v.mpx + a.x, sy = v.mpy + a.y, sz = v.mpz + a.z;
+  float ux = -hx, uy = -hy, uz = -hz;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    ux = fmaf(w[b], fmaf(-2.f, nb[b].x, sx), ux);
+    uy = fmaf(w[b], fmaf(-2.f, nb[b].y, sy), uy);
+    uz = fmaf(w[b], fmaf(-2.f, nb[b].z, sz), uz);
+  }
+  if (dmi) {
+    ux = fmaf(cdx, d[1] * nb[1].z - d[0] * nb[0].z, ux);
+    uy = fmaf(cdy, d[3] * nb[3].z - d[2] * nb[2].z, uy);
+    uz = fmaf(-cdx, d[1] * nb[1].x - d[0] * nb[0].x, uz);
+    uz = fmaf(-cdy, d[3] * nb[3].y - d[2] * nb[2].y, uz);
+  }
+  return v.dmx * ux + v.dmy * uy + v.dmz * uz;
 }
 
 // longitudinal term (exponent of Eq. 7): dq = m'^2 - m^2 = m^2 t (2 + t)
