@@ -135,6 +135,12 @@ typedef struct {
                                  numbers of chain c of a batch, so the plain and
                                  batched forms of the same chain are the same
                                  Markov chain, bit for bit.                      [0] */
+    int sweep_variant;        /* sublattice pass of batches whose chains are all
+                                 one cell thick with uniform material: 0 time the
+                                 occupancies at create (on a saved copy of the
+                                 initial state) and keep the fastest, 1, 2, 3 = 6,
+                                 7, 8 blocks of 128 threads per SM.  Results are
+                                 identical for any value.                       [0] */
 } mmc_options;
 
 /* One chain of a batch. T_cell (optional, HOST) gives a per-cell temperature;
@@ -377,6 +383,12 @@ mmc_status mmc_phase_times(mmc_ctx *ctx, int64_t n, uint64_t seed, double ms[6],
  * repeat bit for bit across contexts.  (HOST outputs.)  Not a paper quantity: a
  * tuning record of this implementation. */
 mmc_status mmc_fft_tuning(const mmc_ctx *ctx, int *variant, double ms[4]);
+
+/* Occupancy variant of the batch's sublattice pass (mmc_options.sweep_variant;
+ * 0 when the batch does not use the one-cell-thick uniform pass) and, when it
+ * was timed at create, the per-pass times in ms of the three variants (HOST
+ * outputs).  A tuning record of this implementation, not a paper quantity. */
+mmc_status mmc_sweep_tuning(const mmc_ctx *ctx, int *variant, double ms[3]);
 
 /* Number of kernels the library launched since create (all kinds). */
 int64_t mmc_kernel_launches(const mmc_ctx *ctx);

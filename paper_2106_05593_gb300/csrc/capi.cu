@@ -188,6 +188,8 @@ struct mmc_ctx {
   std::vector<ChainGroup> groups;
   cudaEvent_t ev_fork = nullptr;
   int tuned_variant = 0;                // FFT variant picked at create (0: not tuned)
+  int sweep_variant = 3;                // production pass occupancy of uniform one-cell-thick batches
+  double sweep_ms[3] = {0.0, 0.0, 0.0}; // per-pass time of the three occupancies when timed
   double tune_ms[4] = {0.0, 0.0, 0.0, 0.0};  // per-update time of the variants when tuned
   std::vector<DemagPlan> single[2];     // per chain and precision (0 FP32, 1 FP64), built lazily
   // serial exact-demag sweep: real-space tensors per set, proposals scratch
@@ -752,6 +754,7 @@ SweepLaunch sweep_launch(mmc_ctx *c, int color, unsigned off, unsigned key0, uns
   P.nstripes = 1;
   P.stripe = 0;
   P.flat = c->all_flat;
+  P.variant = c->sweep_variant;
   return P;
 }
 
@@ -1021,6 +1024,7 @@ mmc_status mmc_default_options(mmc_options *o) {
   o->demag_self = 0;
   o->fft_variant = 0;
   o->demag_stripes = 1;
+  o->sweep_variant = 0;
   return MMC_OK;
 }
 
@@ -1326,6 +1330,50 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     cudaEventDestroy(e1);
     c->batch_plan.fft_variant = pick;
     c->tuned_variant = pick;
+  }
+  if (o.sweep_variant >= 1 && o.sweep_variant <= 3) c->sweep_variant = o.sweep_variant;
+  if (c->all_flat && !c->any_percell && o.sweep_variant == 0) {
+    // time the three occupancies of the production pass on this batch (both
+    // colours, five times each) on the initial state, which is saved first and
+    // put back afterwards (the timing passes are real moves)
+    void *save_m = nullptr, *save_st = nullptr;
+    const size_t bm = (size_t)c->m_total * sizeof(float4), bs = (size_t)nchains * sizeof(ChainState);
+    CUDA_TRY_OR(cudaMalloc(&save_m, bm));
+    if (cudaMalloc(&save_st, bs) != cudaSuccess) {
+      cudaFree(save_m);
+      mmc_destroy(c);
+      return fail(MMC_ERR_NOMEM, "cudaMalloc of the tuning copy failed");
+    }
+    cudaMemcpyAsync(save_m, c->d_m, bm, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(save_st, c->d_st, bs, cudaMemcpyDeviceToDevice, c->stream);
+    if (c->any_demag) issue_demag(c);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int pick = 3;
+    for (int v = 1; v <= 3; ++v) {
+      c->sweep_variant = v;
+      for (int r = 0; r < 6; ++r) {
+        if (r == 1) cudaEventRecord(e0, c->stream);
+        for (int color = 0; color < 2; ++color) launch_sweep_pass(c->L(), sweep_launch(c, color, 0, 1u, 0u));
+      }
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      c->sweep_ms[v - 1] = ms / 10.0;
+      if (ms < best) { best = ms; pick = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->sweep_variant = pick;
+    cudaMemcpyAsync(c->d_m, save_m, bm, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->d_st, save_st, bs, cudaMemcpyDeviceToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(save_m);
+    cudaFree(save_st);
+    CUDA_TRY_OR(cudaGetLastError());
   }
   if (o.stream_groups != 1 && nchains >= 2 && !o.demag_cufft) {
     // two groups of contiguous chains with about equal cell counts
@@ -1960,6 +2008,13 @@ mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[6], i
 }
 
 int64_t mmc_kernel_launches(const mmc_ctx *c) { return c ? c->launches : 0; }
+
+mmc_status mmc_sweep_tuning(const mmc_ctx *c, int *variant, double ms[3]) {
+  if (!c || !variant || !ms) return fail(MMC_ERR_ARG, "null argument");
+  *variant = c->all_flat && !c->any_percell ? c->sweep_variant : 0;
+  for (int k = 0; k < 3; ++k) ms[k] = c->sweep_ms[k];
+  return MMC_OK;
+}
 
 mmc_status mmc_fft_tuning(const mmc_ctx *c, int *variant, double ms[4]) {
   if (!c || !variant || !ms) return fail(MMC_ERR_ARG, "null argument");

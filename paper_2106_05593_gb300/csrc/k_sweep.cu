@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 7) k_sweep_pass(S
 // slot in the other colour (s - 1 + p, s + p in the row, s in the rows j -+ 1,
 // with the periodic wrap at the edges); exchange, DMI and the field act through
 // one local vector (local_change_flat).
-template <bool PERCELL, bool DEBUG>
-__global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 8) k_sweep_flat(SweepArgs A) {
+template <bool PERCELL, bool DEBUG, int MINB>
+__global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_flat(SweepArgs A) {
   __shared__ float4 skv[kChainKVec];
   __shared__ unsigned wacc[kSweepThreads / 32], watt[kSweepThreads / 32];
   const int2 bd = A.blk_desc[A.blk_base + (int)blockIdx.x];
@@ -256,7 +256,20 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 8) k_sweep_flat(S
     }
   }
 
-  // 2. the trials
+  // 2. the random numbers and the parts of the moves that do not depend on m,
+  // while the loads are in flight
+  MoveAngles ga[kSweepCells];
+  float u3v[kSweepCells], lgv[kSweepCells];
+#pragma unroll
+  for (int e = 0; e < kSweepCells; ++e) {
+    const uint4 r = philox4x32_10_rk(make_uint4(cellid[e], sweep, (unsigned)K.chain, 0u), A.rk);
+    const float sig = PERCELL ? (valid[e] ? M[e].sigma : 0.f) : K.sigma;
+    ga[e] = move_angles(sig, omc, uniform01(r.x), uniform01(r.y), uniform01(r.z));
+    u3v[e] = uniform01(r.w);
+    lgv[e] = log1p_move(ga[e].tt);
+  }
+
+  // 3. the trials
   int accepted[kSweepCells];
 #pragma unroll
   for (int e = 0; e < kSweepCells; ++e) {
@@ -264,17 +277,15 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 8) k_sweep_flat(S
     if (!valid[e]) continue;
     const float wx = K.wx * M[e].bs, wy = K.wy * M[e].bs;
     const float w[4] = {wx * pres[e][0], wx * pres[e][1], wy * pres[e][2], wy * pres[e][3]};
-    const uint4 r = philox4x32_10_rk(make_uint4(cellid[e], sweep, (unsigned)K.chain, 0u), A.rk);
-    const float u0 = uniform01(r.x), u1 = uniform01(r.y), u2 = uniform01(r.z), u3 = uniform01(r.w);
+    const float u3 = u3v[e];
     Move v = move_length(a[e], M[e].me2h, M[e].me2l);
-    move_direction(v, a[e], M[e].sigma, omc, u0, u1, u2);
+    move_direction_g(v, a[e], ga[e]);
     const float floc = local_change_flat(v, a[e], nb[e], w, pres[e], K.cdx * M[e].bs, K.cdy * M[e].bs,
                                          (flags & F_DMI) != 0, h[e].x, h[e].y, h[e].z);
     const float flong = longitudinal_change(v, M[e].p2, M[e].p4);
     const float fan = anisotropy_change(v, flags, M[e].k1, M[e].k2, M[e].ex, M[e].ey, M[e].ez);
     const float dF = floc + flong + fan;
-    const float lg = log1p_move(v.tt);
-    const float dl = dF - 4.f * lg;
+    const float dl = dF - 4.f * lgv[e];
     float dec;
     if (DEBUG || dl > 0.f) dec = dl + __logf(u3);
     else dec = dl;
@@ -327,15 +338,22 @@ void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
     }
   }
   const int v = (P.percell ? 4 : 0) | (P.dec_dbg != nullptr ? 2 : 0) | (P.flat ? 1 : 0);
+  const dim3 g(P.nblocks), b(kSweepThreads);
   switch (v) {
-    case 0: k_sweep_pass<false, false, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
-    case 1: k_sweep_flat<false, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
-    case 2: k_sweep_pass<false, true, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
-    case 3: k_sweep_flat<false, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
-    case 4: k_sweep_pass<true, false, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
-    case 5: k_sweep_flat<true, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
-    case 6: k_sweep_pass<true, true, false><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
-    default: k_sweep_flat<true, true><<<P.nblocks, kSweepThreads, 0, L.stream>>>(A); break;
+    case 0: k_sweep_pass<false, false, false><<<g, b, 0, L.stream>>>(A); break;
+    case 1:
+      // the production pass of uniform one-cell-thick chains comes in three
+      // occupancies (blocks per SM), picked by timing at create
+      if (P.variant == 1) k_sweep_flat<false, false, 6><<<g, b, 0, L.stream>>>(A);
+      else if (P.variant == 2) k_sweep_flat<false, false, 7><<<g, b, 0, L.stream>>>(A);
+      else k_sweep_flat<false, false, 8><<<g, b, 0, L.stream>>>(A);
+      break;
+    case 2: k_sweep_pass<false, true, false><<<g, b, 0, L.stream>>>(A); break;
+    case 3: k_sweep_flat<false, true, 8><<<g, b, 0, L.stream>>>(A); break;
+    case 4: k_sweep_pass<true, false, false><<<g, b, 0, L.stream>>>(A); break;
+    case 5: k_sweep_flat<true, false, 5><<<g, b, 0, L.stream>>>(A); break;
+    case 6: k_sweep_pass<true, true, false><<<g, b, 0, L.stream>>>(A); break;
+    default: k_sweep_flat<true, true, 5><<<g, b, 0, L.stream>>>(A); break;
   }
   ++*L.counter;
 }

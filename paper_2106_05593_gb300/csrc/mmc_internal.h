@@ -193,6 +193,7 @@ struct SweepLaunch {
   signed char *acc_dbg;
   int nstripes, stripe;         // nstripes > 1: only the band `stripe` of rows of every chain
   bool flat;                    // every chain has nz == 1
+  int variant;                  // uniform one-cell-thick production pass: 1, 2, 3 = 6, 7, 8 blocks per SM
 };
 void launch_sweep_pass(const Launch &L, const SweepLaunch &P);
 void launch_advance(const Launch &L, ChainState *st, int nchains, unsigned by, unsigned *sweep_base,

@@ -190,6 +190,38 @@ __device__ __forceinline__ void move_direction(Move &v, float4 a, float sigma, f
   v.dmx = v.mpx - a.x; v.dmy = v.mpy - a.y; v.dmz = v.mpz - a.z;
 }
 
+// The parts of a move that depend only on its random numbers, not on m: the
+// cone's cos / sin, the azimuth's cos / sin and the length factor (the same
+// operations as move_direction), so that they can run while m is being loaded.
+struct MoveAngles {
+  float ct, st, cp, sp, tt;
+};
+__device__ __forceinline__ MoveAngles move_angles(float sigma, float omc, float u0, float u1, float u2) {
+  MoveAngles g;
+  const float t = u0 * omc;
+  g.ct = 1.f - t;
+  const float t2 = t * (2.f - t);
+  g.st = t2 * rsqrtf(t2);
+  sincospi_move(2.f * u1, g.sp, g.cp);
+  g.tt = sigma * (2.f * u2 - 1.f);
+  return g;
+}
+// move_direction with the angles given
+__device__ __forceinline__ void move_direction_g(Move &v, float4 a, const MoveAngles &g) {
+  const float sg = v.n2 >= 0.f ? 1.f : -1.f;
+  const float aa = -__fdividef(1.f, sg + v.n2);
+  const float bb = v.n0 * v.n1 * aa;
+  const float e1x = 1.f + sg * v.n0 * v.n0 * aa, e1y = sg * bb, e1z = -sg * v.n0;
+  const float e2x = bb, e2y = sg + v.n1 * v.n1 * aa, e2z = -v.n1;
+  v.dx = g.ct * v.n0 + g.st * (g.cp * e1x + g.sp * e2x);
+  v.dy = g.ct * v.n1 + g.st * (g.cp * e1y + g.sp * e2y);
+  v.dz = g.ct * v.n2 + g.st * (g.cp * e1z + g.sp * e2z);
+  v.tt = g.tt;
+  const float ls = v.len * (1.f + v.tt);
+  v.mpx = ls * v.dx; v.mpy = ls * v.dy; v.mpz = ls * v.dz;
+  v.dmx = v.mpx - a.x; v.dmy = v.mpy - a.y; v.dmz = v.mpz - a.z;
+}
+
 // exchange (pair form of Eq. 10): sum_j w_j (|m' - m_j|^2 - |m - m_j|^2)
 __device__ __forceinline__ float exchange_change(const Move &v, float4 a, const float4 nb[6], const float w[6],
                                                  float wx, float wy, float wz, bool has_z) {
