@@ -510,9 +510,6 @@ def run_ours(args):
                 compare["fp64_demag"] = fp64_demag_compare(MMC, specs, seed, stream, cells_per_step)
                 compare["demag_update_ms"]["own_fp64"] = compare["fp64_demag"]["demag_update_ms"]
             v, tms = g.fft_tuning()
-            sv, sms = g.sweep_tuning()
-            compare["sweep_variant"] = {"picked_blocks_per_sm": {0: None, 1: 6, 2: 7, 3: 8}[sv],
-                                        "create_time_ms_per_pass": {"6": sms[0], "7": sms[1], "8": sms[2]}}
             compare["fft_variant"] = {"picked": {0: None, 1: "radix16", 2: "radix32", 3: "radix16x2", 4: "warp32x32"}[v],
                                       "create_time_ms": {"radix16": tms[0], "radix32": tms[1],
                                                          "radix16x2": tms[2], "warp32x32": tms[3]}}

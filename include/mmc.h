@@ -49,7 +49,7 @@ typedef enum {
     MMC_OK = 0,
     MMC_ERR_ARG = -1,         /* invalid argument (null, T <= 0, odd periodic extent, ...) */
     MMC_ERR_CUDA = -2,        /* a CUDA runtime / cuFFT call failed */
-    MMC_ERR_TIMEOUT = -3,     /* a bounded device-side wait gave up */
+    MMC_ERR_TIMEOUT = -3,     /* a bounded device-side wait gave up (reported by mmc_observables) */
     MMC_ERR_NONFINITE = -4,   /* non-finite values in input or state */
     MMC_ERR_UNSUPPORTED = -5, /* a combination the library does not implement */
     MMC_ERR_NOMEM = -6        /* device or host allocation failed */
@@ -135,12 +135,20 @@ typedef struct {
                                  numbers of chain c of a batch, so the plain and
                                  batched forms of the same chain are the same
                                  Markov chain, bit for bit.                      [0] */
-    int sweep_variant;        /* sublattice pass of batches whose chains are all
-                                 one cell thick with uniform material: 0 time the
-                                 occupancies at create (on a saved copy of the
-                                 initial state) and keep the fastest, 1, 2, 3 = 6,
-                                 7, 8 blocks of 128 threads per SM.  Results are
-                                 identical for any value.                       [0] */
+    int sweep_tiles;          /* 1: batches whose chains are all one cell thick,
+                                 with uniform material and at most 1024 cells per
+                                 row, run the sublattice pass on shared-memory
+                                 halo tiles: bands of rows brought in by bulk
+                                 asynchronous copies while the previous band is
+                                 computed; 0: the per-block pass.  Same moves
+                                 either way.                                    [1] */
+    int wait_polls;           /* bound of a kernel's wait for its copies, in polls
+                                 of the barrier (0: 2^22, about a second); a wait
+                                 that runs out skips its band and makes the next
+                                 mmc_observables return MMC_ERR_TIMEOUT          [0] */
+    int wait_test;            /* test hook for that path: 1 makes every band wait
+                                 for 16 bytes that no copy delivers, so every wait
+                                 runs out (no band is updated)                  [0] */
 } mmc_options;
 
 /* One chain of a batch. T_cell (optional, HOST) gives a per-cell temperature;
@@ -384,11 +392,6 @@ mmc_status mmc_phase_times(mmc_ctx *ctx, int64_t n, uint64_t seed, double ms[6],
  * tuning record of this implementation. */
 mmc_status mmc_fft_tuning(const mmc_ctx *ctx, int *variant, double ms[4]);
 
-/* Occupancy variant of the batch's sublattice pass (mmc_options.sweep_variant;
- * 0 when the batch does not use the one-cell-thick uniform pass) and, when it
- * was timed at create, the per-pass times in ms of the three variants (HOST
- * outputs).  A tuning record of this implementation, not a paper quantity. */
-mmc_status mmc_sweep_tuning(const mmc_ctx *ctx, int *variant, double ms[3]);
 
 /* Number of kernels the library launched since create (all kinds). */
 int64_t mmc_kernel_launches(const mmc_ctx *ctx);

@@ -188,8 +188,6 @@ struct mmc_ctx {
   std::vector<ChainGroup> groups;
   cudaEvent_t ev_fork = nullptr;
   int tuned_variant = 0;                // FFT variant picked at create (0: not tuned)
-  int sweep_variant = 3;                // production pass occupancy of uniform one-cell-thick batches
-  double sweep_ms[3] = {0.0, 0.0, 0.0}; // per-pass time of the three occupancies when timed
   double tune_ms[4] = {0.0, 0.0, 0.0, 0.0};  // per-update time of the variants when tuned
   std::vector<DemagPlan> single[2];     // per chain and precision (0 FP32, 1 FP64), built lazily
   // serial exact-demag sweep: real-space tensors per set, proposals scratch
@@ -208,6 +206,12 @@ struct mmc_ctx {
   signed char *d_acc = nullptr;
   long long max_ncell = 0, max_slots = 0;
   bool all_flat = true;                 // every chain one cell thick (nz == 1)
+  // banded sublattice pass with shared-memory halo tiles (k_sweep_band)
+  bool band = false;
+  int4 *d_items = nullptr;              // per band: (chain, first row, rows, 0), by chain
+  std::vector<int> item_first;          // first item of every chain (nchains + 1 entries)
+  int band_grid = 0, stage_own = 0, stage_other = 0;
+  int *d_err = nullptr;                 // device error word of the kernels' bounded waits
   long long launches = 0;
   uint64_t host_sweep = 0;
   bool heff_stale = true;               // state or field changed since the last demag update
@@ -754,7 +758,16 @@ SweepLaunch sweep_launch(mmc_ctx *c, int color, unsigned off, unsigned key0, uns
   P.nstripes = 1;
   P.stripe = 0;
   P.flat = c->all_flat;
-  P.variant = c->sweep_variant;
+  P.band = c->band;
+  P.items = c->d_items;
+  P.i0 = 0;
+  P.i1 = c->band ? c->item_first.back() : 0;
+  P.band_grid = c->band_grid;
+  P.stage_own = c->stage_own;
+  P.stage_other = c->stage_other;
+  P.max_polls = c->opt.wait_polls > 0 ? (unsigned)c->opt.wait_polls : (1u << 22);
+  P.err = c->d_err;
+  P.wait_test = c->opt.wait_test;
   return P;
 }
 
@@ -854,6 +867,10 @@ void issue_block(mmc_ctx *c, int k, unsigned key0, unsigned key1, int sample_eve
             SweepLaunch P = sweep_launch(c, color, (unsigned)off, key0, key1);
             P.blk_base = b0;
             P.nblocks = nb;
+            if (c->band) {
+              P.i0 = c->item_first[(size_t)g.c0];
+              P.i1 = c->item_first[(size_t)g.c1];
+            }
             P.nstripes = nbands;
             P.stripe = band;
             launch_sweep_pass(Lg, P);
@@ -1024,7 +1041,9 @@ mmc_status mmc_default_options(mmc_options *o) {
   o->demag_self = 0;
   o->fft_variant = 0;
   o->demag_stripes = 1;
-  o->sweep_variant = 0;
+  o->sweep_tiles = 1;
+  o->wait_polls = 0;
+  o->wait_test = 0;
   return MMC_OK;
 }
 
@@ -1276,6 +1295,34 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     std::vector<int2> bd(bc.size());
     for (size_t b = 0; b < bc.size(); ++b) bd[b] = make_int2(bc[b], (int)((long long)b - bf[(size_t)bc[b]]));
     MMC_TRY_OR(upload(c, &c->d_sw_desc, bd));
+    // bands of the banded pass: R rows of a chain with R hx <= 512 slots
+    bool band = o.sweep_tiles != 0 && c->all_flat && !c->any_percell;
+    for (int ci = 0; ci < nchains && band; ++ci) band = c->ch[ci].hx <= 512;
+    if (band) {
+      std::vector<int4> items;
+      int own = 0, other = 0;
+      for (int ci = 0; ci < nchains; ++ci) {
+        const ChainDev &D = c->ch[ci];
+        const int R = std::max(1, 512 / D.hx);
+        c->item_first.push_back((int)items.size());
+        for (int r0 = 0; r0 < D.ny; r0 += R) items.push_back(make_int4(ci, r0, std::min(R, D.ny - r0), 0));
+        own = std::max(own, R * D.hx);
+        other = std::max(other, (R + 2) * D.hx);
+      }
+      c->item_first.push_back((int)items.size());
+      MMC_TRY_OR(upload(c, &c->d_items, items));
+      c->stage_own = own;
+      c->stage_other = other;
+      const size_t bytes = band_smem_bytes(own, other);
+      CUDA_TRY_OR(band_set_smem(bytes));
+      int dev = 0, nsm = 1;
+      CUDA_TRY_OR(cudaGetDevice(&dev));
+      CUDA_TRY_OR(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      c->band_grid = band_blocks_per_sm(bytes) * nsm;
+      c->band = true;
+    }
+    MMC_TRY_OR(dalloc_t(c, &c->d_err, 1));
+    CUDA_TRY_OR(cudaMemset(c->d_err, 0, sizeof(int)));
     std::vector<int> oc;
     std::vector<long long> of;
     for (int ci = 0; ci < nchains; ++ci) {
@@ -1330,50 +1377,6 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     cudaEventDestroy(e1);
     c->batch_plan.fft_variant = pick;
     c->tuned_variant = pick;
-  }
-  if (o.sweep_variant >= 1 && o.sweep_variant <= 3) c->sweep_variant = o.sweep_variant;
-  if (c->all_flat && !c->any_percell && o.sweep_variant == 0) {
-    // time the three occupancies of the production pass on this batch (both
-    // colours, five times each) on the initial state, which is saved first and
-    // put back afterwards (the timing passes are real moves)
-    void *save_m = nullptr, *save_st = nullptr;
-    const size_t bm = (size_t)c->m_total * sizeof(float4), bs = (size_t)nchains * sizeof(ChainState);
-    CUDA_TRY_OR(cudaMalloc(&save_m, bm));
-    if (cudaMalloc(&save_st, bs) != cudaSuccess) {
-      cudaFree(save_m);
-      mmc_destroy(c);
-      return fail(MMC_ERR_NOMEM, "cudaMalloc of the tuning copy failed");
-    }
-    cudaMemcpyAsync(save_m, c->d_m, bm, cudaMemcpyDeviceToDevice, c->stream);
-    cudaMemcpyAsync(save_st, c->d_st, bs, cudaMemcpyDeviceToDevice, c->stream);
-    if (c->any_demag) issue_demag(c);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best = 1e30f;
-    int pick = 3;
-    for (int v = 1; v <= 3; ++v) {
-      c->sweep_variant = v;
-      for (int r = 0; r < 6; ++r) {
-        if (r == 1) cudaEventRecord(e0, c->stream);
-        for (int color = 0; color < 2; ++color) launch_sweep_pass(c->L(), sweep_launch(c, color, 0, 1u, 0u));
-      }
-      cudaEventRecord(e1, c->stream);
-      cudaEventSynchronize(e1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      c->sweep_ms[v - 1] = ms / 10.0;
-      if (ms < best) { best = ms; pick = v; }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    c->sweep_variant = pick;
-    cudaMemcpyAsync(c->d_m, save_m, bm, cudaMemcpyDeviceToDevice, c->stream);
-    cudaMemcpyAsync(c->d_st, save_st, bs, cudaMemcpyDeviceToDevice, c->stream);
-    cudaStreamSynchronize(c->stream);
-    cudaFree(save_m);
-    cudaFree(save_st);
-    CUDA_TRY_OR(cudaGetLastError());
   }
   if (o.stream_groups != 1 && nchains >= 2 && !o.demag_cufft) {
     // two groups of contiguous chains with about equal cell counts
@@ -1639,6 +1642,10 @@ mmc_status mmc_pass_debug(mmc_ctx *c, int chain, int color, uint32_t sweep, uint
   P.sweep_base = c->d_dbg_sweep;
   P.blk_base = (int)c->sw_first[chain];
   P.nblocks = (int)(c->sw_first[chain + 1] - c->sw_first[chain]);
+  if (c->band) {
+    P.i0 = c->item_first[(size_t)chain];
+    P.i1 = c->item_first[(size_t)chain + 1];
+  }
   P.omc_override = (float)(1.0 - std::cos(theta_deg * kPi / 180.0));
   P.dec_dbg = c->d_dec;
   P.acc_dbg = c->d_acc;
@@ -1653,10 +1660,25 @@ mmc_status mmc_pass_debug(mmc_ctx *c, int chain, int color, uint32_t sweep, uint
   return MMC_OK;
 }
 
+// the error word of the kernels' bounded waits: a wait that gave up since the
+// last check makes this call fail with MMC_ERR_TIMEOUT (and clears the word)
+static mmc_status take_device_error(mmc_ctx *c) {
+  if (!c->d_err) return MMC_OK;
+  int e = 0;
+  CUDA_TRY(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (e == 0) return MMC_OK;
+  CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return fail(MMC_ERR_TIMEOUT, "a band of the sublattice pass gave up waiting for its copies; the bands that "
+                               "gave up were not updated");
+}
+
 mmc_status mmc_observables(mmc_ctx *c, int chain, mmc_obs *out, int reset) {
   Trace trace("mmc_observables");
   MMC_TRY(check_chain(c, chain));
   if (!out) return fail(MMC_ERR_ARG, "null output");
+  MMC_TRY(take_device_error(c));
   ChainState s;
   CUDA_TRY(cudaMemcpyAsync(&s, c->d_st + chain, sizeof(ChainState), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -2008,13 +2030,6 @@ mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[6], i
 }
 
 int64_t mmc_kernel_launches(const mmc_ctx *c) { return c ? c->launches : 0; }
-
-mmc_status mmc_sweep_tuning(const mmc_ctx *c, int *variant, double ms[3]) {
-  if (!c || !variant || !ms) return fail(MMC_ERR_ARG, "null argument");
-  *variant = c->all_flat && !c->any_percell ? c->sweep_variant : 0;
-  for (int k = 0; k < 3; ++k) ms[k] = c->sweep_ms[k];
-  return MMC_OK;
-}
 
 mmc_status mmc_fft_tuning(const mmc_ctx *c, int *variant, double ms[4]) {
   if (!c || !variant || !ms) return fail(MMC_ERR_ARG, "null argument");

@@ -16,10 +16,12 @@
 // is exchange + DMI (pair sums, Eqs. 10, 15) + anisotropy (Eq. 11 / 12) +
 // Zeeman and frozen demag field (Eq. 14) + longitudinal (Eq. 7); the move is
 // accepted iff dF/kT - 4 ln(m'/m) + ln u3 < 0 (Eq. 5).
+#include <algorithm>
 #include <cstdio>
 
 #include "mmc_internal.h"
 #include "philox.cuh"
+#include "tma.cuh"
 #include "trial.cuh"
 
 namespace mmc {
@@ -41,6 +43,13 @@ struct SweepArgs {
   signed char *acc_dbg;
   int nstripes, stripe;     // nstripes > 1: the band of rows [r0, r1) of the stripe only
   unsigned rk[20];          // Philox round keys of (key0, key1), see philox4x32_10_rk
+  // banded pass (k_sweep_band): work items [i0, i1) of the item table
+  const int4 *items;        // per band: (chain, first row, rows, 0)
+  int i0, i1;
+  int stage_own, stage_other;   // float4 capacity of a stage's own-colour and other-colour tiles
+  unsigned max_polls;       // bound of a wait for a band's copies
+  int *err;                 // device error word (MMC_ERR_TIMEOUT on a wait that gave up)
+  int wait_test;            // test hook: every band's barrier waits for 16 bytes no copy delivers
 };
 
 // A thread handles kSweepCells cells of its block's 256 slots (slot t + j 128):
@@ -320,6 +329,228 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_flat(SweepArgs A)
   }
 }
 
+// Banded pass with shared-memory halo tiles, for batches of uniform one-cell-
+// thick chains.  Work items are bands of R rows of one chain (R hx <= 512 slots);
+// a block walks the items blockIdx.x, blockIdx.x + gridDim.x, ... and, while it
+// computes one band, one thread has the bulk-copy engine bring the next band
+// into the other of two shared-memory stages: the band's own-colour rows, the
+// other colour's rows r0 - 1 .. r0 + R (the halo rows, wrapped on periodic y
+// axes, left out at open edges) and the h_eff rows.  Every neighbour of a band's
+// cell is then in shared memory: the -x, +x neighbours in the other colour's
+// row at slots s - 1 + p, s + p, the -y, +y neighbours in the rows above and
+// below at slot s.  The moves are those of k_sweep_flat, cell for cell.
+constexpr int kBandThreads = 256;
+constexpr int kBandCells = 2;                // cells per thread: 512 slots per band at most
+
+struct BandStage {
+  float4 *own, *other, *heff;
+};
+
+__device__ __forceinline__ BandStage band_stage(unsigned char *base, int k, const SweepArgs &A) {
+  float4 *b = reinterpret_cast<float4 *>(base) + (size_t)k * (2 * A.stage_own + A.stage_other);
+  return BandStage{b, b + A.stage_own, b + A.stage_own + A.stage_other};
+}
+
+// one thread: arm bar with the bytes of item `it` and start its copies into stage g
+// (extra: bytes the barrier waits for beyond the copies, a test hook whose
+// barrier never completes)
+__device__ __forceinline__ void band_issue(const SweepArgs &A, int4 it, const BandStage &g, uint64_t *bar,
+                                           unsigned extra) {
+  const ChainDev &ch = A.chains[it.x];
+  const bool demag = (ch.flags & F_DEMAG) != 0;
+  const int hx = ch.hx, ny = ch.ny, r0 = it.y, nr = it.z;
+  const long long S = (long long)ch.nrows * hx;
+  const float4 *own = A.m + ch.m_off + (long long)A.color * S;
+  const float4 *oth = A.m + ch.m_off + (long long)(1 - A.color) * S;
+  const unsigned row_b = (unsigned)hx * 16u;
+  const bool pby = (ch.pbc & 2) != 0;
+  const int rb = r0 > 0 ? r0 - 1 : (pby ? ny - 1 : -1);
+  const int ra = r0 + nr < ny ? r0 + nr : (pby ? 0 : -1);
+  unsigned bytes = 2u * (unsigned)nr * row_b + (rb >= 0 ? row_b : 0u) + (ra >= 0 ? row_b : 0u);
+  if (demag) bytes += (unsigned)nr * row_b;
+  mbar_arrive_expect_tx(bar, bytes + extra);
+  bulk_g2s(g.own, own + (long long)r0 * hx, (unsigned)nr * row_b, bar);
+  bulk_g2s(g.other + hx, oth + (long long)r0 * hx, (unsigned)nr * row_b, bar);
+  if (rb >= 0) bulk_g2s(g.other, oth + (long long)rb * hx, row_b, bar);
+  if (ra >= 0) bulk_g2s(g.other + (long long)(nr + 1) * hx, oth + (long long)ra * hx, row_b, bar);
+  if (demag) bulk_g2s(g.heff, A.heff + ch.h_off + (long long)A.color * S + (long long)r0 * hx, (unsigned)nr * row_b, bar);
+}
+
+template <bool DEBUG>
+__global__ void __launch_bounds__(kBandThreads, 2) k_sweep_band(SweepArgs A) {
+  extern __shared__ __align__(16) unsigned char band_smem[];
+  __shared__ uint64_t bar[2];
+  __shared__ float4 skv[kChainKVec];
+  __shared__ unsigned wacc[2][kBandThreads / 32], watt[2][kBandThreads / 32];
+  __shared__ int abort_band;
+  const int G = (int)gridDim.x;
+  const unsigned extra = A.wait_test ? 16u : 0u;
+  const unsigned sweep = *A.sweep_base + A.sweep_off;
+  const int color = A.color;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+    abort_band = 0;
+  }
+  __syncthreads();
+  int item = A.i0 + (int)blockIdx.x;
+  if (threadIdx.x == 0 && item < A.i1) band_issue(A, A.items[item], band_stage(band_smem, 0, A), &bar[0], extra);
+  int prev_c = -1, k = 0;
+  for (; item < A.i1; ++k, item += G) {
+    const int st = k & 1;
+    const int4 it = A.items[item];
+    if (threadIdx.x == 0) {
+      const int nxt = item + G;
+      if (nxt < A.i1) {
+        fence_proxy_async_smem();
+        band_issue(A, A.items[nxt], band_stage(band_smem, st ^ 1, A), &bar[st ^ 1], extra);
+      }
+      if (prev_c >= 0) {                      // counts of the previous band
+        unsigned sa = 0, sv = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kBandThreads / 32; ++w2) { sa += wacc[st ^ 1][w2]; sv += watt[st ^ 1][w2]; }
+        if (sv) {
+          atomicAdd(&A.st[prev_c].win_acc, (unsigned long long)sa);
+          atomicAdd(&A.st[prev_c].win_att, (unsigned long long)sv);
+        }
+      }
+    }
+    if (threadIdx.x < kChainKVec) skv[threadIdx.x] = __ldg(reinterpret_cast<const float4 *>(A.chains + it.x) + threadIdx.x);
+    if (!mbar_wait(&bar[st], (unsigned)(k >> 1) & 1u, A.max_polls)) {
+      abort_band = 1;
+      atomicExch(A.err, (int)MMC_ERR_TIMEOUT_CODE);
+    }
+    __syncthreads();
+    if (abort_band) break;
+    const ChainK K = load_chain_vec(skv);
+    const int c = it.x, r0 = it.y, nr = it.z;
+    const int nx = K.nx, ny = K.ny, hx = K.hx;
+    const int pbc = K.pbc & 3;
+    const long long S = (long long)K.nrows * hx;
+    float4 *mc = A.m + K.m_off + (long long)color * S;
+    const BandStage g = band_stage(band_smem, st, A);
+    const float omc = A.omc_override >= 0.f ? A.omc_override : A.st[c].omc;
+    const int flags = K.flags;
+    const unsigned nslots = (unsigned)(nr * hx);
+
+    bool valid[kBandCells];
+    unsigned ql[kBandCells], cellid[kBandCells];
+    float4 a[kBandCells], h[kBandCells], nb[kBandCells][4];
+    float pres[kBandCells][4];
+#pragma unroll
+    for (int e = 0; e < kBandCells; ++e) {
+      const unsigned q = threadIdx.x + (unsigned)(e * kBandThreads);
+      bool ok = q < nslots;
+      const int rl = ok ? (int)divq(q, K.hx_m, K.hx_l) : 0;
+      const int s = (int)(q - (unsigned)rl * (unsigned)hx);
+      const int j = r0 + rl;
+      const int p = (j + color) & 1;
+      const int i = 2 * s + p;
+      ok = ok && (i < nx);
+      valid[e] = ok;
+      ql[e] = q;
+      cellid[e] = (unsigned)i + (unsigned)nx * (unsigned)j;
+      if (ok) {
+        a[e] = g.own[q];
+        const float4 *O = g.other + (rl + 1) * hx + s;
+        const bool hl = i > 0 || (pbc & 1), hr = i < nx - 1 || (pbc & 1);
+        const bool hu = j > 0 || (pbc & 2), hd = j < ny - 1 || (pbc & 2);
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        nb[e][0] = hl ? O[i > 0 ? p - 1 : hx - 1] : z4;
+        nb[e][1] = hr ? O[i < nx - 1 ? p : 1 - hx] : z4;
+        nb[e][2] = hu ? O[-hx] : z4;
+        nb[e][3] = hd ? O[hx] : z4;
+        pres[e][0] = hl ? 1.f : 0.f;
+        pres[e][1] = hr ? 1.f : 0.f;
+        pres[e][2] = hu ? 1.f : 0.f;
+        pres[e][3] = hd ? 1.f : 0.f;
+        if (flags & F_GRAIN) {
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (nb[e][b].w != a[e].w) pres[e][b] *= K.gscale;
+        }
+        h[e] = (flags & F_DEMAG) ? g.heff[q] : make_float4(K.zee * K.Bx, K.zee * K.By, K.zee * K.Bz, 0.f);
+      }
+    }
+    int accepted[kBandCells];
+#pragma unroll
+    for (int e = 0; e < kBandCells; ++e) {
+      accepted[e] = 0;
+      if (!valid[e]) continue;
+      const float w[4] = {K.wx * pres[e][0], K.wx * pres[e][1], K.wy * pres[e][2], K.wy * pres[e][3]};
+      const uint4 r = philox4x32_10_rk(make_uint4(cellid[e], sweep, (unsigned)K.chain, 0u), A.rk);
+      const MoveAngles ga = move_angles(K.sigma, omc, uniform01(r.x), uniform01(r.y), uniform01(r.z));
+      const float u3 = uniform01(r.w);
+      Move v = move_length(a[e], K.me2h, K.me2l);
+      move_direction_g(v, a[e], ga);
+      const float floc = local_change_flat(v, a[e], nb[e], w, pres[e], K.cdx, K.cdy, (flags & F_DMI) != 0,
+                                           h[e].x, h[e].y, h[e].z);
+      const float flong = longitudinal_change(v, K.p2, K.p4);
+      const float fan = anisotropy_change(v, flags, K.k1, K.k2, K.ex, K.ey, K.ez);
+      const float dl = floc + flong + fan - 4.f * log1p_move(v.tt);
+      float dec;
+      if (DEBUG || dl > 0.f) dec = dl + __logf(u3);
+      else dec = dl;
+      accepted[e] = dec < 0.f;
+      const unsigned qg = (unsigned)r0 * (unsigned)hx + ql[e];
+      if (accepted[e]) mc[qg] = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
+      if (DEBUG) {
+        A.dec_dbg[cellid[e]] = dec;
+        A.acc_dbg[cellid[e]] = (signed char)accepted[e];
+      }
+    }
+    unsigned na = 0, nv = 0;
+#pragma unroll
+    for (int e = 0; e < kBandCells; ++e) {
+      na += __popc(__ballot_sync(0xffffffffu, accepted[e]));
+      nv += __popc(__ballot_sync(0xffffffffu, valid[e]));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      wacc[st][threadIdx.x >> 5] = na;
+      watt[st][threadIdx.x >> 5] = nv;
+    }
+    prev_c = c;
+    __syncthreads();                          // stage st, skv and the counts are read
+  }
+  if (abort_band) {
+    // copies of this band and of the next may still be in flight into the
+    // block's shared memory: give them a fixed time (about a millisecond, far
+    // beyond a copy's latency) to land before the block exits
+    const long long t0 = clock64();
+    while (clock64() - t0 < (1LL << 21)) {
+    }
+    return;
+  }
+  if (threadIdx.x == 0 && prev_c >= 0) {
+    const int st = (k - 1) & 1;
+    unsigned sa = 0, sv = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < kBandThreads / 32; ++w2) { sa += wacc[st][w2]; sv += watt[st][w2]; }
+    if (sv) {
+      atomicAdd(&A.st[prev_c].win_acc, (unsigned long long)sa);
+      atomicAdd(&A.st[prev_c].win_att, (unsigned long long)sv);
+    }
+  }
+}
+
+size_t band_smem_bytes(int stage_own, int stage_other) {
+  return (size_t)2 * (2 * stage_own + stage_other) * sizeof(float4);
+}
+
+cudaError_t band_set_smem(size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_band<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_sweep_band<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int band_blocks_per_sm(size_t bytes) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_band<false>, kBandThreads, bytes) != cudaSuccess)
+    return 1;
+  return n < 1 ? 1 : n;
+}
+
 void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
   SweepArgs A;
   A.chains = P.chains; A.st = P.st; A.blk_desc = P.blk_desc;
@@ -337,19 +568,24 @@ void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
       k1 += 0xBB67AE85u;
     }
   }
+  A.items = P.items; A.i0 = P.i0; A.i1 = P.i1;
+  A.stage_own = P.stage_own; A.stage_other = P.stage_other;
+  A.max_polls = P.max_polls; A.err = P.err; A.wait_test = P.wait_test;
+  if (P.band && P.nstripes <= 1 && P.i1 > P.i0) {
+    const int grid = std::min(P.i1 - P.i0, P.band_grid);
+    const size_t sm = band_smem_bytes(P.stage_own, P.stage_other);
+    if (P.dec_dbg) k_sweep_band<true><<<grid, kBandThreads, sm, L.stream>>>(A);
+    else k_sweep_band<false><<<grid, kBandThreads, sm, L.stream>>>(A);
+    ++*L.counter;
+    return;
+  }
   const int v = (P.percell ? 4 : 0) | (P.dec_dbg != nullptr ? 2 : 0) | (P.flat ? 1 : 0);
   const dim3 g(P.nblocks), b(kSweepThreads);
   switch (v) {
     case 0: k_sweep_pass<false, false, false><<<g, b, 0, L.stream>>>(A); break;
-    case 1:
-      // the production pass of uniform one-cell-thick chains comes in three
-      // occupancies (blocks per SM), picked by timing at create
-      if (P.variant == 1) k_sweep_flat<false, false, 6><<<g, b, 0, L.stream>>>(A);
-      else if (P.variant == 2) k_sweep_flat<false, false, 7><<<g, b, 0, L.stream>>>(A);
-      else k_sweep_flat<false, false, 8><<<g, b, 0, L.stream>>>(A);
-      break;
+    case 1: k_sweep_flat<false, false, 7><<<g, b, 0, L.stream>>>(A); break;
     case 2: k_sweep_pass<false, true, false><<<g, b, 0, L.stream>>>(A); break;
-    case 3: k_sweep_flat<false, true, 8><<<g, b, 0, L.stream>>>(A); break;
+    case 3: k_sweep_flat<false, true, 7><<<g, b, 0, L.stream>>>(A); break;
     case 4: k_sweep_pass<true, false, false><<<g, b, 0, L.stream>>>(A); break;
     case 5: k_sweep_flat<true, false, 5><<<g, b, 0, L.stream>>>(A); break;
     case 6: k_sweep_pass<true, true, false><<<g, b, 0, L.stream>>>(A); break;

@@ -193,9 +193,21 @@ struct SweepLaunch {
   signed char *acc_dbg;
   int nstripes, stripe;         // nstripes > 1: only the band `stripe` of rows of every chain
   bool flat;                    // every chain has nz == 1
-  int variant;                  // uniform one-cell-thick production pass: 1, 2, 3 = 6, 7, 8 blocks per SM
+  // banded pass with shared-memory halo tiles (uniform one-cell-thick batches)
+  bool band;
+  const int4 *items;            // per band: (chain, first row, rows, 0), by chain
+  int i0, i1;                   // items of this launch
+  int band_grid;                // resident blocks (SMs x blocks per SM)
+  int stage_own, stage_other;   // float4 capacity of a stage's own-colour and other-colour tiles
+  unsigned max_polls;           // bound of a wait for a band's copies
+  int *err;                     // device error word
+  int wait_test;                // test hook (mmc_options.wait_test)
 };
+constexpr int MMC_ERR_TIMEOUT_CODE = -3;   // mmc_status MMC_ERR_TIMEOUT
 void launch_sweep_pass(const Launch &L, const SweepLaunch &P);
+size_t band_smem_bytes(int stage_own, int stage_other);
+cudaError_t band_set_smem(size_t bytes);
+int band_blocks_per_sm(size_t bytes);
 void launch_advance(const Launch &L, ChainState *st, int nchains, unsigned by, unsigned *sweep_base,
                     int adapt_now, int adapt, float tmin, float tmax);
 

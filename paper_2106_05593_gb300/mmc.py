@@ -329,14 +329,6 @@ class MMC:
         check(load().mmc_fft_tuning(self._ctx, C.byref(v), _dptr(ms)), "mmc_fft_tuning")
         return int(v.value), tuple(float(x) for x in ms)
 
-    def sweep_tuning(self):
-        """(variant, create-time ms per pass of the occupancy variants 1, 2, 3) of
-        the sublattice pass of uniform one-cell-thick batches (variant 0: not used)."""
-        v = C.c_int(0)
-        ms = np.zeros(3)
-        check(load().mmc_sweep_tuning(self._ctx, C.byref(v), _dptr(ms)), "mmc_sweep_tuning")
-        return int(v.value), tuple(float(x) for x in ms)
-
     @property
     def launches(self) -> int:
         """Kernels the context has launched (graph replays counted per kernel)."""
