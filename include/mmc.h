@@ -140,8 +140,10 @@ typedef struct {
                                  row, run the sublattice pass on shared-memory
                                  halo tiles: bands of rows brought in by bulk
                                  asynchronous copies while the previous band is
-                                 computed; 0: the per-block pass.  Same moves
-                                 either way.                                    [1] */
+                                 computed; 0: the per-block pass.  The same
+                                 moves either way, up to the last-bit rounding of
+                                 the energy terms (separately compiled kernels;
+                                 each is deterministic on its own).             [1] */
     int wait_polls;           /* bound of a kernel's wait for its copies, in polls
                                  of the barrier (0: 2^22, about a second); a wait
                                  that runs out skips its band and makes the next
