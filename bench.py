@@ -60,6 +60,8 @@ def parse():
                          "3 radix 16 two blocks per SM, 4 warp 32x32 transforms (1024-point grids)")
     ap.add_argument("--stream-groups", type=int, default=0,
                     help="chain groups iterating on concurrent streams: 0 auto (2), 1 one stream")
+    ap.add_argument("--sweep-tiles", type=int, default=1, choices=(0, 1),
+                    help="1 banded pass on shared-memory halo tiles where the batch allows it, 0 per-block pass")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the cuFFT demag timing and the one-chain-per-launch comparison")
     ap.add_argument("--chains", type=int, default=0, help="use only the first N chains of the workload")
@@ -428,14 +430,14 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     if args.profile_run > 0:
         gp = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), use_graphs=0,
-                 fft_variant=args.fft_variant, stream=stream)
+                 fft_variant=args.fft_variant, sweep_tiles=args.sweep_tiles, stream=stream)
         gp.init_random(replica_seed(rank))
         gp.sweep(args.profile_run, replica_seed(rank))
         torch.cuda.synchronize()
         print("profile run ok", gp.launches, flush=True)
         return
     g = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=args.fft_variant,
-            stream_groups=args.stream_groups, stream=stream)
+            stream_groups=args.stream_groups, sweep_tiles=args.sweep_tiles, stream=stream)
     seed = replica_seed(rank)
     g.init_random(seed)
     ncell = sum(g.ncell)
