@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_flat(SweepArgs A)
     const float sig = PERCELL ? (valid[e] ? M[e].sigma : 0.f) : K.sigma;
     ga[e] = move_angles(sig, omc, uniform01(r.x), uniform01(r.y), uniform01(r.z));
     u3v[e] = uniform01(r.w);
-    lgv[e] = log1p_move(ga[e].tt);
+    lgv[e] = PERCELL ? log1p_move(ga[e].tt) : log1p_move_s(ga[e].tt, K.sigma);
   }
 
   // 3. the trials
@@ -295,9 +295,8 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_flat(SweepArgs A)
     const float fan = anisotropy_change(v, flags, M[e].k1, M[e].k2, M[e].ex, M[e].ey, M[e].ez);
     const float dF = floc + flong + fan;
     const float dl = dF - 4.f * lgv[e];
-    float dec;
-    if (DEBUG || dl > 0.f) dec = dl + __logf(u3);
-    else dec = dl;
+    // ln u3 < 0: accept iff dl + ln u3 < 0 (taken for every cell: no divergent branch)
+    const float dec = dl + __logf(u3);
     accepted[e] = dec < 0.f;
     if (accepted[e]) mc[qq[e]] = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
     if (DEBUG) {
@@ -377,7 +376,7 @@ __device__ __forceinline__ void band_issue(const SweepArgs &A, int4 it, const Ba
 }
 
 template <bool DEBUG>
-__global__ void __launch_bounds__(kBandThreads, 2) k_sweep_band(SweepArgs A) {
+__global__ void __launch_bounds__(kBandThreads, 3) k_sweep_band(SweepArgs A) {
   extern __shared__ __align__(16) unsigned char band_smem[];
   __shared__ uint64_t bar[2];
   __shared__ float4 skv[kChainKVec];
@@ -488,10 +487,8 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_sweep_band(SweepArgs A) {
                                            h[e].x, h[e].y, h[e].z);
       const float flong = longitudinal_change(v, K.p2, K.p4);
       const float fan = anisotropy_change(v, flags, K.k1, K.k2, K.ex, K.ey, K.ez);
-      const float dl = floc + flong + fan - 4.f * log1p_move(v.tt);
-      float dec;
-      if (DEBUG || dl > 0.f) dec = dl + __logf(u3);
-      else dec = dl;
+      const float dl = floc + flong + fan - 4.f * log1p_move_s(v.tt, K.sigma);
+      const float dec = dl + __logf(u3);
       accepted[e] = dec < 0.f;
       const unsigned qg = (unsigned)r0 * (unsigned)hx + ql[e];
       if (accepted[e]) mc[qg] = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);

@@ -311,10 +311,17 @@ __device__ __forceinline__ float anisotropy_change(const Move &v, int flags, flo
 }
 
 // ln(1 + t): Taylor series through t^7 when |t| <= 0.05 (error below t^8 / 8)
+__device__ __forceinline__ float log1p_series(float tt) {
+  return tt * (1.f - tt * (0.5f - tt * (1.f / 3.f - tt * (0.25f - tt * (0.2f - tt * (1.f / 6.f - tt * (1.f / 7.f)))))));
+}
 __device__ __forceinline__ float log1p_move(float tt) {
-  if (fabsf(tt) <= 0.05f)
-    return tt * (1.f - tt * (0.5f - tt * (1.f / 3.f - tt * (0.25f - tt * (0.2f - tt * (1.f / 6.f - tt * (1.f / 7.f)))))));
+  if (fabsf(tt) <= 0.05f) return log1p_series(tt);
   return log1pf(tt);
+}
+// the same for a cell of a chain whose length-move width is sigma (|t| <= sigma):
+// one branch per chain instead of one per cell when sigma <= 0.05
+__device__ __forceinline__ float log1p_move_s(float tt, float sigma) {
+  return sigma <= 0.05f ? log1p_series(tt) : log1p_move(tt);
 }
 
 }  // namespace mmc
