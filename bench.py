@@ -41,6 +41,7 @@ import workloads as W  # noqa: E402
 METRIC = "MMC cell-updates/s incl. demag"
 UNIT = "cell-updates/s"
 SWEEPS_PER_STEP = 100
+LOOP_SWEEPS = 5000          # iterations per field of the hysteresis-loop workload
 
 
 def parse():
@@ -50,8 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chiral512",
-                    choices=["chiral512", "chiral512_periodic", "film256", "permalloy32", "granular",
-                             "probe8192"])
+                    choices=["chiral512", "chiral512_periodic", "film256", "film256_loop", "permalloy32",
+                             "granular", "probe8192"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-demag", action="store_true")
@@ -60,7 +61,7 @@ def parse():
                          "3 radix 16 two blocks per SM, 4 warp 32x32 transforms (1024-point grids)")
     ap.add_argument("--stream-groups", type=int, default=0,
                     help="chain groups iterating on concurrent streams: 0 auto (2), 1 one stream")
-    ap.add_argument("--sweep-tiles", type=int, default=1, choices=(0, 1),
+    ap.add_argument("--sweep-tiles", type=int, default=0, choices=(0, 1),
                     help="1 banded pass on shared-memory halo tiles where the batch allows it, 0 per-block pass")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the cuFFT demag timing and the one-chain-per-launch comparison")
@@ -79,6 +80,10 @@ def workload(name):
                 "2x2x1 nm, DMI+Ku, T=50..650 K")
     if name == "film256":
         return [W.film256(256)], True, "256x256x1, 4 nm, demag, B=100 mT"
+    if name == "film256_loop":
+        return ([W.film256(256)], True,
+                "256x256x1, 4 nm, demag; hysteresis loop of 41 fields +100 -> -100 mT along x, "
+                f"{LOOP_SWEEPS} iterations per field (one field per step), snapshot every 50 iterations")
     if name == "permalloy32":
         return [W.permalloy32()], False, "32x32x1 periodic, 5 nm, no demag"
     if name == "granular":
@@ -441,9 +446,24 @@ def run_ours(args):
     seed = replica_seed(rank)
     g.init_random(seed)
     ncell = sum(g.ncell)
-    cells_per_step = ncell * SWEEPS_PER_STEP
+    loop = args.workload == "film256_loop"
+    sweeps_per_step = LOOP_SWEEPS if loop else SWEEPS_PER_STEP
+    cells_per_step = ncell * sweeps_per_step
+    fields = W.hysteresis_fields(41)
+    step_no = [0]
+
+    def do_step():
+        """One step: 100 iterations of the batch, or for the loop workload the
+        next field of the loop and its iterations with snapshots."""
+        if loop:
+            g.set_field(fields[step_no[0] % len(fields)])
+            g.sweep_sampled(LOOP_SWEEPS, seed, 50)
+        else:
+            g.sweep(SWEEPS_PER_STEP, seed)
+        step_no[0] += 1
+
     for _ in range(args.warmup):
-        g.sweep(SWEEPS_PER_STEP, seed)
+        do_step()
     torch.cuda.synchronize()
 
     def barrier():
@@ -461,7 +481,7 @@ def run_ours(args):
     nvtx_range("timed_steps")            # lets a profiler select the timed launches
     e0.record(stream)
     for _ in range(args.steps):
-        g.sweep(SWEEPS_PER_STEP, seed)
+        do_step()
     e1.record(stream)
     torch.cuda.synchronize()
     nvtx_range(None)
@@ -554,7 +574,7 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             for k in range(g.nchains):
                 g.set_m(host_m[k], k)
-            g.sweep(SWEEPS_PER_STEP, seed)
+            do_step()
             for k in range(g.nchains):
                 ob = g.observables(k)
                 d2h += 8 * (3 + 2) + 8 * ob["hist"].size
@@ -577,7 +597,7 @@ def run_ours(args):
             "dtype": "f32 (demag FFT f64)" if args.fp64_demag else "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "cells": ncell,
-                       "sweeps_per_step": SWEEPS_PER_STEP, "demag": "once per iteration" if demag else "off",
+                       "sweeps_per_step": sweeps_per_step, "demag": "once per iteration" if demag else "off",
                        "l2": "working set larger than L2" if args.workload in ("chiral512", "chiral512_periodic", "granular", "probe8192")
                        else "working set L2-resident (no flush)", "graphs": True},
             "roofline": roofline, "roofline_sweep_pass": sweep_roof, "compare": compare,

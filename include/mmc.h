@@ -143,7 +143,10 @@ typedef struct {
                                  computed; 0: the per-block pass.  The same
                                  moves either way, up to the last-bit rounding of
                                  the energy terms (separately compiled kernels;
-                                 each is deterministic on its own).             [1] */
+                                 each is deterministic on its own).  On GB300
+                                 the per-block pass is faster for these chains
+                                 (the pass is bound by instruction issue, and
+                                 the banded kernel holds more registers).       [0] */
     int wait_polls;           /* bound of a kernel's wait for its copies, in polls
                                  of the barrier (0: 2^22, about a second); a wait
                                  that runs out skips its band and makes the next

@@ -1041,7 +1041,7 @@ mmc_status mmc_default_options(mmc_options *o) {
   o->demag_self = 0;
   o->fft_variant = 0;
   o->demag_stripes = 1;
-  o->sweep_tiles = 1;
+  o->sweep_tiles = 0;
   o->wait_polls = 0;
   o->wait_test = 0;
   return MMC_OK;

@@ -128,3 +128,73 @@ def test_angular_histogram_averages_to_a_density():
     assert e.calls == 4
     assert np.allclose(c, (np.arange(10) + 0.5) / 10)
     assert np.isclose(dens.sum() * 0.1, 1.0) and np.isclose(dens[0], 0.75 / 0.1)
+
+
+def _oracle_loop(spec, fields, chain, seed, chunk, threshold, min_chunks, max_chunks, every):
+    """The Sec. III loop protocol on one oracle chain (runs in a spawned
+    process): per field, chunks of `chunk` iterations averaging a snapshot every
+    `every` iterations, until at least min_chunks chunks ran and the last two
+    chunk averages of m along the field differ by less than threshold.  Returns
+    the accepted chunk average per field and the chunks used."""
+    import numpy as np
+    import oracle as O
+    o = O.Oracle(spec)
+    me = O.me(float(spec["T"]), float(spec["Tc"]))
+    m = np.zeros((o.n, 3))
+    m[:, 0] = me
+    st = O.new_state(seed=seed, chain=chain, theta_deg=30.0, adapt=True, demag_mode=1)
+    mpar, used = [], []
+    for B in fields:
+        B = np.asarray(B, dtype=np.float64)
+        bhat = B / np.linalg.norm(B) if np.linalg.norm(B) > 0 else np.array([1.0, 0.0, 0.0])
+        o.set_field(B)
+        hist = []
+        while len(hist) < max_chunks:
+            m, _, ob = o.run(m, chunk, st, obs_every=every)
+            hist.append(float(np.dot(ob["mean_m"], bhat)))
+            if len(hist) >= min_chunks and abs(hist[-1] - hist[-2]) < threshold:
+                break
+        mpar.append(hist[-1])
+        used.append(len(hist))
+    return mpar, used
+
+
+@pytest.mark.gpu
+def test_gpu_loop_matches_oracle_within_3_se():
+    """The field loop of Sec. III (2000-iteration chunks, at least two, accepted
+    when consecutive chunk averages of m along the field differ by < 0.01) on a
+    16 x 16 film of 4 nm cells with demag, fields +100, +40, 0, -40, -100 mT
+    along x: 32 GPU chains (one batch, the library's hysteresis driver) against
+    16 oracle chains (other seeds) running the same protocol; at every field the
+    chain means of the accepted m along the field agree within 3 standard
+    errors."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    from gpu_common import lib_or_skip, welch_z
+    P = lib_or_skip()
+    import oracle as O
+    import workloads as W
+    spec = W.film256(16, B_mT=0.0)
+    fields = [(b * 1e-3, 0.0, 0.0) for b in (100.0, 40.0, 0.0, -40.0, -100.0)]
+    ng, no = 32, 16
+    args = dict(chunk=2000, threshold=0.01, min_chunks=2, max_chunks=12, every=10)
+    with cf.ProcessPoolExecutor(max_workers=max(1, min(no, (os.cpu_count() or 2) - 1)),
+                                mp_context=mp.get_context("spawn")) as ex:
+        fut = [ex.submit(_oracle_loop, spec, fields, c, 500 + c, **args) for c in range(no)]
+        me = O.me(300.0, 870.0)
+        g = P.MMC([spec] * ng, demag=1, fft_variant=1)
+        for k in range(ng):
+            g.set_m(W.uniform_state(16 * 16, (1, 0, 0), me), k)
+        out = hysteresis(g, fields, seed=7, chunk=args["chunk"], threshold=args["threshold"],
+                         min_chunks=args["min_chunks"], max_chunks=args["max_chunks"],
+                         sample_every=args["every"])
+        res = [f.result() for f in fut]
+    gm = np.array(out["m_par"])                      # [field, chain]
+    om = np.array([r[0] for r in res]).T             # [field, chain]
+    for f in range(len(fields)):
+        z = welch_z(gm[f], om[f])
+        print("field %+6.1f mT: gpu %.5f oracle %.5f z %+.2f chunks gpu %.2f oracle %.2f"
+              % (fields[f][0] * 1e3, gm[f].mean(), om[f].mean(), z, np.mean(out["chunks"][f]),
+                 np.mean([r[1][f] for r in res])))
+        assert abs(z) < 3.0, (f, z)
