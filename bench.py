@@ -532,6 +532,10 @@ def run_ours(args):
                 compare["fp64_demag"] = fp64_demag_compare(MMC, specs, seed, stream, cells_per_step)
                 compare["demag_update_ms"]["own_fp64"] = compare["fp64_demag"]["demag_update_ms"]
             v, tms = g.fft_tuning()
+            tu = g.tuning()
+            compare["autotune"] = {"stream_groups": tu["stream_groups"], "from_cache": tu["from_cache"],
+                                   "iteration_ms_by_groups": {"1": tu["groups_ms"][0], "2": tu["groups_ms"][1],
+                                                              "3": tu["groups_ms"][2]}}
             compare["fft_variant"] = {"picked": {0: None, 1: "radix16", 2: "radix32", 3: "radix16x2", 4: "warp32x32"}[v],
                                       "create_time_ms": {"radix16": tms[0], "radix32": tms[1],
                                                          "radix16x2": tms[2], "warp32x32": tms[3]}}

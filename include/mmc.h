@@ -110,9 +110,10 @@ typedef struct {
     int use_graphs;           /* 1: capture 100-sweep blocks in CUDA graphs         [1] */
     int stream_groups;        /* chain groups whose iterations run concurrently on
                                  their own streams, so that one group's kernel tails
-                                 overlap the other's work; 0 auto (2 when the batch
-                                 has >= 2 chains), 1 one stream, G > 1 G groups.
-                                 Results are identical for any value.            [0] */
+                                 overlap the other's work; 0 auto (1, 2 or 3 groups,
+                                 timed on the batch at create, see mmc_tuning), 1
+                                 one stream, G > 1 G groups.  Results are
+                                 identical for any value.                        [0] */
     int demag_self;           /* serial form (mmc_sweep_serial) only: add the demag
                                  self term (mu0 V / 2) Ms0^2 dm.N(0).dm to Eq. 14,
                                  making its demag energy change exact           [0] */
@@ -396,6 +397,20 @@ mmc_status mmc_phase_times(mmc_ctx *ctx, int64_t n, uint64_t seed, double ms[6],
  * repeat bit for bit across contexts.  (HOST outputs.)  Not a paper quantity: a
  * tuning record of this implementation. */
 mmc_status mmc_fft_tuning(const mmc_ctx *ctx, int *variant, double ms[4]);
+
+/* The create-time autotuner's picks: the FFT variant (as mmc_fft_tuning), the
+ * number of chain groups on concurrent streams, and whether both came from the
+ * tuning cache (1) or were timed on the batch (0).  ms (optional, 7 doubles):
+ * per-update times of FFT variants 1..4 and per-iteration times with 1, 2, 3
+ * groups, as timed (0 where not timed).  The cache is a text file, one line per
+ * problem, named by the environment variable MMC_TUNE_CACHE ("" or "off"
+ * disables it), by default $XDG_CACHE_HOME/mmc_gb300/tune.txt or
+ * ~/.cache/mmc_gb300/tune.txt; its key is the GPU model and a hash of the
+ * chains' extents, periodicity, demag images and per-cell flag and of the
+ * kernel-selecting options.  A second create of the same problem reads the
+ * picks instead of timing, so both contexts run the same kernels.  (HOST
+ * outputs; a tuning record of this implementation, not a paper quantity.) */
+mmc_status mmc_tuning(const mmc_ctx *ctx, int *fft_variant, int *stream_groups, int *from_cache, double ms[7]);
 
 
 /* Number of kernels the library launched since create (all kinds). */

@@ -20,7 +20,7 @@ EXPORTS = [
     "mmc_default_options", "mmc_create", "mmc_create_single", "mmc_destroy", "mmc_set_field",
     "mmc_set_m", "mmc_get_m", "mmc_init_random", "mmc_sweep", "mmc_sweep_sampled",
     "mmc_demag_update", "mmc_pass_debug", "mmc_observables", "mmc_energy", "mmc_demag_field",
-    "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_fft_tuning", "mmc_sweep_field", "mmc_sweep_serial", "mmc_minimize", "mmc_set_temperature", "mmc_angle_hist", "mmc_trial_terms", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell", "mmc_demag_kernel", "mmc_thermo",
+    "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_fft_tuning", "mmc_tuning", "mmc_sweep_field", "mmc_sweep_serial", "mmc_minimize", "mmc_set_temperature", "mmc_angle_hist", "mmc_trial_terms", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell", "mmc_demag_kernel", "mmc_thermo",
     "mmc_checkpoint", "mmc_restore", "mmc_observables_noalloc", "mmc_status_str", "mmc_last_error",
 ]
 
@@ -134,6 +134,8 @@ def load():
     L.mmc_sweep_serial.argtypes = [vp, C.c_int64, C.c_uint64]
     L.mmc_fft_tuning.restype = st
     L.mmc_fft_tuning.argtypes = [vp, C.POINTER(C.c_int), dp]
+    L.mmc_tuning.restype = st
+    L.mmc_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
     L.mmc_kernel_launches.restype = C.c_int64
     L.mmc_kernel_launches.argtypes = [vp]
     L.mmc_nchains.restype = C.c_int

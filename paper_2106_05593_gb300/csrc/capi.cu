@@ -3,7 +3,12 @@
 // measurements and checkpoints.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <filesystem>
+#include <fstream>
+#include <sstream>
 #include <string>
 #include <thread>
 #include <vector>
@@ -188,6 +193,9 @@ struct mmc_ctx {
   std::vector<ChainGroup> groups;
   cudaEvent_t ev_fork = nullptr;
   int tuned_variant = 0;                // FFT variant picked at create (0: not tuned)
+  int tuned_groups = 0;                 // chain groups picked at create (0: not tuned)
+  bool tune_cached = false;             // the picks came from the tuning cache
+  double group_ms[3] = {0.0, 0.0, 0.0}; // per-iteration time with 1, 2, 3 groups when timed
   double tune_ms[4] = {0.0, 0.0, 0.0, 0.0};  // per-update time of the variants when tuned
   std::vector<DemagPlan> single[2];     // per chain and precision (0 FP32, 1 FP64), built lazily
   // serial exact-demag sweep: real-space tensors per set, proposals scratch
@@ -963,6 +971,125 @@ mmc_status sweep_impl(mmc_ctx *c, int64_t n, uint64_t seed, int sample_every) {
   return MMC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuning record cache: one line per tuned problem, "key fft_variant groups",
+// in the file named by MMC_TUNE_CACHE (an empty value or "off" disables it), by
+// default $XDG_CACHE_HOME/mmc_gb300/tune.txt or ~/.cache/mmc_gb300/tune.txt.
+// The key is the GPU name and a 64-bit FNV-1a hash of everything the picks
+// depend on: the chains' extents, periodicity, demag images and per-cell flag,
+// and the options that select kernels.  A later line wins.
+std::string tune_cache_path() {
+  const char *e = std::getenv("MMC_TUNE_CACHE");
+  if (e) {
+    const std::string v(e);
+    return (v.empty() || v == "off") ? std::string() : v;
+  }
+  const char *x = std::getenv("XDG_CACHE_HOME");
+  const char *h = std::getenv("HOME");
+  if (x && *x) return std::string(x) + "/mmc_gb300/tune.txt";
+  if (h && *h) return std::string(h) + "/.cache/mmc_gb300/tune.txt";
+  return std::string();
+}
+
+std::string tune_key(const mmc_ctx *c) {
+  std::ostringstream d;
+  d << "v1|n" << c->nchains << "|fp64 " << c->opt.demag_fp64 << "|cufft " << c->opt.demag_cufft << "|demag "
+    << c->opt.demag << "|pp " << c->opt.demag_per_pass << "|st " << c->opt.demag_stripes << "|tiles "
+    << c->opt.sweep_tiles;
+  for (int i = 0; i < c->nchains; ++i) {
+    const mmc_mesh &m = c->hc[i].mesh;
+    d << "|" << m.nx << "x" << m.ny << "x" << m.nz << "p" << m.periodic[0] << m.periodic[1] << m.periodic[2] << "i"
+      << m.demag_images << "c" << (c->hc[i].percell ? 1 : 0);
+  }
+  const std::string str = d.str();
+  unsigned long long hsh = 1469598103934665603ULL;
+  for (unsigned char ch : str) {
+    hsh ^= ch;
+    hsh *= 1099511628211ULL;
+  }
+  int dev = 0;
+  cudaDeviceProp prop;
+  std::string name = "gpu";
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) name = prop.name;
+  for (char &ch : name)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  char buf[32];
+  std::snprintf(buf, sizeof(buf), "%016llx", hsh);
+  return name + ":" + buf;
+}
+
+bool tune_cache_read(const std::string &path, const std::string &key, int &fft, int &groups) {
+  std::ifstream f(path);
+  if (!f) return false;
+  bool found = false;
+  std::string line;
+  while (std::getline(f, line)) {
+    std::istringstream in(line);
+    std::string k;
+    int a = 0, b = 0;
+    if ((in >> k >> a >> b) && k == key) {
+      fft = a;
+      groups = b;
+      found = true;
+    }
+  }
+  return found;
+}
+
+void tune_cache_write(const std::string &path, const std::string &key, int fft, int groups) {
+  std::error_code ec;
+  const std::filesystem::path p(path);
+  if (p.has_parent_path()) std::filesystem::create_directories(p.parent_path(), ec);
+  std::ofstream f(path, std::ios::app);
+  if (f) f << key << " " << fft << " " << groups << "\n";
+}
+
+void free_groups(mmc_ctx *c) {
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto &g : c->groups) {
+    if (g.done) cudaEventDestroy(g.done);
+    if (g.stream) cudaStreamDestroy(g.stream);
+  }
+  c->groups.clear();
+}
+
+// G groups of contiguous chains with about equal cell counts, each with its own
+// stream and demag plan (over the batch's spectrum buffer); G <= 1: no groups
+mmc_status make_groups(mmc_ctx *c, int G) {
+  free_groups(c);
+  const int nchains = c->nchains;
+  G = std::min(G, nchains);
+  if (G <= 1) return MMC_OK;
+  long long total = 0;
+  for (int i = 0; i < nchains; ++i) total += c->hc[i].ncell;
+  int start = 0;
+  long long done = 0;
+  for (int gi = 0; gi < G; ++gi) {
+    int end = start + 1;
+    const long long target = total * (gi + 1) / G;
+    long long acc = done + c->hc[start].ncell;
+    while (end < nchains - (G - 1 - gi) && acc + c->hc[end].ncell / 2 <= target) acc += c->hc[end++].ncell;
+    if (gi == G - 1) { end = nchains; acc = total; }
+    mmc_ctx::ChainGroup g;
+    g.c0 = start;
+    g.c1 = end;
+    c->groups.push_back(g);
+    start = end;
+    done = acc;
+  }
+  if (!c->ev_fork) CUDA_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  for (auto &g : c->groups) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+    if (c->opt.demag) {
+      std::vector<int> ids;
+      for (int i = g.c0; i < g.c1; ++i) ids.push_back(i);
+      MMC_TRY(build_demag_plan(c, g.plan, ids, c->opt.demag_fp64 != 0, false, c->batch_plan.spec));
+    }
+  }
+  return MMC_OK;
+}
+
 mmc_status serial_prepare(mmc_ctx *c) {
   if (c->serial_ready) return MMC_OK;
   if (c->any_demag) {
@@ -1352,63 +1479,111 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     for (int i = 0; i < nchains; ++i) all[i] = i;
     MMC_TRY_OR(build_demag_plan(c, c->batch_plan, all, o.demag_fp64 != 0, false));
   }
-  if (o.demag && !o.demag_cufft && !o.demag_fp64 && c->batch_plan.il2d && o.fft_variant == 0) {
-    // time both FP32 variants on this batch (a few updates each) and keep the faster
-    float best = 1e30f;
+  // autotuning: the FFT variant of the FP32 2D demag kernels and the number of
+  // chain groups that iterate on concurrent streams, timed on this batch unless
+  // the tuning cache holds picks for the same problem on this GPU model
+  const bool want_fft = o.demag && !o.demag_cufft && !o.demag_fp64 && c->batch_plan.il2d && o.fft_variant == 0;
+  const bool want_groups = o.stream_groups == 0 && nchains >= 2 && !o.demag_cufft;
+  const std::string cpath = (want_fft || want_groups) ? tune_cache_path() : std::string();
+  std::string tkey;
+  int cached_fft = 0, cached_groups = 0;
+  if (!cpath.empty()) {
+    tkey = tune_key(c);
+    c->tune_cached = tune_cache_read(cpath, tkey, cached_fft, cached_groups);
+  }
+  if (want_fft) {
+    const auto usable = [&](int v) {
+      return v >= 1 && v <= 4 && (v != 3 || c->batch_plan.small.ok) && (v != 4 || c->batch_plan.w32.ok);
+    };
     int pick = 1;
-    cudaEvent_t e0, e1;
-    CUDA_TRY_OR(cudaEventCreate(&e0));
-    CUDA_TRY_OR(cudaEventCreate(&e1));
-    for (int v = 1; v <= 4; ++v) {
-      if (v == 3 && !c->batch_plan.small.ok) continue;
-      if (v == 4 && !c->batch_plan.w32.ok) continue;
-      c->batch_plan.fft_variant = v;
-      issue_demag(c);
-      CUDA_TRY_OR(cudaEventRecord(e0, c->stream));
-      for (int r = 0; r < 5; ++r) issue_demag(c);
-      CUDA_TRY_OR(cudaEventRecord(e1, c->stream));
-      CUDA_TRY_OR(cudaEventSynchronize(e1));
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      c->tune_ms[v - 1] = ms / 5.0;
-      if (ms < best) { best = ms; pick = v; }
+    if (c->tune_cached && usable(cached_fft)) {
+      pick = cached_fft;
+    } else {
+      // time the FP32 variants on this batch (a few updates each) and keep the fastest
+      float best = 1e30f;
+      cudaEvent_t e0, e1;
+      CUDA_TRY_OR(cudaEventCreate(&e0));
+      CUDA_TRY_OR(cudaEventCreate(&e1));
+      for (int v = 1; v <= 4; ++v) {
+        if (!usable(v)) continue;
+        c->batch_plan.fft_variant = v;
+        issue_demag(c);
+        CUDA_TRY_OR(cudaEventRecord(e0, c->stream));
+        for (int r = 0; r < 5; ++r) issue_demag(c);
+        CUDA_TRY_OR(cudaEventRecord(e1, c->stream));
+        CUDA_TRY_OR(cudaEventSynchronize(e1));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c->tune_ms[v - 1] = ms / 5.0;
+        if (ms < best) { best = ms; pick = v; }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      c->tune_cached = false;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     c->batch_plan.fft_variant = pick;
     c->tuned_variant = pick;
   }
-  if (o.stream_groups != 1 && nchains >= 2 && !o.demag_cufft) {
-    // two groups of contiguous chains with about equal cell counts
-    const int G = o.stream_groups > 1 ? std::min(o.stream_groups, nchains) : 2;
-    long long total = 0;
-    for (int i = 0; i < nchains; ++i) total += c->hc[i].ncell;
-    int start = 0;
-    long long done = 0;
-    for (int gi = 0; gi < G; ++gi) {
-      int end = start + 1;
-      const long long target = total * (gi + 1) / G;
-      long long acc = done + c->hc[start].ncell;
-      while (end < nchains - (G - 1 - gi) && acc + c->hc[end].ncell / 2 <= target) acc += c->hc[end++].ncell;
-      if (gi == G - 1) { end = nchains; acc = total; }
-      mmc_ctx::ChainGroup g;
-      g.c0 = start;
-      g.c1 = end;
-      c->groups.push_back(g);
-      start = end;
-      done = acc;
+  int G = 1;
+  if (o.stream_groups == 1 || nchains < 2 || o.demag_cufft) {
+    G = 1;
+  } else if (o.stream_groups > 1) {
+    G = std::min(o.stream_groups, nchains);
+  } else if (c->tune_cached && cached_groups >= 1 && (cached_fft == c->tuned_variant || !want_fft)) {
+    G = std::min(cached_groups, nchains);
+  } else {
+    // time whole iterations with 1, 2 and 3 groups on a saved copy of the state
+    // (the timing iterations are real moves; the state, the window counters and
+    // the iteration counter are put back afterwards)
+    void *save_m = nullptr, *save_st = nullptr;
+    const size_t bm = (size_t)c->m_total * sizeof(float4), bs = (size_t)nchains * sizeof(ChainState);
+    CUDA_TRY_OR(cudaMalloc(&save_m, bm));
+    if (cudaMalloc(&save_st, bs) != cudaSuccess) {
+      cudaFree(save_m);
+      mmc_destroy(c);
+      return fail(MMC_ERR_NOMEM, "cudaMalloc of the tuning copy failed");
     }
-    CUDA_TRY_OR(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-    for (auto &g : c->groups) {
-      CUDA_TRY_OR(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
-      CUDA_TRY_OR(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
-      if (o.demag) {
-        std::vector<int> ids;
-        for (int i = g.c0; i < g.c1; ++i) ids.push_back(i);
-        MMC_TRY_OR(build_demag_plan(c, g.plan, ids, o.demag_fp64 != 0, false, c->batch_plan.spec));
-      }
+    unsigned save_base = 0;
+    cudaMemcpyAsync(save_m, c->d_m, bm, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(save_st, c->d_st, bs, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(&save_base, c->d_sweep_base, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    mmc_status st = MMC_OK;
+    for (int gcount = 1; gcount <= std::min(3, nchains) && st == MMC_OK; ++gcount) {
+      st = make_groups(c, gcount);
+      if (st != MMC_OK) break;
+      issue_block(c, 5, 1u, 0u, 0, 0);
+      cudaEventRecord(e0, c->stream);
+      issue_block(c, 10, 1u, 0u, 0, 0);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      c->group_ms[gcount - 1] = ms / 10.0;
+      if (ms < best) { best = ms; G = gcount; }
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaMemcpyAsync(c->d_m, save_m, bm, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->d_st, save_st, bs, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->d_sweep_base, &save_base, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(save_m);
+    cudaFree(save_st);
+    if (st != MMC_OK) {
+      mmc_destroy(c);
+      return st;
+    }
+    CUDA_TRY_OR(cudaGetLastError());
+    c->tune_cached = false;
   }
+  if (want_groups) c->tuned_groups = G;
+  MMC_TRY_OR(make_groups(c, G));
+  if (!cpath.empty() && !c->tune_cached) tune_cache_write(cpath, tkey, c->tuned_variant, G);
   if (o.demag && o.demag_cufft) {
     // one batched cuFFT plan pair per padded size
     for (int i = 0; i < nchains; ++i) {
@@ -2030,6 +2205,18 @@ mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[6], i
 }
 
 int64_t mmc_kernel_launches(const mmc_ctx *c) { return c ? c->launches : 0; }
+
+mmc_status mmc_tuning(const mmc_ctx *c, int *fft_variant, int *stream_groups, int *from_cache, double ms[7]) {
+  if (!c) return fail(MMC_ERR_ARG, "null context");
+  if (fft_variant) *fft_variant = c->batch_plan.ready && c->batch_plan.il2d ? c->batch_plan.fft_variant : 0;
+  if (stream_groups) *stream_groups = c->groups.empty() ? 1 : (int)c->groups.size();
+  if (from_cache) *from_cache = c->tune_cached ? 1 : 0;
+  if (ms) {
+    for (int k = 0; k < 4; ++k) ms[k] = c->tune_ms[k];
+    for (int k = 0; k < 3; ++k) ms[4 + k] = c->group_ms[k];
+  }
+  return MMC_OK;
+}
 
 mmc_status mmc_fft_tuning(const mmc_ctx *c, int *variant, double ms[4]) {
   if (!c || !variant || !ms) return fail(MMC_ERR_ARG, "null argument");

@@ -329,6 +329,16 @@ class MMC:
         check(load().mmc_fft_tuning(self._ctx, C.byref(v), _dptr(ms)), "mmc_fft_tuning")
         return int(v.value), tuple(float(x) for x in ms)
 
+    def tuning(self):
+        """The create-time autotuner's picks: dict with fft_variant, stream_groups,
+        from_cache and the timed ms per update (FFT variants 1..4) and per
+        iteration (1, 2, 3 groups)."""
+        v, gr, fc = C.c_int(0), C.c_int(0), C.c_int(0)
+        ms = np.zeros(7)
+        check(load().mmc_tuning(self._ctx, C.byref(v), C.byref(gr), C.byref(fc), _dptr(ms)), "mmc_tuning")
+        return {"fft_variant": int(v.value), "stream_groups": int(gr.value), "from_cache": bool(fc.value),
+                "fft_ms": tuple(float(x) for x in ms[:4]), "groups_ms": tuple(float(x) for x in ms[4:])}
+
     @property
     def launches(self) -> int:
         """Kernels the context has launched (graph replays counted per kernel)."""
