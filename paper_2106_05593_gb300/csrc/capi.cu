@@ -720,6 +720,7 @@ DemagLaunch make_demag_launch(mmc_ctx *c, const DemagPlan &P, float4 *heff, doub
   D.fft_variant = P.fft_variant;
   D.inv_smem = P.inv_smem;
   D.w32 = false;
+  D.err = c->d_err;
   D.nhatT = (const void *const *)c->d_nhat32t;
   D.tw1024 = c->d_tw1024;
   if (P.il2d && P.fft_variant == 4 && P.w32.ok && !P.fp64) {
@@ -1348,11 +1349,11 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
       void *d32t = nullptr;
       if (ss.Px == 1024 && ss.Py == 1024 && ss.Pz == 1 && !ss.pd.circ[0] && !ss.pd.circ[1]) {
         // [comp][kyq][kx] -> [comp][kx][kyq] for the column blocks of the warp-transform path
-        const size_t q = 513;
-        std::vector<float> tr(4 * q * q);
+        const size_t q = 513, tp = (size_t)kW32TensorPitch;
+        std::vector<float> tr(4 * q * tp, 0.f);
         for (size_t cp = 0; cp < 4; ++cp)
           for (size_t ky = 0; ky < q; ++ky)
-            for (size_t kx = 0; kx < q; ++kx) tr[(cp * q + kx) * q + ky] = (float)sp[(cp * q + ky) * q + kx];
+            for (size_t kx = 0; kx < q; ++kx) tr[(cp * q + kx) * tp + ky] = (float)sp[(cp * q + ky) * q + kx];
         float *dt = nullptr;
         MMC_TRY_OR(upload(c, &dt, tr));
         d32t = dt;

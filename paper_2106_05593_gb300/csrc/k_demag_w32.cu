@@ -2,7 +2,8 @@
 // is 1024 x 1024, on warp-resident 1024-point transforms (fft_w32.cuh).
 //
 // Spectrum layout (per chain, at ChainDev::s_off; R4 = rows rounded up to 4,
-// Sx = row stride): component c, row y and column kx at
+// Sx = 520 the row stride of every 1024-point grid): component c, row y and
+// column kx at
 //   c R4 Sx + (y / 4) 4 Sx + 4 kx + y % 4,
 // i.e. tiles of four rows stored column by column.  The forward row kernel
 // writes one whole tile per component (contiguous); the column kernel reads and
@@ -22,6 +23,7 @@
 //                   and the sweep's field zee (B + mu0 H) in the split layout.
 #include "demag_args.cuh"
 #include "fft_w32.cuh"
+#include "tma.cuh"
 
 namespace mmc {
 
@@ -38,14 +40,20 @@ struct W32Args {
   float4 *heff;
   double *Hd;
   int Hd_chain;
+  int *err;                       // device error word (a wait for the tensor copy that gave up)
 };
 
 constexpr int kW32Half = 513;           // kx = 0..512
-constexpr int kW32TilePitch = 524;      // smem row pitch of the inverse-row input tile
+constexpr int kW32TPitch = kW32TensorPitch;                    // tensor row (kyq) pitch, 16-byte multiple
+constexpr long long kW32TQ = (long long)kW32Half * kW32TPitch; // one tensor component
+constexpr int kW32Sx = 520;             // spectrum row stride of a 1024-point grid (complex values)
+constexpr int kW32Tile = 4 * kW32Sx;    // one tile of four rows
+constexpr int kW32TilePitch = 524;      // smem row pitch of the row kernels' tiles
+constexpr unsigned kW32Polls = 1u << 22;
 
 __device__ __forceinline__ long long w32_at(const ChainDev &ch, int comp, int y, int kx) {
   const long long R4 = (long long)((ch.nrows + 3) & ~3);
-  return ch.s_off + (long long)comp * R4 * ch.Sx + (long long)(y >> 2) * 4 * ch.Sx + 4LL * kx + (y & 3);
+  return ch.s_off + (long long)comp * R4 * kW32Sx + (long long)(y >> 2) * kW32Tile + 4LL * kx + (y & 3);
 }
 
 __global__ void __launch_bounds__(192, 3) k_w32_rows_fwd(W32Args A) {
@@ -60,22 +68,31 @@ __global__ void __launch_bounds__(192, 3) k_w32_rows_fwd(W32Args A) {
   const int nx = ch.nx, ny = ch.ny;
   float2 *buf = sm + w * kW32Buf;
 
-  // z = Mx + i My of row r0 (q = 0) or r1 (q = 1), or Mz(r0) + i Mz(r1) (q = 2)
+  // z = Mx + i My of row r0 (q = 0) or r1 (q = 1), or Mz(r0) + i Mz(r1) (q = 2).
+  // Cell x = 32 n1 + lane of row r is in colour (lane + r) & 1 at slot
+  // 16 n1 + lane / 2 (one-cell-thick chain: row r = j)
+  const long long S = (long long)ch.nrows * ch.hx;
+  const bool pc = ch.ms_off >= 0;
+  const float Msu = (float)ch.Ms0d;
+  const int ra = q == 1 ? r1 : r0;                     // the row of x + i y, or of Mz (q = 2)
+  const long long oa = (long long)((lane + ra) & 1) * S + (long long)ra * ch.hx + (lane >> 1);
+  const long long ob = (long long)((lane + r1) & 1) * S + (long long)r1 * ch.hx + (lane >> 1);
+  const float4 *ma = A.m + ch.m_off + oa, *mb = A.m + ch.m_off + ob;
+  const bool ha = ra < ny, hb = q == 2 && r1 < ny;
   float2 v[32];
 #pragma unroll
   for (int n1 = 0; n1 < 16; ++n1) {
-    const int x = 32 * n1 + lane;
+    const bool in = 32 * n1 + lane < nx;
     float2 z = make_float2(0.f, 0.f);
-    if (x < nx) {
-      float Mx, My, Mz;
-      if (q == 0) {
-        if (r0 < ny) { load_M<float>(ch, A.m, A.ms, r0, x, Mx, My, Mz); z = make_float2(Mx, My); }
-      } else if (q == 1) {
-        if (r1 < ny) { load_M<float>(ch, A.m, A.ms, r1, x, Mx, My, Mz); z = make_float2(Mx, My); }
-      } else {
-        if (r0 < ny) { load_M<float>(ch, A.m, A.ms, r0, x, Mx, My, Mz); z.x = Mz; }
-        if (r1 < ny) { load_M<float>(ch, A.m, A.ms, r1, x, Mx, My, Mz); z.y = Mz; }
-      }
+    if (in && ha) {
+      const float4 t = ma[16 * n1];
+      const float Ms = pc ? A.ms[ch.ms_off + oa + 16 * n1] : Msu;
+      z = q == 2 ? make_float2(Ms * t.z, 0.f) : make_float2(Ms * t.x, Ms * t.y);
+    }
+    if (in && hb) {
+      const float4 t = mb[16 * n1];
+      const float Ms = pc ? A.ms[ch.ms_off + ob + 16 * n1] : Msu;
+      z.y = Ms * t.z;
     }
     v[n1] = z;
   }
@@ -97,44 +114,61 @@ __global__ void __launch_bounds__(192, 3) k_w32_rows_fwd(W32Args A) {
     Y[k2] = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));
   }
   __syncthreads();                                     // every warp done with its buffer
-  // output tile [comp][kx][4 rows] in shared memory (aliases the warp buffers)
+  // output tile [comp][row][kx] in shared memory (aliases the warp buffers; row
+  // pitch kW32TilePitch keeps the stores and the gather below free of bank conflicts)
   const int cA = q == 2 ? 2 : 0, cB = q == 2 ? 2 : 1;
   const int rA = q == 1 ? 2 * p + 1 : 2 * p, rB = q == 0 ? 2 * p : 2 * p + 1;
 #pragma unroll
   for (int k2 = 0; k2 < 17; ++k2) {
     if (k2 == 16 && lane != 0) break;
     const int k = lane + 32 * k2;
-    sm[(cA * kW32Half + k) * 4 + rA] = X[k2];
-    sm[(cB * kW32Half + k) * 4 + rB] = Y[k2];
+    sm[(cA * 4 + rA) * kW32TilePitch + k] = X[k2];
+    sm[(cB * 4 + rB) * kW32TilePitch + k] = Y[k2];
   }
   __syncthreads();
-  // the tile of every component is contiguous in global memory: 513 x 4 values
-  const float4 *src = reinterpret_cast<const float4 *>(sm);
+  // the tile of every component is contiguous in global memory: [kx][4 rows],
+  // written as float4 pairs (rows 2h, 2h + 1 of one kx)
   constexpr int per = kW32Half * 2;                    // float4 per component
   for (int i = threadIdx.x; i < 3 * per; i += blockDim.x) {
     const int comp = i / per, o = i - comp * per;
+    const int kx = o >> 1, h = o & 1;
+    const float2 a = sm[(comp * 4 + 2 * h) * kW32TilePitch + kx];
+    const float2 b = sm[(comp * 4 + 2 * h + 1) * kW32TilePitch + kx];
     float4 *dst = reinterpret_cast<float4 *>(A.S + w32_at(ch, comp, 4 * tile, 0));
-    dst[o] = src[i];
+    dst[o] = make_float4(a.x, a.y, b.x, b.y);
   }
 }
 
 __global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+  float *tn = reinterpret_cast<float *>(sm + 3 * kW32Buf);   // this column's tensor, [4][kW32TPitch]
+  __shared__ uint64_t tbar;
   const int c = A.blk_chain[blockIdx.x];
   const ChainDev &ch = A.chains[c];
   const int kx = (int)(blockIdx.x - A.blk_first[c]);
   const int lane = threadIdx.x & 31, comp = threadIdx.x >> 5;
   const int ny = ch.ny;
   float2 *buf = sm + comp * kW32Buf;
-  float2 *S = A.S;
+  // the column's four tensor components come in by bulk copy while the
+  // forward transforms run
+  if (threadIdx.x == 0) {
+    mbar_init(&tbar, 1);
+    mbar_init_fence();
+    const float *src = A.nhatT[ch.spec] + (long long)kx * kW32TPitch;
+    mbar_arrive_expect_tx(&tbar, 4u * kW32TPitch * 4u);
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      bulk_g2s(tn + t * kW32TPitch, src + (long long)t * kW32TQ, kW32TPitch * 4u, &tbar);
+  }
+  // column kx of component comp: row y = 32 n1 + lane is in tile 8 n1 + lane / 4
+  const long long R4 = (long long)((ch.nrows + 3) & ~3);
+  float2 *col = A.S + ch.s_off + (long long)comp * R4 * kW32Sx + (long long)(lane >> 2) * kW32Tile + 4 * kx + (lane & 3);
 
   float2 v[32];
 #pragma unroll
-  for (int n1 = 0; n1 < 16; ++n1) {
-    const int y = 32 * n1 + lane;
-    v[n1] = y < ny ? S[w32_at(ch, comp, y, kx)] : make_float2(0.f, 0.f);
-  }
+  for (int n1 = 0; n1 < 16; ++n1)
+    v[n1] = 32 * n1 + lane < ny ? col[(long long)n1 * 8 * kW32Tile] : make_float2(0.f, 0.f);
   dft32_lo16(v);
   w32_fwd_tail(v, buf, A.tw, lane);                    // v[k2] = M^_comp(kx, lane + 32 k2)
 
@@ -142,38 +176,43 @@ __global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A) {
 #pragma unroll
   for (int k2 = 0; k2 < 32; ++k2) buf[lane + 32 * k2] = v[k2];
   __syncthreads();
-  const float *nt = A.nhatT[ch.spec];
-  constexpr long long Q = (long long)kW32Half * kW32Half;
-  const long long col = (long long)kx * kW32Half;
+  if (!mbar_wait(&tbar, 0u, kW32Polls)) {
+    // MMC_ERR_TIMEOUT; this column's field is left as it was.  The copy may
+    // still be in flight: give it a fixed time (about a millisecond) to land
+    // before the block's shared memory is released.
+    if (threadIdx.x == 0) atomicExch(A.err, -3);
+    const long long t0 = clock64();
+    while (clock64() - t0 < (1LL << 21)) {
+    }
+    return;
+  }
   if (comp < 2) {
     const float2 *other = sm + (1 - comp) * kW32Buf;
-    const float *Nd = nt + comp * Q + col;             // xx (x warp) or yy (y warp)
-    const float *Nxy = nt + 3 * Q + col;
+    const float *Nd = tn + comp * kW32TPitch;          // xx (x warp) or yy (y warp)
+    const float *Nxy = tn + 3 * kW32TPitch;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) {
       const int ky = lane + 32 * k2;
       const int kyq = ky <= 512 ? ky : kW32N - ky;
-      const float nd = __ldg(Nd + kyq);
-      const float nxy = ky <= 512 ? __ldg(Nxy + kyq) : -__ldg(Nxy + kyq);
+      const float nd = Nd[kyq];
+      const float nxy = ky <= 512 ? Nxy[kyq] : -Nxy[kyq];
       const float2 o = other[lane + 32 * k2];
       v[k2] = make_float2(-(nd * v[k2].x + nxy * o.x), -(nd * v[k2].y + nxy * o.y));
     }
   } else {
-    const float *Nzz = nt + 2 * Q + col;
+    const float *Nzz = tn + 2 * kW32TPitch;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) {
       const int ky = lane + 32 * k2;
-      const float nz = __ldg(Nzz + (ky <= 512 ? ky : kW32N - ky));
+      const float nz = Nzz[ky <= 512 ? ky : kW32N - ky];
       v[k2] = make_float2(-nz * v[k2].x, -nz * v[k2].y);
     }
   }
   __syncthreads();                                     // the other warp has read this buffer
   w32_inv(v, buf, A.tw, lane);                         // v[n''] = H_comp(kx, row lane + 32 n'')
 #pragma unroll
-  for (int n2 = 0; n2 < 16; ++n2) {
-    const int y = lane + 32 * n2;
-    if (y < ny) S[w32_at(ch, comp, y, kx)] = v[n2];
-  }
+  for (int n2 = 0; n2 < 16; ++n2)
+    if (lane + 32 * n2 < ny) col[(long long)n2 * 8 * kW32Tile] = v[n2];
 }
 
 __global__ void __launch_bounds__(192, 3) k_w32_rows_inv(W32Args A) {
@@ -255,8 +294,9 @@ __global__ void __launch_bounds__(192, 3) k_w32_rows_inv(W32Args A) {
 }
 
 constexpr size_t kW32RowsSmem = 6 * kW32Buf * sizeof(float2);
-constexpr size_t kW32ColsSmem = 3 * kW32Buf * sizeof(float2);
-static_assert(kW32RowsSmem >= 3 * kW32Half * 4 * sizeof(float2), "output tile fits the warp buffers");
+constexpr size_t kW32ColsSmem = 3 * kW32Buf * sizeof(float2) + 4 * kW32TPitch * sizeof(float);
+static_assert(kW32RowsSmem >= 12 * kW32TilePitch * sizeof(float2), "output tile fits the warp buffers");
+static_assert((3 * kW32Buf * sizeof(float2)) % 16 == 0 && (kW32TPitch * 4) % 16 == 0, "bulk copy alignment");
 static_assert(kW32RowsSmem >= 12 * kW32TilePitch * sizeof(float2), "input tile fits the warp buffers");
 static_assert(kW32RowsSmem >= 12 * 512 * sizeof(float), "field tile fits the warp buffers");
 
@@ -267,6 +307,7 @@ void launch_w32(const Launch &L, const DemagLaunch &P) {
   A.nhatT = reinterpret_cast<const float *const *>(P.nhatT);
   A.tw = reinterpret_cast<const float2 *>(P.tw1024);
   A.heff = P.heff; A.Hd = P.Hd; A.Hd_chain = P.Hd_chain;
+  A.err = P.err;
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
   if (P.ev) cudaEventRecord(P.ev[0], L.stream);
   k_w32_rows_fwd<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);

@@ -270,14 +270,16 @@ struct DemagLaunch {
   int fft_variant;              // FP32 2D kernels: 1 radix 16 (384 threads), 2 radix 32 (192 threads)
   size_t inv_smem;              // shared memory of the 2D inverse row kernel
   bool w32;                     // FP32 1024 x 1024 warp-transform kernels (k_demag_w32.cu)
-  const void *const *nhatT;     // their tensor spectra, per set [comp][kx][kyq] (or null)
+  const void *const *nhatT;     // their tensor spectra, per set [comp][kx][kyq] (or null), kyq pitch kW32TensorPitch
   const void *tw1024;           // their 32 x 32 twiddle table
+  int *err;                     // device error word of bounded waits
 };
+constexpr int kW32TensorPitch = 516;   // kyq = 0..512 padded to a 16-byte multiple of floats
 void launch_w32(const Launch &L, const DemagLaunch &P);
 cudaError_t w32_set_smem();
 // a chain the warp-transform path handles: one cell thick, padded grid 1024 x 1024, open demag
 inline bool w32_chain(const ChainDev &D) {
-  return D.nz == 1 && D.Pz == 1 && D.Px == 1024 && D.Py == 1024 && D.circ == 0 && D.Sx >= 513;
+  return D.nz == 1 && D.Pz == 1 && D.Px == 1024 && D.Py == 1024 && D.circ == 0 && D.Sx == 520;
 }
 // rows of a chain's spectrum buffer: 2D chains round up to tiles of four rows
 inline long long spectrum_rows(const ChainDev &D) { return D.Pz == 1 ? ((D.nrows + 3) & ~3) : D.nrows; }
