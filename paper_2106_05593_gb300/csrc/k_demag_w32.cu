@@ -56,7 +56,7 @@ __device__ __forceinline__ long long w32_at(const ChainDev &ch, int comp, int y,
   return ch.s_off + (long long)comp * R4 * kW32Sx + (long long)(y >> 2) * kW32Tile + 4LL * kx + (y & 3);
 }
 
-__global__ void __launch_bounds__(192, 4) k_w32_rows_fwd(W32Args A) {
+__global__ void __launch_bounds__(192, 3) k_w32_rows_fwd(W32Args A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
   const int c = A.blk_chain[blockIdx.x];
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A) {
     if (lane + 32 * n2 < ny) col[(long long)n2 * 8 * kW32Tile] = v[n2];
 }
 
-__global__ void __launch_bounds__(192, 4) k_w32_rows_inv(W32Args A) {
+__global__ void __launch_bounds__(192, 3) k_w32_rows_inv(W32Args A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
   const int c = A.blk_chain[blockIdx.x];
