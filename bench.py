@@ -435,7 +435,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     if args.profile_run > 0:
         gp = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), use_graphs=0,
-                 fft_variant=args.fft_variant, sweep_tiles=args.sweep_tiles, stream=stream)
+                 fft_variant=args.fft_variant, sweep_tiles=args.sweep_tiles, stream_groups=args.stream_groups,
+                 stream=stream)
         gp.init_random(replica_seed(rank))
         gp.sweep(args.profile_run, replica_seed(rank))
         torch.cuda.synchronize()
