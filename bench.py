@@ -63,6 +63,8 @@ def parse():
                     help="chain groups iterating on concurrent streams: 0 auto (2), 1 one stream")
     ap.add_argument("--sweep-tiles", type=int, default=0, choices=(0, 1),
                     help="1 banded pass on shared-memory halo tiles where the batch allows it, 0 per-block pass")
+    ap.add_argument("--fuse-passes", type=int, default=1, choices=(0, 1),
+                    help="1 black pass fused with the next forward row transforms where the batch allows it")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the cuFFT demag timing and the one-chain-per-launch comparison")
     ap.add_argument("--chains", type=int, default=0, help="use only the first N chains of the workload")
@@ -233,6 +235,8 @@ def algorithmic_bytes(kind, demag, percell, spec=24.0):
         return 2.0 * spec
     if kind == "demag_rows_inv":  # spectrum read (spec B), h_eff written 16 B
         return spec + 16.0
+    if kind == "black_pass_rows_fwd":   # m read 16 B (both colours), black m written 8 B and black h_eff
+        return 16.0 + 8.0 + 8.0 + spec  # read 8 B per cell (16 B per black cell), spectrum written
     return 0.0
 
 
@@ -436,14 +440,15 @@ def run_ours(args):
     if args.profile_run > 0:
         gp = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), use_graphs=0,
                  fft_variant=args.fft_variant, sweep_tiles=args.sweep_tiles, stream_groups=args.stream_groups,
-                 stream=stream)
+                 fuse_passes=args.fuse_passes, stream=stream)
         gp.init_random(replica_seed(rank))
         gp.sweep(args.profile_run, replica_seed(rank))
         torch.cuda.synchronize()
         print("profile run ok", gp.launches, flush=True)
         return
     g = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=args.fft_variant,
-            stream_groups=args.stream_groups, sweep_tiles=args.sweep_tiles, stream=stream)
+            stream_groups=args.stream_groups, sweep_tiles=args.sweep_tiles, fuse_passes=args.fuse_passes,
+            stream=stream)
     seed = replica_seed(rank)
     g.init_random(seed)
     ncell = sum(g.ncell)
@@ -521,7 +526,15 @@ def run_ours(args):
         compare = {}
         if demag:
             kinds = ("demag_rows_fwd", "demag_cols", "demag_rows_inv")
-            own = sum(phases[k][0] for k in kinds) / max(phases["demag_cols"][1], 1)
+            ph_d = phases
+            if phases["black_pass_rows_fwd"][1] > 0:
+                # the forward rows run inside the fused black pass: time the three
+                # demag kernels on their own in a context without the fusion
+                gu = MMC(specs, demag=1, fuse_passes=0, fft_variant=g.fft_tuning()[0], stream=stream)
+                gu.init_random(seed)
+                ph_d = gu.phase_times(20, seed)
+                del gu
+            own = sum(ph_d[k][0] for k in kinds) / max(ph_d["demag_cols"][1], 1)
             cf = MMC(specs, demag=1, demag_cufft=1, demag_fp64=int(args.fp64_demag), stream=stream)
             cf.init_random(seed)
             ph = cf.phase_times(20, seed)

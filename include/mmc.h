@@ -155,6 +155,14 @@ typedef struct {
     int wait_test;            /* test hook for that path: 1 makes every band wait
                                  for 16 bytes that no copy delivers, so every wait
                                  runs out (no band is updated)                  [0] */
+    int fuse_passes;          /* 1: batches of uniform one-cell-thick chains on the
+                                 1024 x 1024 warp-transform demag kernels (FFT
+                                 variant 4) run the black pass and the next
+                                 iteration's forward row transforms as one kernel
+                                 per tile of four rows (the rows are final once
+                                 their black cells moved); 0: separate kernels.
+                                 The same moves either way, up to the last-bit
+                                 rounding of separately compiled kernels.       [1] */
 } mmc_options;
 
 /* One chain of a batch. T_cell (optional, HOST) gives a per-cell temperature;
@@ -381,9 +389,11 @@ mmc_status mmc_minimize(mmc_ctx *ctx, int chain, int64_t maxit, double tol, int6
  * graphs) with CUDA events recorded on the context's stream around every kernel
  * and returns, per kernel kind, the summed duration in ms (ms) and the number
  * of launches (count).  Kinds: 0 demag rows forward, 1 demag columns, 2 demag
- * rows inverse, 3 sublattice pass, 4 observables, 5 window/adaptation step.
- * Both arrays have 6 entries (HOST). */
-mmc_status mmc_phase_times(mmc_ctx *ctx, int64_t n, uint64_t seed, double ms[6], int64_t count[6]);
+ * rows inverse, 3 sublattice pass, 4 observables, 5 window/adaptation step,
+ * 6 black pass fused with the forward rows (mmc_options.fuse_passes; then kind
+ * 0 is the forward rows that start each block of iterations and kind 3 the red
+ * passes).  Both arrays have 7 entries (HOST). */
+mmc_status mmc_phase_times(mmc_ctx *ctx, int64_t n, uint64_t seed, double ms[7], int64_t count[7]);
 
 /* FFT variant of the batch's FP32 2D demag kernels (1 radix 16 with 768-thread
  * blocks, 2 radix 32 with 384-thread blocks, 3 radix 16 with 384-thread blocks,

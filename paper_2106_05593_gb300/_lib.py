@@ -54,7 +54,7 @@ class Options(C.Structure):
         ("sigma_cap", C.c_double), ("hist_bins", C.c_int), ("hist_max", C.c_double),
         ("use_graphs", C.c_int), ("stream_groups", C.c_int), ("demag_self", C.c_int), ("fft_variant", C.c_int),
         ("demag_stripes", C.c_int), ("chain_base", C.c_int),
-        ("sweep_tiles", C.c_int), ("wait_polls", C.c_int), ("wait_test", C.c_int),
+        ("sweep_tiles", C.c_int), ("wait_polls", C.c_int), ("wait_test", C.c_int), ("fuse_passes", C.c_int),
     ]
 
 

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <filesystem>
+#include <functional>
 #include <fstream>
 #include <sstream>
 #include <string>
@@ -855,10 +856,72 @@ void timed(mmc_ctx *c, PhaseTimer *pt, int kind, F fn) {
   pt->marks.push_back({kind, {i0, i1}});
 }
 
+// the iteration of batches on the warp-transform demag path with uniform
+// one-cell-thick chains fuses the black pass with the next iteration's forward
+// row transforms (k_w32_black_rows_fwd): a block of k iterations is the forward
+// rows of the current state, then k times {columns, inverse rows, red pass,
+// black pass + forward rows}
+bool fused_path(const mmc_ctx *c) {
+  return c->opt.fuse_passes && c->any_demag && c->cf.empty() && !c->batch_plan.fp64 &&
+         c->batch_plan.fft_variant == 4 && c->batch_plan.w32.ok && c->all_flat && !c->any_percell && !c->band &&
+         !c->opt.demag_per_pass && pass_bands(c) == 1;
+}
+
+// k fused iterations of the chains of plan / blocks [b0, b0 + nb) on L
+void issue_fused(mmc_ctx *c, const Launch &L, const DemagPlan &plan, int b0, int nb, int k, unsigned key0,
+                 unsigned key1, int sample_every, uint64_t start, PhaseTimer *pt) {
+  const DemagLaunch D = make_demag_launch(c, plan, c->d_heff, nullptr, -1);
+  const auto tm = [&](int kind, const std::function<void()> &fn) {
+    if (!pt) { fn(); return; }
+    const int i0 = (int)pt->used;
+    cudaEventRecord(pt->next(), L.stream);
+    fn();
+    const int i1 = (int)pt->used;
+    cudaEventRecord(pt->next(), L.stream);
+    pt->marks.push_back({kind, {i0, i1}});
+  };
+  tm(0, [&] { launch_w32_stage(L, D, 0); });
+  for (int off = 0; off < k; ++off) {
+    tm(1, [&] { launch_w32_stage(L, D, 1); });
+    tm(2, [&] { launch_w32_stage(L, D, 2); });
+    SweepLaunch red = sweep_launch(c, 0, (unsigned)off, key0, key1);
+    red.blk_base = b0;
+    red.nblocks = nb;
+    tm(3, [&] { launch_sweep_pass(L, red); });
+    const SweepLaunch blk = sweep_launch(c, 1, (unsigned)off, key0, key1);
+    tm(6, [&] { launch_w32_black_rows_fwd(L, D, blk); });
+    if (sample_every > 0 && (start + off + 1) % (uint64_t)sample_every == 0) {
+      Trace t("observables");
+      tm(4, [&] { launch_obs(L, obs_launch(c, 1)); });
+    }
+  }
+}
+
 // k sweeps starting at global sweep index `start` (device base == start)
 void issue_block(mmc_ctx *c, int k, unsigned key0, unsigned key1, int sample_every, uint64_t start,
                  PhaseTimer *pt = nullptr) {
   Launch L = c->L();
+  if (fused_path(c)) {
+    if (!c->groups.empty() && !pt && sample_every == 0) {
+      cudaEventRecord(c->ev_fork, c->stream);
+      for (auto &g : c->groups) {
+        cudaStreamWaitEvent(g.stream, c->ev_fork, 0);
+        Launch Lg{g.stream, &c->launches};
+        const int b0 = (int)c->sw_first[(size_t)g.c0], nb = (int)(c->sw_first[(size_t)g.c1] - b0);
+        issue_fused(c, Lg, g.plan, b0, nb, k, key0, key1, 0, start, nullptr);
+        cudaEventRecord(g.done, g.stream);
+        cudaStreamWaitEvent(c->stream, g.done, 0);
+      }
+    } else {
+      issue_fused(c, L, c->batch_plan, 0, c->sw_blocks, k, key0, key1, sample_every, start, pt);
+    }
+    const int adapt_now = ((start + k) % 100 == 0) ? 1 : 0;
+    Trace t("advance");
+    timed(c, pt, 5, [&] {
+      launch_advance(L, c->d_st, c->nchains, (unsigned)k, c->d_sweep_base, adapt_now, c->opt.adapt, 1.f, 180.f);
+    });
+    return;
+  }
   if (!c->groups.empty() && !pt && sample_every == 0) {
     // fork: every group runs its k iterations on its own stream (the chains of
     // different groups never interact), join before the window step
@@ -996,7 +1059,7 @@ std::string tune_key(const mmc_ctx *c) {
   std::ostringstream d;
   d << "v1|n" << c->nchains << "|fp64 " << c->opt.demag_fp64 << "|cufft " << c->opt.demag_cufft << "|demag "
     << c->opt.demag << "|pp " << c->opt.demag_per_pass << "|st " << c->opt.demag_stripes << "|tiles "
-    << c->opt.sweep_tiles;
+    << c->opt.sweep_tiles << "|fuse " << c->opt.fuse_passes;
   for (int i = 0; i < c->nchains; ++i) {
     const mmc_mesh &m = c->hc[i].mesh;
     d << "|" << m.nx << "x" << m.ny << "x" << m.nz << "p" << m.periodic[0] << m.periodic[1] << m.periodic[2] << "i"
@@ -1170,6 +1233,7 @@ mmc_status mmc_default_options(mmc_options *o) {
   o->fft_variant = 0;
   o->demag_stripes = 1;
   o->sweep_tiles = 0;
+  o->fuse_passes = 1;
   o->wait_polls = 0;
   o->wait_test = 0;
   return MMC_OK;
@@ -2175,10 +2239,10 @@ mmc_status mmc_minimize(mmc_ctx *c, int chain, int64_t maxit, double tol, int64_
   return MMC_OK;
 }
 
-mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[6], int64_t count[6]) {
+mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[7], int64_t count[7]) {
   if (!c || !ms || !count) return fail(MMC_ERR_ARG, "null argument");
   if (n < 0) return fail(MMC_ERR_ARG, "negative sweep count");
-  for (int k = 0; k < 6; ++k) { ms[k] = 0; count[k] = 0; }
+  for (int k = 0; k < 7; ++k) { ms[k] = 0; count[k] = 0; }
   const unsigned key0 = (unsigned)(seed & 0xffffffffu), key1 = (unsigned)(seed >> 32);
   PhaseTimer pt;
   mmc_status st = MMC_OK;

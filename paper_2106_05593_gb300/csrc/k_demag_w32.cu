@@ -23,7 +23,9 @@
 //                   and the sweep's field zee (B + mu0 H) in the split layout.
 #include "demag_args.cuh"
 #include "fft_w32.cuh"
+#include "philox.cuh"
 #include "tma.cuh"
+#include "trial.cuh"
 
 namespace mmc {
 
@@ -293,6 +295,225 @@ __global__ void __launch_bounds__(192, 3) k_w32_rows_inv(W32Args A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// The black sublattice pass of a tile of four rows fused with the forward row
+// transforms of the next iteration's demag update (uniform one-cell-thick
+// chains on this path).  Once the black pass of a tile is done its four rows
+// are final for the iteration (the red cells were final after the red pass),
+// so the block can transform them at once.  The tile's black rows, the red rows
+// r0 - 1 .. r0 + 4 (halo rows wrapped on periodic y axes, left out at open
+// edges) and the black h_eff rows come into shared memory by bulk copy; the
+// black pass runs there (the moves of the per-block pass, cell for cell) and
+// writes its accepted moves to the tile and to the state; the transforms then
+// read every M value from the tiles.
+constexpr int kFusedHx = 256;                          // largest hx on this path (nx <= 512)
+constexpr int kFusedThreads = 192;
+constexpr size_t kFusedSmem = (size_t)14 * kFusedHx * sizeof(float4);
+static_assert(kFusedSmem >= 6 * kW32Buf * sizeof(float2), "the tiles cover the warp buffers");
+
+struct FusedArgs {
+  W32Args W;
+  float4 *m;                    // the state (written by the pass)
+  ChainState *st;
+  const float4 *heff;           // the sweep's field, split layout
+  const unsigned *sweep_base;
+  unsigned sweep_off;
+  unsigned rk[20];              // Philox round keys
+  unsigned max_polls;
+};
+
+__global__ void __launch_bounds__(kFusedThreads, 3) k_w32_black_rows_fwd(FusedArgs F) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+  float4 *tb = reinterpret_cast<float4 *>(smem_raw);  // black rows r0 .. r0 + nr - 1, pitch hx
+  float4 *tr = tb + 4 * kFusedHx;                      // red rows r0 - 1 .. r0 + nr, pitch hx
+  float4 *th = tr + 6 * kFusedHx;                      // black h_eff rows r0 .. r0 + nr - 1
+  __shared__ uint64_t bar;
+  __shared__ float4 skv[kChainKVec];
+  __shared__ unsigned wacc[kFusedThreads / 32], watt[kFusedThreads / 32];
+  const W32Args &A = F.W;
+  const int c = A.blk_chain[blockIdx.x];
+  const ChainDev &ch = A.chains[c];
+  const int tile = (int)(blockIdx.x - A.blk_first[c]);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nx = ch.nx, ny = ch.ny, hx = ch.hx;
+  const int r0 = 4 * tile, nr = min(4, ny - r0);
+  const long long S = (long long)ch.nrows * hx;
+  const float4 *mred = A.m + ch.m_off;
+  float4 *mblk = F.m + ch.m_off + S;
+  if (threadIdx.x < kChainKVec) skv[threadIdx.x] = __ldg(reinterpret_cast<const float4 *>(A.chains + c) + threadIdx.x);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+    const bool pby = (ch.pbc & 2) != 0;
+    const int rb = r0 > 0 ? r0 - 1 : (pby ? ny - 1 : -1);
+    const int ra = r0 + nr < ny ? r0 + nr : (pby ? 0 : -1);
+    const unsigned row_b = (unsigned)hx * 16u;
+    mbar_arrive_expect_tx(&bar, 3u * (unsigned)nr * row_b + (rb >= 0 ? row_b : 0u) + (ra >= 0 ? row_b : 0u));
+    bulk_g2s(tb, mblk + (long long)r0 * hx, (unsigned)nr * row_b, &bar);
+    bulk_g2s(tr + hx, mred + (long long)r0 * hx, (unsigned)nr * row_b, &bar);
+    if (rb >= 0) bulk_g2s(tr, mred + (long long)rb * hx, row_b, &bar);
+    if (ra >= 0) bulk_g2s(tr + (long long)(nr + 1) * hx, mred + (long long)ra * hx, row_b, &bar);
+    bulk_g2s(th, F.heff + ch.h_off + S + (long long)r0 * hx, (unsigned)nr * row_b, &bar);
+  }
+  __syncthreads();
+  const ChainK K = load_chain_vec(skv);
+  if (!mbar_wait(&bar, 0u, F.max_polls)) {
+    if (threadIdx.x == 0) atomicExch(A.err, -3);      // MMC_ERR_TIMEOUT: this tile is left as it was
+    const long long t0 = clock64();
+    while (clock64() - t0 < (1LL << 21)) {
+    }
+    return;
+  }
+
+  // 1. the black pass (colour 1) on the tile's cells
+  const unsigned sweep = *F.sweep_base + F.sweep_off;
+  const float omc = F.st[c].omc;
+  const int pbc = K.pbc & 3, flags = K.flags;
+  const unsigned nslots = (unsigned)(nr * hx);
+  unsigned na = 0, nv = 0;
+#pragma unroll 1
+  for (int e0 = 0; e0 < 6; e0 += 2) {                  // 4 rows x 256 slots over 192 threads
+    bool valid[2];
+    unsigned ql[2], cellid[2];
+    float4 a[2], h[2], nb[2][4];
+    float pres[2][4];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const unsigned q = threadIdx.x + (unsigned)((e0 + e) * kFusedThreads);
+      bool ok = q < nslots;
+      const int rl = ok ? (int)divq(q, K.hx_m, K.hx_l) : 0;
+      const int sl = (int)(q - (unsigned)rl * (unsigned)hx);
+      const int j = r0 + rl;
+      const int pp = (j + 1) & 1;
+      const int i = 2 * sl + pp;
+      ok = ok && (i < nx);
+      valid[e] = ok;
+      ql[e] = q;
+      cellid[e] = (unsigned)i + (unsigned)nx * (unsigned)j;
+      if (ok) {
+        a[e] = tb[q];
+        const float4 *O = tr + (rl + 1) * hx + sl;
+        const bool hl = i > 0 || (pbc & 1), hr = i < nx - 1 || (pbc & 1);
+        const bool hu = j > 0 || (pbc & 2), hd = j < ny - 1 || (pbc & 2);
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        nb[e][0] = hl ? O[i > 0 ? pp - 1 : hx - 1] : z4;
+        nb[e][1] = hr ? O[i < nx - 1 ? pp : 1 - hx] : z4;
+        nb[e][2] = hu ? O[-hx] : z4;
+        nb[e][3] = hd ? O[hx] : z4;
+        pres[e][0] = hl ? 1.f : 0.f;
+        pres[e][1] = hr ? 1.f : 0.f;
+        pres[e][2] = hu ? 1.f : 0.f;
+        pres[e][3] = hd ? 1.f : 0.f;
+        if (flags & F_GRAIN) {
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (nb[e][b].w != a[e].w) pres[e][b] *= K.gscale;
+        }
+        h[e] = th[q];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      int acc = 0;
+      if (valid[e]) {
+        const float wv[4] = {K.wx * pres[e][0], K.wx * pres[e][1], K.wy * pres[e][2], K.wy * pres[e][3]};
+        const uint4 r = philox4x32_10_rk(make_uint4(cellid[e], sweep, (unsigned)K.chain, 0u), F.rk);
+        const MoveAngles ga = move_angles(K.sigma, omc, uniform01(r.x), uniform01(r.y), uniform01(r.z));
+        const float u3 = uniform01(r.w);
+        Move v = move_length(a[e], K.me2h, K.me2l);
+        move_direction_g(v, a[e], ga);
+        const float floc = local_change_flat(v, a[e], nb[e], wv, pres[e], K.cdx, K.cdy, (flags & F_DMI) != 0,
+                                             h[e].x, h[e].y, h[e].z);
+        const float flong = longitudinal_change(v, K.p2, K.p4);
+        const float fan = anisotropy_change(v, flags, K.k1, K.k2, K.ex, K.ey, K.ez);
+        const float dl = floc + flong + fan - 4.f * log1p_move_s(v.tt, K.sigma);
+        acc = dl + __logf(u3) < 0.f;
+        if (acc) {
+          const float4 mp = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
+          tb[ql[e]] = mp;
+          mblk[(long long)r0 * hx + ql[e]] = mp;
+        }
+      }
+      na += __popc(__ballot_sync(0xffffffffu, acc));
+      nv += __popc(__ballot_sync(0xffffffffu, valid[e]));
+    }
+  }
+  if (lane == 0) {
+    wacc[w] = na;
+    watt[w] = nv;
+  }
+  __syncthreads();                                     // the tile's rows are final; counts ready
+  if (threadIdx.x == 0) {
+    unsigned sa = 0, sv = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < kFusedThreads / 32; ++w2) { sa += wacc[w2]; sv += watt[w2]; }
+    if (sv) {
+      atomicAdd(&F.st[c].win_acc, (unsigned long long)sa);
+      atomicAdd(&F.st[c].win_att, (unsigned long long)sv);
+    }
+  }
+
+  // 2. the forward row transforms of the four rows, M from the tiles
+  const int p = w / 3, q = w - 3 * p;
+  const int rA = 4 * tile + 2 * p, rB = rA + 1;
+  const float Ms = (float)ch.Ms0d;
+  const int ra = q == 1 ? rB : rA;
+  const bool ha = ra < ny, hb = q == 2 && rB < ny;
+  // cell x = 32 n1 + lane of row r: colour (lane + r) & 1, slot 16 n1 + lane / 2
+  const float4 *ta = ((lane + ra) & 1) ? tb + (ra - r0) * hx : tr + (ra - r0 + 1) * hx;
+  const float4 *tbb = ((lane + rB) & 1) ? tb + (rB - r0) * hx : tr + (rB - r0 + 1) * hx;
+  float2 v[32];
+#pragma unroll
+  for (int n1 = 0; n1 < 16; ++n1) {
+    const int sl = 16 * n1 + (lane >> 1);
+    const bool in = 32 * n1 + lane < nx;
+    float2 z = make_float2(0.f, 0.f);
+    if (in && ha) {
+      const float4 t = ta[sl];
+      z = q == 2 ? make_float2(Ms * t.z, 0.f) : make_float2(Ms * t.x, Ms * t.y);
+    }
+    if (in && hb) z.y = Ms * tbb[sl].z;
+    v[n1] = z;
+  }
+  __syncthreads();                                     // every warp holds its sequence: tiles -> warp buffers
+  float2 *buf = sm + w * kW32Buf;
+  dft32_lo16(v);
+  w32_fwd_tail(v, buf, A.tw, lane);
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) buf[lane + 32 * k2] = v[k2];
+  __syncwarp();
+  float2 X[17], Y[17];
+#pragma unroll
+  for (int k2 = 0; k2 < 17; ++k2) {
+    if (k2 == 16 && lane != 0) break;
+    const int k = lane + 32 * k2;
+    const float2 Z = v[k2], Zm = buf[(kW32N - k) & (kW32N - 1)];
+    X[k2] = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
+    Y[k2] = make_float2(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));
+  }
+  __syncthreads();
+  const int cA = q == 2 ? 2 : 0, cB = q == 2 ? 2 : 1;
+  const int oA = q == 1 ? 2 * p + 1 : 2 * p, oB = q == 0 ? 2 * p : 2 * p + 1;
+#pragma unroll
+  for (int k2 = 0; k2 < 17; ++k2) {
+    if (k2 == 16 && lane != 0) break;
+    const int k = lane + 32 * k2;
+    sm[(cA * 4 + oA) * kW32TilePitch + k] = X[k2];
+    sm[(cB * 4 + oB) * kW32TilePitch + k] = Y[k2];
+  }
+  __syncthreads();
+  constexpr int per = kW32Half * 2;
+  for (int i = threadIdx.x; i < 3 * per; i += blockDim.x) {
+    const int comp = i / per, o = i - comp * per;
+    const int kx = o >> 1, hh = o & 1;
+    const float2 aa = sm[(comp * 4 + 2 * hh) * kW32TilePitch + kx];
+    const float2 bb = sm[(comp * 4 + 2 * hh + 1) * kW32TilePitch + kx];
+    float4 *dst = reinterpret_cast<float4 *>(A.S + w32_at(ch, comp, 4 * tile, 0));
+    dst[o] = make_float4(aa.x, aa.y, bb.x, bb.y);
+  }
+}
+
 constexpr size_t kW32RowsSmem = 6 * kW32Buf * sizeof(float2);
 constexpr size_t kW32ColsSmem = 3 * kW32Buf * sizeof(float2) + 4 * kW32TPitch * sizeof(float);
 static_assert(kW32RowsSmem >= 12 * kW32TilePitch * sizeof(float2), "output tile fits the warp buffers");
@@ -300,7 +521,7 @@ static_assert((3 * kW32Buf * sizeof(float2)) % 16 == 0 && (kW32TPitch * 4) % 16 
 static_assert(kW32RowsSmem >= 12 * kW32TilePitch * sizeof(float2), "input tile fits the warp buffers");
 static_assert(kW32RowsSmem >= 12 * 512 * sizeof(float), "field tile fits the warp buffers");
 
-void launch_w32(const Launch &L, const DemagLaunch &P) {
+static W32Args w32_args(const DemagLaunch &P) {
   W32Args A;
   A.chains = P.chains; A.m = P.m; A.tab = P.tab; A.ms = P.ms;
   A.S = reinterpret_cast<float2 *>(P.spec);
@@ -309,6 +530,11 @@ void launch_w32(const Launch &L, const DemagLaunch &P) {
   A.heff = P.heff; A.Hd = P.Hd; A.Hd_chain = P.Hd_chain;
   A.err = P.err;
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
+  return A;
+}
+
+void launch_w32(const Launch &L, const DemagLaunch &P) {
+  W32Args A = w32_args(P);
   if (P.ev) cudaEventRecord(P.ev[0], L.stream);
   k_w32_rows_fwd<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);
   if (P.ev) cudaEventRecord(P.ev[1], L.stream);
@@ -321,11 +547,46 @@ void launch_w32(const Launch &L, const DemagLaunch &P) {
   *L.counter += 3;
 }
 
+void launch_w32_stage(const Launch &L, const DemagLaunch &P, int stage) {
+  W32Args A = w32_args(P);
+  if (stage == 0) {
+    k_w32_rows_fwd<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);
+  } else if (stage == 1) {
+    A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
+    k_w32_cols<<<P.cols_blocks, 96, kW32ColsSmem, L.stream>>>(A);
+  } else {
+    k_w32_rows_inv<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);
+  }
+  ++*L.counter;
+}
+
+void launch_w32_black_rows_fwd(const Launch &L, const DemagLaunch &P, const SweepLaunch &Q) {
+  FusedArgs F;
+  F.W = w32_args(P);
+  F.m = Q.m;
+  F.st = Q.st;
+  F.heff = Q.heff;
+  F.sweep_base = Q.sweep_base;
+  F.sweep_off = Q.sweep_off;
+  unsigned k0 = Q.key0, k1 = Q.key1;
+  for (int r = 0; r < 10; ++r) {
+    F.rk[2 * r] = k0;
+    F.rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  F.max_polls = Q.max_polls;
+  k_w32_black_rows_fwd<<<P.rows_blocks, kFusedThreads, kFusedSmem, L.stream>>>(F);
+  ++*L.counter;
+}
+
 cudaError_t w32_set_smem() {
   cudaError_t e = cudaFuncSetAttribute(k_w32_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kW32RowsSmem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_w32_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW32RowsSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_w32_black_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_w32_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW32ColsSmem);
 }

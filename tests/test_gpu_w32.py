@@ -73,3 +73,48 @@ def test_w32_falls_back_off_its_grids(P):
     for specs in ([W.chiral(256, 300.0)], [W.chiral_periodic(512, 300.0, 2)], [_chiral(512, 512), W.chiral(200)]):
         g = P.MMC(specs, demag=1, fft_variant=4)
         assert g.fft_tuning()[0] == 1
+
+
+def _ndiff(a, b):
+    d = np.abs(a[:, :3].astype(np.float64) - b[:, :3]).max(axis=1)
+    return int((d > 1e-5).sum()), float(d[d <= 1e-5].max(initial=0.0))
+
+
+def test_fused_black_pass_agrees_with_separate_kernels(P):
+    """The black pass fused with the next forward row transforms (default on
+    this path) against separate kernels: three iterations of a batch of square,
+    ragged and periodic chains from the same states end equal to FP32 rounding
+    except the few cells a decision within that rounding of zero can flip; the
+    per-kernel timing reports the fused kernel."""
+    specs = [_chiral(512, 512, 120.0), _chiral(301, 263, 590.0),
+             _chiral(400, 300, 450.0) | {"pbc": (True, True, False)}]
+    out = []
+    for fuse in (1, 0):
+        g = P.MMC(specs, demag=1, fft_variant=4, fuse_passes=fuse, adapt=0)
+        for k, sp in enumerate(specs):
+            g.set_m(W.random_state(int(np.prod(sp["mesh"])), 60 + k, 0.3, 0.9), k)
+        g.sweep(3, 8)
+        out.append([g.get_m(k) for k in range(len(specs))])
+        ph = g.phase_times(2, 9)
+        assert (ph["black_pass_rows_fwd"][1] > 0) == (fuse == 1)
+    for k in range(len(specs)):
+        nd, agree = _ndiff(out[0][k], out[1][k])
+        print("fused vs separate chain", k, specs[k]["mesh"], "differing", nd, "max |dm| elsewhere %.2e" % agree)
+        assert nd <= 2 and agree < 1e-6
+
+
+def test_fused_path_matches_oracle(P):
+    """Three whole iterations of a ragged chain on the fused path against the
+    oracle's run from the same state."""
+    spec = _chiral(301, 263, 520.0)
+    n = 301 * 263
+    m4 = W.random_state(n, 71, 0.3, 0.6)
+    g = P.MMC(spec, demag=1, fft_variant=4, adapt=0)
+    g.set_m(m4)
+    g.sweep(3, 5)
+    o = O.Oracle(spec)
+    st = O.new_state(seed=5, chain=0, theta_deg=30.0, adapt=False, demag_mode=1)
+    mo, _, _ = o.run(m4[:, :3].astype(np.float64), 3, st)
+    nd, agree = _ndiff(g.get_m(0), mo)
+    print("fused path vs oracle: differing", nd, "max |dm| elsewhere %.2e" % agree)
+    assert nd <= 4 and agree < 1e-5
