@@ -157,10 +157,13 @@ typedef struct {
                                  runs out (no band is updated)                  [0] */
     int fuse_passes;          /* 1: batches of uniform one-cell-thick chains on the
                                  1024 x 1024 warp-transform demag kernels (FFT
-                                 variant 4) run the black pass and the next
-                                 iteration's forward row transforms as one kernel
-                                 per tile of four rows (the rows are final once
-                                 their black cells moved); 0: separate kernels.
+                                 variant 4) run the inverse row transforms with
+                                 the red pass, and the black pass with the next
+                                 iteration's forward row transforms, as one kernel
+                                 per tile of four rows each (a tile's red cells
+                                 can move once its field is known, its rows are
+                                 final once their black cells moved); 0: separate
+                                 kernels.
                                  The same moves either way, up to the last-bit
                                  rounding of separately compiled kernels.       [1] */
 } mmc_options;
@@ -390,10 +393,10 @@ mmc_status mmc_minimize(mmc_ctx *ctx, int chain, int64_t maxit, double tol, int6
  * and returns, per kernel kind, the summed duration in ms (ms) and the number
  * of launches (count).  Kinds: 0 demag rows forward, 1 demag columns, 2 demag
  * rows inverse, 3 sublattice pass, 4 observables, 5 window/adaptation step,
- * 6 black pass fused with the forward rows (mmc_options.fuse_passes; then kind
- * 0 is the forward rows that start each block of iterations and kind 3 the red
- * passes).  Both arrays have 7 entries (HOST). */
-mmc_status mmc_phase_times(mmc_ctx *ctx, int64_t n, uint64_t seed, double ms[7], int64_t count[7]);
+ * 6 black pass fused with the forward rows, 7 inverse rows fused with the red
+ * pass (mmc_options.fuse_passes; kind 0 is then the forward rows that start each
+ * block of iterations).  Both arrays have 8 entries (HOST). */
+mmc_status mmc_phase_times(mmc_ctx *ctx, int64_t n, uint64_t seed, double ms[8], int64_t count[8]);
 
 /* FFT variant of the batch's FP32 2D demag kernels (1 radix 16 with 768-thread
  * blocks, 2 radix 32 with 384-thread blocks, 3 radix 16 with 384-thread blocks,

@@ -857,10 +857,11 @@ void timed(mmc_ctx *c, PhaseTimer *pt, int kind, F fn) {
 }
 
 // the iteration of batches on the warp-transform demag path with uniform
-// one-cell-thick chains fuses the black pass with the next iteration's forward
-// row transforms (k_w32_black_rows_fwd): a block of k iterations is the forward
-// rows of the current state, then k times {columns, inverse rows, red pass,
-// black pass + forward rows}
+// one-cell-thick chains fuses the red pass with the inverse row transforms
+// (k_w32_rows_inv_red) and the black pass with the next iteration's forward row
+// transforms (k_w32_black_rows_fwd): a block of k iterations is the forward rows
+// of the current state, then k times {columns, inverse rows + red pass, black
+// pass + forward rows}
 bool fused_path(const mmc_ctx *c) {
   return c->opt.fuse_passes && c->any_demag && c->cf.empty() && !c->batch_plan.fp64 &&
          c->batch_plan.fft_variant == 4 && c->batch_plan.w32.ok && c->all_flat && !c->any_percell && !c->band &&
@@ -868,8 +869,8 @@ bool fused_path(const mmc_ctx *c) {
 }
 
 // k fused iterations of the chains of plan / blocks [b0, b0 + nb) on L
-void issue_fused(mmc_ctx *c, const Launch &L, const DemagPlan &plan, int b0, int nb, int k, unsigned key0,
-                 unsigned key1, int sample_every, uint64_t start, PhaseTimer *pt) {
+void issue_fused(mmc_ctx *c, const Launch &L, const DemagPlan &plan, int k, unsigned key0, unsigned key1,
+                 int sample_every, uint64_t start, PhaseTimer *pt) {
   const DemagLaunch D = make_demag_launch(c, plan, c->d_heff, nullptr, -1);
   const auto tm = [&](int kind, const std::function<void()> &fn) {
     if (!pt) { fn(); return; }
@@ -883,11 +884,8 @@ void issue_fused(mmc_ctx *c, const Launch &L, const DemagPlan &plan, int b0, int
   tm(0, [&] { launch_w32_stage(L, D, 0); });
   for (int off = 0; off < k; ++off) {
     tm(1, [&] { launch_w32_stage(L, D, 1); });
-    tm(2, [&] { launch_w32_stage(L, D, 2); });
-    SweepLaunch red = sweep_launch(c, 0, (unsigned)off, key0, key1);
-    red.blk_base = b0;
-    red.nblocks = nb;
-    tm(3, [&] { launch_sweep_pass(L, red); });
+    const SweepLaunch red = sweep_launch(c, 0, (unsigned)off, key0, key1);
+    tm(7, [&] { launch_w32_rows_inv_red(L, D, red); });
     const SweepLaunch blk = sweep_launch(c, 1, (unsigned)off, key0, key1);
     tm(6, [&] { launch_w32_black_rows_fwd(L, D, blk); });
     if (sample_every > 0 && (start + off + 1) % (uint64_t)sample_every == 0) {
@@ -907,13 +905,12 @@ void issue_block(mmc_ctx *c, int k, unsigned key0, unsigned key1, int sample_eve
       for (auto &g : c->groups) {
         cudaStreamWaitEvent(g.stream, c->ev_fork, 0);
         Launch Lg{g.stream, &c->launches};
-        const int b0 = (int)c->sw_first[(size_t)g.c0], nb = (int)(c->sw_first[(size_t)g.c1] - b0);
-        issue_fused(c, Lg, g.plan, b0, nb, k, key0, key1, 0, start, nullptr);
+        issue_fused(c, Lg, g.plan, k, key0, key1, 0, start, nullptr);
         cudaEventRecord(g.done, g.stream);
         cudaStreamWaitEvent(c->stream, g.done, 0);
       }
     } else {
-      issue_fused(c, L, c->batch_plan, 0, c->sw_blocks, k, key0, key1, sample_every, start, pt);
+      issue_fused(c, L, c->batch_plan, k, key0, key1, sample_every, start, pt);
     }
     const int adapt_now = ((start + k) % 100 == 0) ? 1 : 0;
     Trace t("advance");
@@ -2239,10 +2236,10 @@ mmc_status mmc_minimize(mmc_ctx *c, int chain, int64_t maxit, double tol, int64_
   return MMC_OK;
 }
 
-mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[7], int64_t count[7]) {
+mmc_status mmc_phase_times(mmc_ctx *c, int64_t n, uint64_t seed, double ms[8], int64_t count[8]) {
   if (!c || !ms || !count) return fail(MMC_ERR_ARG, "null argument");
   if (n < 0) return fail(MMC_ERR_ARG, "negative sweep count");
-  for (int k = 0; k < 7; ++k) { ms[k] = 0; count[k] = 0; }
+  for (int k = 0; k < 8; ++k) { ms[k] = 0; count[k] = 0; }
   const unsigned key0 = (unsigned)(seed & 0xffffffffu), key1 = (unsigned)(seed >> 32);
   PhaseTimer pt;
   mmc_status st = MMC_OK;

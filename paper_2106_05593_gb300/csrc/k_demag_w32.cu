@@ -514,6 +514,198 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_black_rows_fwd(FusedAr
   }
 }
 
+// The inverse row transforms of a tile of four rows fused with the red pass of
+// the same rows: once a tile's field is in shared memory the red cells of its
+// rows can move (their field is final, their black neighbours do not move in
+// this pass).  After the transforms, one thread brings the tile's red rows and
+// the black rows r0 - 1 .. r0 + 4 into the space the transposes used; the block
+// writes h_eff of the black cells (for the fused black pass), then runs the red
+// pass from shared memory with each red cell's field taken from the tile.
+constexpr size_t kFieldTileBytes = 12 * 512 * sizeof(float);
+constexpr size_t kFusedInvSmem = kFieldTileBytes + (size_t)10 * kFusedHx * sizeof(float4);
+static_assert(kFusedInvSmem >= 6 * kW32Buf * sizeof(float2), "the buffers cover the warp buffers");
+static_assert(kFieldTileBytes % 16 == 0, "bulk copy alignment");
+
+__global__ void __launch_bounds__(kFusedThreads, 3) k_w32_rows_inv_red(FusedArgs F) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+  float *ft = reinterpret_cast<float *>(smem_raw);                      // field tile [comp][row][x]
+  float4 *tred = reinterpret_cast<float4 *>(smem_raw + kFieldTileBytes);  // red rows r0 .. r0 + nr - 1
+  float4 *tblk = tred + 4 * kFusedHx;                                     // black rows r0 - 1 .. r0 + nr
+  __shared__ uint64_t bar;
+  __shared__ float4 skv[kChainKVec];
+  __shared__ unsigned wacc[kFusedThreads / 32], watt[kFusedThreads / 32];
+  const W32Args &A = F.W;
+  const int c = A.blk_chain[blockIdx.x];
+  const ChainDev &ch = A.chains[c];
+  const int tile = (int)(blockIdx.x - A.blk_first[c]);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int p = w / 3, q = w - 3 * p;
+  const int nx = ch.nx, ny = ch.ny, hx = ch.hx;
+  const int r0 = 4 * tile, nr = min(4, ny - r0);
+  const long long S = (long long)ch.nrows * hx;
+  if (threadIdx.x < kChainKVec) skv[threadIdx.x] = __ldg(reinterpret_cast<const float4 *>(A.chains + c) + threadIdx.x);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  {
+    constexpr int per = kW32Half * 2;
+    for (int i = threadIdx.x; i < 3 * per; i += blockDim.x) {
+      const int comp = i / per, o = i - comp * per;
+      const float4 t = reinterpret_cast<const float4 *>(A.S + w32_at(ch, comp, 4 * tile, 0))[o];
+      const int kx = o >> 1, r = 2 * (o & 1);
+      sm[(comp * 4 + r) * kW32TilePitch + kx] = make_float2(t.x, t.y);
+      sm[(comp * 4 + r + 1) * kW32TilePitch + kx] = make_float2(t.z, t.w);
+    }
+  }
+  __syncthreads();
+  const int cA = q == 2 ? 2 : 0, cB = q == 2 ? 2 : 1;
+  const int rA = q == 1 ? 2 * p + 1 : 2 * p, rB = q == 0 ? 2 * p : 2 * p + 1;
+  const float2 *ta = sm + (cA * 4 + rA) * kW32TilePitch;
+  const float2 *tb = sm + (cB * 4 + rB) * kW32TilePitch;
+  float2 v[32];
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) {
+    const int k = lane + 32 * k2;
+    if (k2 < 16) {
+      const float2 a = ta[k], b = tb[k];
+      v[k2] = k == 0 ? make_float2(a.x, b.x) : make_float2(a.x - b.y, a.y + b.x);
+    } else {
+      const int km = kW32N - k;
+      const float2 a = ta[km], b = tb[km];
+      v[k2] = km == 512 ? make_float2(a.x, b.x) : make_float2(a.x + b.y, b.x - a.y);
+    }
+  }
+  __syncthreads();
+  w32_inv(v, sm + w * kW32Buf, A.tw, lane);
+  __syncthreads();                                     // transposes done: the space is free
+  if (threadIdx.x == 0) {
+    fence_proxy_async_smem();
+    const bool pby = (ch.pbc & 2) != 0;
+    const int rb = r0 > 0 ? r0 - 1 : (pby ? ny - 1 : -1);
+    const int ra = r0 + nr < ny ? r0 + nr : (pby ? 0 : -1);
+    const unsigned row_b = (unsigned)hx * 16u;
+    const float4 *mred = A.m + ch.m_off, *mblk = A.m + ch.m_off + S;
+    mbar_arrive_expect_tx(&bar, 2u * (unsigned)nr * row_b + (rb >= 0 ? row_b : 0u) + (ra >= 0 ? row_b : 0u));
+    bulk_g2s(tred, mred + (long long)r0 * hx, (unsigned)nr * row_b, &bar);
+    bulk_g2s(tblk + hx, mblk + (long long)r0 * hx, (unsigned)nr * row_b, &bar);
+    if (rb >= 0) bulk_g2s(tblk, mblk + (long long)rb * hx, row_b, &bar);
+    if (ra >= 0) bulk_g2s(tblk + (long long)(nr + 1) * hx, mblk + (long long)ra * hx, row_b, &bar);
+  }
+  const float scale = 1.f / ((float)kW32N * (float)kW32N);
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) {
+    const int x = lane + 32 * n2;
+    ft[(cA * 4 + rA) * 512 + x] = v[n2].x * scale;
+    ft[(cB * 4 + rB) * 512 + x] = v[n2].y * scale;
+  }
+  __syncthreads();
+  const ChainK K = load_chain_vec(skv);
+  const float mu0f = (float)mu0;
+  // h_eff of the black cells, for the fused black pass
+  const unsigned nslots = (unsigned)(nr * hx);
+  for (unsigned qb = threadIdx.x; qb < nslots; qb += blockDim.x) {
+    const int rl = (int)divq(qb, K.hx_m, K.hx_l), sl = (int)(qb - (unsigned)rl * (unsigned)hx);
+    const int x = 2 * sl + ((r0 + rl + 1) & 1);
+    if (x >= nx) continue;
+    const float Hx = ft[(0 * 4 + rl) * 512 + x], Hy = ft[(1 * 4 + rl) * 512 + x], Hz = ft[(2 * 4 + rl) * 512 + x];
+    A.heff[ch.h_off + S + (long long)r0 * hx + qb] = make_float4(
+        ch.zee * (ch.Bx + mu0f * Hx), ch.zee * (ch.By + mu0f * Hy), ch.zee * (ch.Bz + mu0f * Hz), 0.f);
+  }
+  if (!mbar_wait(&bar, 0u, F.max_polls)) {
+    if (threadIdx.x == 0) atomicExch(A.err, -3);      // MMC_ERR_TIMEOUT: the tile's red cells do not move
+    const long long t0 = clock64();
+    while (clock64() - t0 < (1LL << 21)) {
+    }
+    return;
+  }
+  // the red pass (colour 0) on the tile's cells
+  const unsigned sweep = *F.sweep_base + F.sweep_off;
+  const float omc = F.st[c].omc;
+  const int pbc = K.pbc & 3, flags = K.flags;
+  float4 *mredw = F.m + ch.m_off;
+  unsigned na = 0, nv = 0;
+#pragma unroll 1
+  for (int e0 = 0; e0 < 6; e0 += 2) {
+    bool valid[2];
+    unsigned ql[2], cellid[2];
+    float4 a[2], h[2], nb[2][4];
+    float pres[2][4];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const unsigned qq = threadIdx.x + (unsigned)((e0 + e) * kFusedThreads);
+      bool ok = qq < nslots;
+      const int rl = ok ? (int)divq(qq, K.hx_m, K.hx_l) : 0;
+      const int sl = (int)(qq - (unsigned)rl * (unsigned)hx);
+      const int j = r0 + rl;
+      const int pp = j & 1;
+      const int i = 2 * sl + pp;
+      ok = ok && (i < nx);
+      valid[e] = ok;
+      ql[e] = qq;
+      cellid[e] = (unsigned)i + (unsigned)nx * (unsigned)j;
+      if (ok) {
+        a[e] = tred[qq];
+        const float4 *O = tblk + (rl + 1) * hx + sl;
+        const bool hl = i > 0 || (pbc & 1), hr = i < nx - 1 || (pbc & 1);
+        const bool hu = j > 0 || (pbc & 2), hd = j < ny - 1 || (pbc & 2);
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        nb[e][0] = hl ? O[i > 0 ? pp - 1 : hx - 1] : z4;
+        nb[e][1] = hr ? O[i < nx - 1 ? pp : 1 - hx] : z4;
+        nb[e][2] = hu ? O[-hx] : z4;
+        nb[e][3] = hd ? O[hx] : z4;
+        pres[e][0] = hl ? 1.f : 0.f;
+        pres[e][1] = hr ? 1.f : 0.f;
+        pres[e][2] = hu ? 1.f : 0.f;
+        pres[e][3] = hd ? 1.f : 0.f;
+        if (flags & F_GRAIN) {
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (nb[e][b].w != a[e].w) pres[e][b] *= K.gscale;
+        }
+        const float Hx = ft[(0 * 4 + rl) * 512 + i], Hy = ft[(1 * 4 + rl) * 512 + i], Hz = ft[(2 * 4 + rl) * 512 + i];
+        h[e] = make_float4(ch.zee * (ch.Bx + mu0f * Hx), ch.zee * (ch.By + mu0f * Hy), ch.zee * (ch.Bz + mu0f * Hz), 0.f);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      int acc = 0;
+      if (valid[e]) {
+        const float wv[4] = {K.wx * pres[e][0], K.wx * pres[e][1], K.wy * pres[e][2], K.wy * pres[e][3]};
+        const uint4 r = philox4x32_10_rk(make_uint4(cellid[e], sweep, (unsigned)K.chain, 0u), F.rk);
+        const MoveAngles ga = move_angles(K.sigma, omc, uniform01(r.x), uniform01(r.y), uniform01(r.z));
+        const float u3 = uniform01(r.w);
+        Move mv = move_length(a[e], K.me2h, K.me2l);
+        move_direction_g(mv, a[e], ga);
+        const float floc = local_change_flat(mv, a[e], nb[e], wv, pres[e], K.cdx, K.cdy, (flags & F_DMI) != 0,
+                                             h[e].x, h[e].y, h[e].z);
+        const float flong = longitudinal_change(mv, K.p2, K.p4);
+        const float fan = anisotropy_change(mv, flags, K.k1, K.k2, K.ex, K.ey, K.ez);
+        const float dl = floc + flong + fan - 4.f * log1p_move_s(mv.tt, K.sigma);
+        acc = dl + __logf(u3) < 0.f;
+        if (acc) mredw[(long long)r0 * hx + ql[e]] = make_float4(mv.mpx, mv.mpy, mv.mpz, a[e].w);
+      }
+      na += __popc(__ballot_sync(0xffffffffu, acc));
+      nv += __popc(__ballot_sync(0xffffffffu, valid[e]));
+    }
+  }
+  if (lane == 0) {
+    wacc[w] = na;
+    watt[w] = nv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned sa = 0, sv = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < kFusedThreads / 32; ++w2) { sa += wacc[w2]; sv += watt[w2]; }
+    if (sv) {
+      atomicAdd(&F.st[c].win_acc, (unsigned long long)sa);
+      atomicAdd(&F.st[c].win_att, (unsigned long long)sv);
+    }
+  }
+}
+
 constexpr size_t kW32RowsSmem = 6 * kW32Buf * sizeof(float2);
 constexpr size_t kW32ColsSmem = 3 * kW32Buf * sizeof(float2) + 4 * kW32TPitch * sizeof(float);
 static_assert(kW32RowsSmem >= 12 * kW32TilePitch * sizeof(float2), "output tile fits the warp buffers");
@@ -560,6 +752,31 @@ void launch_w32_stage(const Launch &L, const DemagLaunch &P, int stage) {
   ++*L.counter;
 }
 
+static FusedArgs fused_args(const DemagLaunch &P, const SweepLaunch &Q) {
+  FusedArgs F;
+  F.W = w32_args(P);
+  F.m = Q.m;
+  F.st = Q.st;
+  F.heff = Q.heff;
+  F.sweep_base = Q.sweep_base;
+  F.sweep_off = Q.sweep_off;
+  unsigned k0 = Q.key0, k1 = Q.key1;
+  for (int r = 0; r < 10; ++r) {
+    F.rk[2 * r] = k0;
+    F.rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  F.max_polls = Q.max_polls;
+  return F;
+}
+
+void launch_w32_rows_inv_red(const Launch &L, const DemagLaunch &P, const SweepLaunch &Q) {
+  FusedArgs F = fused_args(P, Q);
+  k_w32_rows_inv_red<<<P.rows_blocks, kFusedThreads, kFusedInvSmem, L.stream>>>(F);
+  ++*L.counter;
+}
+
 void launch_w32_black_rows_fwd(const Launch &L, const DemagLaunch &P, const SweepLaunch &Q) {
   FusedArgs F;
   F.W = w32_args(P);
@@ -587,6 +804,8 @@ cudaError_t w32_set_smem() {
   e = cudaFuncSetAttribute(k_w32_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW32RowsSmem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_w32_black_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_w32_rows_inv_red, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedInvSmem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_w32_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kW32ColsSmem);
 }

@@ -279,6 +279,8 @@ void launch_w32(const Launch &L, const DemagLaunch &P);
 void launch_w32_stage(const Launch &L, const DemagLaunch &P, int stage);   // 0 rows fwd, 1 cols, 2 rows inv
 // the black pass fused with the forward row transforms (k_demag_w32.cu)
 void launch_w32_black_rows_fwd(const Launch &L, const DemagLaunch &P, const SweepLaunch &Q);
+// the inverse row transforms fused with the red pass (k_demag_w32.cu)
+void launch_w32_rows_inv_red(const Launch &L, const DemagLaunch &P, const SweepLaunch &Q);
 cudaError_t w32_set_smem();
 // a chain the warp-transform path handles: one cell thick, padded grid 1024 x 1024, open demag
 inline bool w32_chain(const ChainDev &D) {

@@ -314,13 +314,13 @@ class MMC:
 
     def phase_times(self, n, seed):
         """n iterations eagerly with CUDA events around every kernel: returns
-        {kind: (total ms, launches)} for the seven kernel kinds."""
-        ms = np.zeros(7)
-        cnt = np.zeros(7, dtype=np.int64)
+        {kind: (total ms, launches)} for the eight kernel kinds."""
+        ms = np.zeros(8)
+        cnt = np.zeros(8, dtype=np.int64)
         check(load().mmc_phase_times(self._ctx, int(n), int(seed), _dptr(ms),
                                      cnt.ctypes.data_as(C.POINTER(C.c_int64))), "mmc_phase_times")
         kinds = ("demag_rows_fwd", "demag_cols", "demag_rows_inv", "sweep_pass", "observables", "advance",
-                 "black_pass_rows_fwd")
+                 "black_pass_rows_fwd", "rows_inv_red_pass")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(kinds)}
 
     def fft_tuning(self):
