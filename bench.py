@@ -174,7 +174,8 @@ def nvtx_range(name):
 
 
 KERNEL_SOURCES = ("k_sweep.cu", "k_demag.cu", "k_demag_il.cuh", "demag_il.h", "demag_args.cuh", "fft.cuh",
-                  "fft_il.cuh", "trial.cuh", "philox.cuh", "mmc_internal.h", "k_demag_w32.cu", "fft_w32.cuh")
+                  "fft_il.cuh", "trial.cuh", "philox.cuh", "mmc_internal.h", "k_demag_w32.cu", "fft_w32.cuh",
+                  "tma.cuh")
 
 
 def strip_comments(src):
