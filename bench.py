@@ -55,7 +55,9 @@ def parse():
                              "granular", "probe8192"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-demag", action="store_true")
+    ap.add_argument("--fp64-demag", action="store_true", help="demag FFT convolution in FP64")
+    ap.add_argument("--ff-demag", action="store_true",
+                    help="demag FFT convolution in float-float (pairs of FP32 values on the FP32 pipe)")
     ap.add_argument("--fft-variant", type=int, default=0, choices=(0, 1, 2, 3, 4),
                     help="FP32 2D demag kernels: 0 timed pick at create, 1 radix 16, 2 radix 32, "
                          "3 radix 16 two blocks per SM, 4 warp 32x32 transforms (1024-point grids)")
@@ -368,14 +370,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def fp64_demag_compare(MMC, specs, seed, stream, cells_per_step, steps=2):
-    """The FP64-demag form of the workload (demag FFT convolution in FP64, the
-    sweep in FP32): whole-batch rate over `steps` steps, the demag update time,
-    and the largest difference of the Eq. 5 decision values (kT) of one pass of
-    chain 0 between the FP32 and the FP64 convolution on the same state (the FP64
-    convolution equals the oracle's to 1e-9 relative in the parity tests)."""
+def demag_prec(args):
+    """mmc_options.demag_fp64 of the run: 0 FP32, 1 FP64, 2 float-float."""
+    return 2 if args.ff_demag else int(args.fp64_demag)
+
+
+def fp64_demag_compare(MMC, specs, seed, stream, cells_per_step, steps=2, prec=1):
+    """The workload with its demag FFT convolution accumulated at FP64 precision
+    (prec 1: FP64; prec 2: float-float on the FP32 pipe), the sweep in FP32:
+    whole-batch rate over `steps` steps, the demag update time, and the largest
+    difference of the Eq. 5 decision values (kT) of one pass of chain 0 between
+    the FP32 and this convolution on the same state (the FP64 and float-float
+    fields equal the oracle's to 1e-9 and 1e-10 of max |H| in the parity tests)."""
     import torch
-    g64 = MMC(specs, demag=1, demag_fp64=1, stream=stream)
+    g64 = MMC(specs, demag=1, demag_fp64=prec, stream=stream)
     g64.init_random(seed)
     g64.sweep(SWEEPS_PER_STEP, seed)
     torch.cuda.synchronize()
@@ -391,7 +399,7 @@ def fp64_demag_compare(MMC, specs, seed, stream, cells_per_step, steps=2):
     upd = sum(ph[k][0] for k in ("demag_rows_fwd", "demag_cols", "demag_rows_inv")) / max(ph["demag_cols"][1], 1)
     m4 = g64.get_m(0)
     g32 = MMC(specs[:1], demag=1, stream=stream)
-    g1 = MMC(specs[:1], demag=1, demag_fp64=1, stream=stream)
+    g1 = MMC(specs[:1], demag=1, demag_fp64=prec, stream=stream)
     dd = 0.0
     for color in (0, 1):
         decs = []
@@ -400,19 +408,20 @@ def fp64_demag_compare(MMC, specs, seed, stream, cells_per_step, steps=2):
             decs.append(gg.pass_debug(0, color, 7, seed, 20.0)[0])
         dd = max(dd, float(np.abs(decs[0].astype(np.float64) - decs[1]).max()))
     return {"value": cells_per_step * steps / (ms * 1e-3), "unit": UNIT, "steps": steps,
-            "demag_update_ms": upd, "decision_value_max_diff_fp32_vs_fp64_kT": dd}
+            "demag_update_ms": upd,
+            "decision_value_max_diff_fp32_vs_%s_kT" % ("fp64" if prec == 1 else "float_float"): dd}
 
 
 def batched_plain_identity(MMC, specs, demag, args, variant, seed, stream, iters=100):
     """Batched and plain forms at equal accuracy: one-chain contexts given
     chain_base = k run chain k's Markov chain; after `iters` iterations from the
     same random start every chain's state equals the batch's bit for bit."""
-    b = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=variant, stream=stream)
+    b = MMC(specs, demag=int(demag), demag_fp64=demag_prec(args), fft_variant=variant, stream=stream)
     b.init_random(seed)
     b.sweep(iters, seed)
     same = 0
     for k, sp in enumerate(specs):
-        p = MMC([sp], demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=variant, chain_base=k,
+        p = MMC([sp], demag=int(demag), demag_fp64=demag_prec(args), fft_variant=variant, chain_base=k,
                 stream=stream)
         p.init_random(seed)
         p.sweep(iters, seed)
@@ -441,7 +450,7 @@ def run_ours(args):
     percell = args.workload == "granular"
     stream = torch.cuda.Stream()
     if args.profile_run > 0:
-        gp = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), use_graphs=0,
+        gp = MMC(specs, demag=int(demag), demag_fp64=demag_prec(args), use_graphs=0,
                  fft_variant=args.fft_variant, sweep_tiles=args.sweep_tiles, stream_groups=args.stream_groups,
                  fuse_passes=args.fuse_passes, stream=stream)
         gp.init_random(replica_seed(rank))
@@ -449,7 +458,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         print("profile run ok", gp.launches, flush=True)
         return
-    g = MMC(specs, demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=args.fft_variant,
+    g = MMC(specs, demag=int(demag), demag_fp64=demag_prec(args), fft_variant=args.fft_variant,
             stream_groups=args.stream_groups, sweep_tiles=args.sweep_tiles, fuse_passes=args.fuse_passes,
             stream=stream)
     seed = replica_seed(rank)
@@ -509,7 +518,8 @@ def run_ours(args):
             best = kind
     tms, cnt = phases[best]
     avg_s = tms / cnt * 1e-3
-    spec_b = spectrum_bytes_per_cell(specs)
+    # FP64 and float-float spectra hold 16 B per complex value, FP32 8 B
+    spec_b = spectrum_bytes_per_cell(specs) * (2.0 if demag_prec(args) else 1.0)
     bytes_per_launch = algorithmic_bytes(best, demag, percell, spec_b) * ncell
     achieved = bytes_per_launch / avg_s / 1e9
     src = kernel_source_hash()
@@ -541,16 +551,18 @@ def run_ours(args):
         if demag:
             kinds = ("demag_rows_fwd", "demag_cols", "demag_rows_inv")
             own = sum(ph_unfused[k][0] for k in kinds) / max(ph_unfused["demag_cols"][1], 1)
-            cf = MMC(specs, demag=1, demag_cufft=1, demag_fp64=int(args.fp64_demag), stream=stream)
+            cf = MMC(specs, demag=1, demag_cufft=1, demag_fp64=demag_prec(args), stream=stream)
             cf.init_random(seed)
             ph = cf.phase_times(20, seed)
             # one demag update per iteration; the cuFFT path records one mark per
             # padded-size group, so divide by the updates, not by the marks
             cfm = sum(ph[k][0] for k in kinds) / 20.0
             compare["demag_update_ms"] = {"own": own, "cufft": cfm}
-            if not args.fp64_demag:
+            if not demag_prec(args):
                 compare["fp64_demag"] = fp64_demag_compare(MMC, specs, seed, stream, cells_per_step)
                 compare["demag_update_ms"]["own_fp64"] = compare["fp64_demag"]["demag_update_ms"]
+                compare["ff_demag"] = fp64_demag_compare(MMC, specs, seed, stream, cells_per_step, prec=2)
+                compare["demag_update_ms"]["own_float_float"] = compare["ff_demag"]["demag_update_ms"]
             v, tms = g.fft_tuning()
             tu = g.tuning()
             compare["autotune"] = {"stream_groups": tu["stream_groups"], "from_cache": tu["from_cache"],
@@ -561,7 +573,7 @@ def run_ours(args):
                                                          "radix16x2": tms[2], "warp32x32": tms[3]}}
             del cf
         if len(specs) > 1:
-            plain = [MMC([sp], demag=int(demag), demag_fp64=int(args.fp64_demag), fft_variant=args.fft_variant,
+            plain = [MMC([sp], demag=int(demag), demag_fp64=demag_prec(args), fft_variant=args.fft_variant,
                          stream=stream) for sp in specs]
             for k, p1 in enumerate(plain):
                 p1.set_m(g.get_m(k))
@@ -618,7 +630,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (demag FFT f64)" if args.fp64_demag else "f32",
+            "dtype": {0: "f32", 1: "f32 (demag FFT f64)", 2: "f32 (demag FFT float-float)"}[demag_prec(args)],
             "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "cells": ncell,
                        "sweeps_per_step": sweeps_per_step, "demag": "once per iteration" if demag else "off",

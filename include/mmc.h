@@ -99,7 +99,10 @@ typedef struct {
 typedef struct {
     int demag;                /* 1: include the demag interaction (Eq. 14)          [0] */
     int demag_per_pass;       /* 1: recompute H_d before each sublattice pass       [0] */
-    int demag_fp64;           /* 1: FP64 FFT convolution; 0: FP32 (own kernels)     [0] */
+    int demag_fp64;           /* precision of the sweep's FFT convolution:          [0]
+                                 0 FP32; 1 FP64; 2 float-float (pairs of FP32 values,
+                                 ~48-bit significands, on the FP32 pipe).  Energies
+                                 and mmc_demag_field always use FP64. */
     int demag_cufft;          /* 1: cuFFT R2C/C2R transforms (comparison path) for the
                                  sweep's demag field instead of the own kernels [0] */
     int adapt;                /* 1: adapt the cone angle every 100 sweeps (Sec. II) [1] */

@@ -120,6 +120,7 @@ struct DemagPlan {
   IlTables small;                       // FP32 variant 3: E = 6144 (2 blocks per SM)
   IlTables w32;                         // FP32 variant 4: warp transforms, 1024 x 1024 grids only
   bool fp64 = false;
+  bool ff = false;                      // fp64 plan run by the float-float 2D kernels
   ChainDev *d_ch = nullptr;             // chain table the plan indexes
   int *rows_chain = nullptr;
   long long *rows_first = nullptr;
@@ -166,10 +167,13 @@ struct mmc_ctx {
   unsigned *d_sweep_base = nullptr, *d_dbg_sweep = nullptr;
   float4 *d_m = nullptr, *d_heff = nullptr, *d_tab = nullptr;
   float *d_ms = nullptr;
+  float *d_ms_lo = nullptr;             // per-cell Ms0 minus its FP32 value (FP64 and float-float demag)
   long long m_total = 0, tab_total = 0, ms_total = 0;
   std::vector<SpecSet> specs;
   void **d_nhat32 = nullptr, **d_nhat64 = nullptr, **d_nhat32t = nullptr;
   void *d_tw32 = nullptr, *d_tw64 = nullptr, *d_tw1024 = nullptr;
+  void **d_nhatff = nullptr;            // float-float tensor spectra (demag_fp64 = 2)
+  void *d_twff = nullptr;               // float-float twiddle table
   int *d_sw_chain = nullptr;
   long long *d_sw_first = nullptr;
   int2 *d_sw_desc = nullptr;
@@ -492,7 +496,7 @@ inline long long split_index(const ChainDev &D, int i, int row) {
 
 // per-cell tables of a chain in the split layout: 3 float4 arrays of 2 S entries
 // ({p2, p4, m_e^2, sigma}, {zee, k1, k2, T_ref / T}, {e_A}) and Ms0 per cell
-void fill_percell_tables(const ChainHost &H, const ChainDev &D, float4 *tab, float *ms) {
+void fill_percell_tables(const ChainHost &H, const ChainDev &D, float4 *tab, float *ms, float *ms_lo) {
   const long long S = H.slots;
   for (int row = 0; row < D.nrows; ++row)
     for (int i = 0; i < D.nx; ++i) {
@@ -507,6 +511,7 @@ void fill_percell_tables(const ChainHost &H, const ChainDev &D, float4 *tab, flo
       // m_e^2 as a float-float pair (high part in the first table, low part here)
       tab[4 * S + si] = make_float4((float)et[6], (float)et[7], (float)et[8], (float)(et[2] - (double)(float)et[2]));
       ms[si] = (float)et[3];
+      ms_lo[si] = (float)(et[3] - (double)ms[si]);
     }
 }
 
@@ -580,7 +585,10 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
   // 3 sequences per row pair (np = E / (3 Px)) or 3 components per column
   // (CC = E / (3 Py))
   const int E = il_elements(fp64);
-  bool il = true;
+  // float-float convolution of the sweep's field (energies keep FP64 single-chain
+  // plans): always the generic kernels
+  const bool ffp = fp64 && !single && c->opt.demag_fp64 == 2 && c->d_nhatff != nullptr;
+  bool il = !ffp;
   for (const ChainDev &D : table)
     if (D.Pz != 1 || 3 * D.Px > E || 3 * D.Py > E) il = false;
   std::vector<int> rc, colc;
@@ -649,6 +657,7 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
   P.cols_cc = cc;
   P.cols_smem = csmem;
   P.fp64 = fp64;
+  P.ff = ffp;
   if (il && !fp64) MMC_TRY(build_il_tables(c, P.small, table, ids, nid, il_elements_small(), false));
   if (il && !fp64 && !single) {
     // warp-transform path: every chain on a 1024 x 1024 padded grid; one row block
@@ -697,9 +706,12 @@ DemagLaunch make_demag_launch(mmc_ctx *c, const DemagPlan &P, float4 *heff, doub
   D.m = c->d_m;
   D.tab = c->d_tab;
   D.ms = c->d_ms;
+  D.ms_lo = c->d_ms_lo;
   D.spec = P.spec;
-  D.nhat = P.fp64 ? (const void *const *)c->d_nhat64 : (const void *const *)c->d_nhat32;
-  D.twiddle = P.fp64 ? c->d_tw64 : c->d_tw32;
+  D.nhat = P.ff ? (const void *const *)c->d_nhatff
+           : P.fp64 ? (const void *const *)c->d_nhat64 : (const void *const *)c->d_nhat32;
+  D.twiddle = P.ff ? c->d_twff : P.fp64 ? c->d_tw64 : c->d_tw32;
+  D.ff = P.ff;
   D.heff = heff;
   D.Hd = Hd;
   D.Hd_chain = Hd_chain;
@@ -1264,6 +1276,7 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
   if (!(o.sigma_cap > 0 && o.sigma_cap < 1)) return fail(MMC_ERR_ARG, "sigma_cap must be in (0, 1)");
   if (!(o.theta0_deg >= 1 && o.theta0_deg <= 180)) return fail(MMC_ERR_ARG, "theta0_deg must be in [1, 180]");
   if (o.demag_stripes < 0 || o.demag_stripes > 64) return fail(MMC_ERR_ARG, "demag_stripes must be in [0, 64]");
+  if (o.demag_fp64 < 0 || o.demag_fp64 > 2) return fail(MMC_ERR_ARG, "demag_fp64 must be 0, 1 or 2");
   if (o.chain_base < 0 || (long long)o.chain_base + nchains > 2147483647LL)
     return fail(MMC_ERR_ARG, "chain_base must be >= 0 with chain_base + nchains < 2^31");
   for (int i = 0; i < nchains; ++i) MMC_TRY(validate(chains[i], o, i));
@@ -1372,7 +1385,7 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
   {
     std::vector<float4> m((size_t)moff, make_float4(0, 0, 0, 0));
     std::vector<float4> tab((size_t)std::max(toff, 1LL), make_float4(0, 0, 0, 0));
-    std::vector<float> ms((size_t)std::max(msoff, 1LL), 0.f);
+    std::vector<float> ms((size_t)std::max(msoff, 1LL), 0.f), ms_lo(ms.size(), 0.f);
     std::vector<double> etab_all;
     for (int ci = 0; ci < nchains; ++ci) {
       const ChainDev &D = c->ch[ci];
@@ -1385,19 +1398,31 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
           const float g = H.grain.empty() ? 0.f : H.grain[(size_t)nat];
           m[(size_t)(D.m_off + si)] = make_float4(H.init_len[(size_t)nat], 0.f, 0.f, g);
         }
-      if (H.percell) fill_percell_tables(H, D, tab.data() + D.t_off, ms.data() + D.ms_off);
+      if (H.percell) fill_percell_tables(H, D, tab.data() + D.t_off, ms.data() + D.ms_off, ms_lo.data() + D.ms_off);
     }
     MMC_TRY_OR(upload(c, &c->d_m, m));
     if (toff) MMC_TRY_OR(upload(c, &c->d_tab, tab));
     if (msoff) MMC_TRY_OR(upload(c, &c->d_ms, ms));
+    if (msoff) MMC_TRY_OR(upload(c, &c->d_ms_lo, ms_lo));
     if (o.demag) MMC_TRY_OR(dalloc_t(c, &c->d_heff, (size_t)moff));
   }
   // tensor spectra and twiddles
   if (o.demag) {
-    std::vector<void *> p32, p64, p32t;
+    std::vector<void *> p32, p64, p32t, pff;
     for (auto &ss : c->specs) {
       std::vector<double> sp;
       demag_spectra(ss.h, ss.Px, ss.Py, ss.Pz, sp, ss.pd);
+      if (o.demag_fp64 == 2) {
+        // float-float copy: each FP64 value as its leading FP32 part and the rounded rest
+        std::vector<float2> f(sp.size());
+        for (size_t k = 0; k < sp.size(); ++k) {
+          f[k].x = (float)sp[k];
+          f[k].y = (float)(sp[k] - (double)f[k].x);
+        }
+        float2 *d = nullptr;
+        MMC_TRY_OR(upload(c, &d, f));
+        pff.push_back(d);
+      }
       std::vector<float> spf(sp.begin(), sp.end());
       float *d32 = nullptr;
       double *d64 = nullptr;
@@ -1424,6 +1449,22 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     }
     MMC_TRY_OR(upload(c, &c->d_nhat32, p32));
     MMC_TRY_OR(upload(c, &c->d_nhat64, p64));
+    if (o.demag_fp64 == 2) {
+      auto split = [](double v, float &hi, float &lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+      };
+      MMC_TRY_OR(upload(c, &c->d_nhatff, pff));
+      std::vector<float4> twf(kMaxFFT);
+      for (int t = 0; t < kMaxFFT; ++t) {
+        const double a = -2.0 * kPi * t / kMaxFFT;
+        split(std::cos(a), twf[t].x, twf[t].y);
+        split(std::sin(a), twf[t].z, twf[t].w);
+      }
+      float4 *d = nullptr;
+      MMC_TRY_OR(upload(c, &d, twf));
+      c->d_twff = d;
+    }
     MMC_TRY_OR(upload(c, &c->d_nhat32t, p32t));
     {
       // 32 x 32 twiddles of the warp transforms: entry k1 * 32 + t = exp(-2 pi i t k1 / 1024)
@@ -1736,12 +1777,14 @@ mmc_status mmc_set_temperature(mmc_ctx *c, int chain, double T, const double *T_
     apply_temperature(H, D, c->opt, T, T_cell);
     if (H.percell) {
       std::vector<float4> tab((size_t)(6 * H.slots));
-      std::vector<float> ms((size_t)(2 * H.slots));
-      fill_percell_tables(H, D, tab.data(), ms.data());
+      std::vector<float> ms((size_t)(2 * H.slots)), ms_lo(ms.size());
+      fill_percell_tables(H, D, tab.data(), ms.data(), ms_lo.data());
       CUDA_TRY(cudaMemcpyAsync(c->d_tab + D.t_off, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice,
                                c->stream));
       CUDA_TRY(cudaMemcpyAsync(c->d_ms + D.ms_off, ms.data(), ms.size() * sizeof(float), cudaMemcpyHostToDevice,
                                c->stream));
+      CUDA_TRY(cudaMemcpyAsync(c->d_ms_lo + D.ms_off, ms_lo.data(), ms_lo.size() * sizeof(float),
+                               cudaMemcpyHostToDevice, c->stream));
       CUDA_TRY(cudaStreamSynchronize(c->stream));   // the host vectors go out of scope
     }
     CUDA_TRY(cudaMemcpyAsync(c->d_ch + i, &D, sizeof(ChainDev), cudaMemcpyHostToDevice, c->stream));

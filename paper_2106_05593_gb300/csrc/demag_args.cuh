@@ -17,6 +17,7 @@ struct DemagArgs {
   const float4 *m;
   const float4 *tab;
   const float *ms;
+  const float *ms_lo;   // per-cell Ms0 minus its FP32 value (FP64 and float-float convolutions)
   C *S;
   const R *const *nhat;
   const C *tw;
@@ -35,14 +36,17 @@ __device__ __forceinline__ int pairs_per_block(int Px) {
 
 // M = Ms0 m of cell (x, row r) from the split layout, formed in the convolution's precision
 template <typename R>
-__device__ __forceinline__ void load_M(const ChainDev &ch, const float4 *m, const float *ms, int r, int x,
-                                       R &Mx, R &My, R &Mz) {
+__device__ __forceinline__ void load_M(const ChainDev &ch, const float4 *m, const float *ms, const float *ms_lo,
+                                       int r, int x, R &Mx, R &My, R &Mz) {
   const int k = (int)divq((unsigned)r, ch.ny_m, ch.ny_l), j = r - k * ch.ny;
   const int col = (x + j + k) & 1;
   const long long S = (long long)ch.nrows * ch.hx;
   const long long idx = (long long)col * S + (long long)r * ch.hx + (x >> 1);
   const float4 v = m[ch.m_off + idx];
-  const R Ms = ch.ms_off >= 0 ? (R)ms[ch.ms_off + idx] : (R)ch.Ms0d;
+  R Ms = ch.ms_off >= 0 ? (R)ms[ch.ms_off + idx] : (R)ch.Ms0d;
+  // the wider formats take per-cell Ms0 as the pair (FP32 value, rest)
+  if constexpr (sizeof(R) == 8)
+    if (ch.ms_off >= 0 && ms_lo) Ms = Ms + (R)ms_lo[ch.ms_off + idx];
   Mx = Ms * (R)v.x;
   My = Ms * (R)v.y;
   Mz = Ms * (R)v.z;

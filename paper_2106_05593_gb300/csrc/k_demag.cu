@@ -19,10 +19,15 @@
 //            crop to nx, scale by 1/(Px Py Pz), and write the sweep's static
 //            field h_eff = zee (B + mu0 H_d) in the split layout, optionally
 //            also H_d in FP64, natural order.
-// The FFTs are the shared-memory Stockham transforms of fft.cuh; R = float or
-// double selects the arithmetic of the whole convolution.
+// The FFTs are the shared-memory Stockham transforms of fft.cuh; R = float,
+// double or ff (float-float, ff.cuh) selects the arithmetic of the whole
+// convolution.  The float-float convolution always takes these kernels, also
+// for 2D chains.
+#include <type_traits>
+
 #include "demag_args.cuh"
 #include "demag_il.h"
+#include "ff.cuh"
 #include "fft_il.cuh"
 
 namespace mmc {
@@ -52,8 +57,8 @@ __global__ void k_rows_fwd(DemagArgs<R> A) {
           M1x = Ms * v1[0]; M1y = Ms * v1[1]; M1z = Ms * v1[2];
         }
       } else {
-        load_M<R>(ch, A.m, A.ms, r0, x, M0x, M0y, M0z);
-        if (r1 < nrows) load_M<R>(ch, A.m, A.ms, r1, x, M1x, M1y, M1z);
+        load_M<R>(ch, A.m, A.ms, A.ms_lo, r0, x, M0x, M0y, M0z);
+        if (r1 < nrows) load_M<R>(ch, A.m, A.ms, A.ms_lo, r1, x, M1x, M1y, M1z);
       }
     }
     C z;
@@ -252,19 +257,21 @@ template <typename R>
 void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
   using C = typename Cx<R>::T;
   DemagArgs<R> A;
-  A.chains = P.chains; A.m = P.m; A.tab = P.tab; A.ms = P.ms;
+  A.chains = P.chains; A.m = P.m; A.tab = P.tab; A.ms = P.ms; A.ms_lo = P.ms_lo;
   A.S = reinterpret_cast<C *>(P.spec);
   A.nhat = reinterpret_cast<const R *const *>(P.nhat);
   A.tw = reinterpret_cast<const C *>(P.twiddle);
   A.heff = P.heff; A.Hd = P.Hd; A.Hd_chain = P.Hd_chain;
   A.m_nat = reinterpret_cast<const R *>(P.m_nat);
   A.Ms_override = (R)P.Ms_override;
-  if (P.il2d) {
-    if constexpr (sizeof(R) == 8) launch_il<CfgD16>(L, P, A);
-    else if (P.fft_variant == 2) launch_il<CfgF32>(L, P, A);
-    else if (P.fft_variant == 3) launch_il<CfgF16h>(L, P, A);
-    else launch_il<CfgF16>(L, P, A);
-    return;
+  if constexpr (!std::is_same<R, ff>::value) {
+    if (P.il2d) {
+      if constexpr (sizeof(R) == 8) launch_il<CfgD16>(L, P, A);
+      else if (P.fft_variant == 2) launch_il<CfgF32>(L, P, A);
+      else if (P.fft_variant == 3) launch_il<CfgF16h>(L, P, A);
+      else launch_il<CfgF16>(L, P, A);
+      return;
+    }
   }
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
   if (P.ev) cudaEventRecord(P.ev[0], L.stream);
@@ -280,7 +287,8 @@ void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
 }
 
 void launch_demag(const Launch &L, const DemagLaunch &P, bool fp64) {
-  if (fp64) launch_demag_impl<double>(L, P);
+  if (fp64 && P.ff) launch_demag_impl<ff>(L, P);
+  else if (fp64) launch_demag_impl<double>(L, P);
   else if (P.w32) launch_w32(L, P);
   else launch_demag_impl<float>(L, P);
 }
@@ -299,6 +307,12 @@ cudaError_t demag_set_smem_limits() {
   e = cudaFuncSetAttribute(k_rows_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_rows_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_rows_fwd<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_cols<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_rows_inv<ff>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (e != cudaSuccess) return e;
   const int lil = 200 * 1024;
   if ((e = il_set_smem<CfgF16>(lil)) != cudaSuccess) return e;

@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagA
           M1x = Ms * v1[0]; M1y = Ms * v1[1]; M1z = Ms * v1[2];
         }
       } else {
-        load_M<R>(ch, A.m, A.ms, r0, x, M0x, M0y, M0z);
-        if (r1 < ny) load_M<R>(ch, A.m, A.ms, r1, x, M1x, M1y, M1z);
+        load_M<R>(ch, A.m, A.ms, A.ms_lo, r0, x, M0x, M0y, M0z);
+        if (r1 < ny) load_M<R>(ch, A.m, A.ms, A.ms_lo, r1, x, M1x, M1y, M1z);
       }
     }
     C z;

@@ -249,6 +249,7 @@ struct DemagLaunch {
   const float4 *m;
   const float4 *tab;
   const float *ms;
+  const float *ms_lo;           // per-cell Ms0 minus its FP32 value (or null)
   void *spec;
   const void *const *nhat;
   const void *twiddle;
@@ -273,6 +274,8 @@ struct DemagLaunch {
   const void *const *nhatT;     // their tensor spectra, per set [comp][kx][kyq] (or null), kyq pitch kW32TensorPitch
   const void *tw1024;           // their 32 x 32 twiddle table
   int *err;                     // device error word of bounded waits
+  bool ff;                      // with fp64: float-float arithmetic in the generic kernels (nhat and
+                                // twiddle tables in float-float, the spectrum as pairs of float pairs)
 };
 constexpr int kW32TensorPitch = 516;   // kyq = 0..512 padded to a 16-byte multiple of floats
 void launch_w32(const Launch &L, const DemagLaunch &P);
