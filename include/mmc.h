@@ -252,6 +252,16 @@ mmc_status mmc_set_temperature(mmc_ctx *ctx, int chain, double T, const double *
 mmc_status mmc_set_m(mmc_ctx *ctx, int chain, const float *src, int is_device);
 mmc_status mmc_get_m(mmc_ctx *ctx, int chain, float *dst, int is_device);
 
+/* The same for every chain of the batch in one call (the batched form of
+ * Sec. II's parallel algorithm: one copy and one check instead of one per
+ * chain): src/dst hold chain 0's cells in natural order, then chain 1's, and so
+ * on (sum of the chains' cells x 4 floats).  mmc_set_m_all rejects the whole
+ * batch if any value is non-finite (MMC_ERR_NONFINITE, no chain changed).  The
+ * first call allocates a device buffer of that size (MMC_ERR_NOMEM if it
+ * cannot); the caller's buffer is no longer used when the call returns. */
+mmc_status mmc_set_m_all(mmc_ctx *ctx, const float *src, int is_device);
+mmc_status mmc_get_m_all(mmc_ctx *ctx, float *dst, int is_device);
+
 /* Random initial directions from Philox counter (cell, 0, chain, 1), key seed:
  * z = 2 u0 - 1, phi = 2 pi u1, length len (len <= 0: m_e, or the Eq. 7 rms
  * length where m_e = 0). */
@@ -311,6 +321,12 @@ mmc_status mmc_pass_debug(mmc_ctx *ctx, int chain, int color, uint32_t sweep, ui
 /* Observables of one chain (see mmc_obs); reset != 0 clears the snapshot
  * accumulators after reading them. */
 mmc_status mmc_observables(mmc_ctx *ctx, int chain, mmc_obs *out, int reset);
+
+/* Observables of every chain in one device round trip: out[k] (k < nchains,
+ * HOST array) receives what mmc_observables(ctx, k, &out[k], reset) would, each
+ * out[k].hist optional as there; reset != 0 clears the snapshot accumulators
+ * of every chain.  MMC_ERR_TIMEOUT as for mmc_observables (out not filled). */
+mmc_status mmc_observables_all(mmc_ctx *ctx, mmc_obs *out, int reset);
 
 /* Angular-deviation histogram of one chain's current state (Sec. II, Fig. 1d-f):
  * the polar angle of every cell to the chain's mean direction, counted in `bins`

@@ -18,7 +18,7 @@ STATUS = {0: "MMC_OK", -1: "MMC_ERR_ARG", -2: "MMC_ERR_CUDA", -3: "MMC_ERR_TIMEO
 # every function declared in include/mmc.h
 EXPORTS = [
     "mmc_default_options", "mmc_create", "mmc_create_single", "mmc_destroy", "mmc_set_field",
-    "mmc_set_m", "mmc_get_m", "mmc_init_random", "mmc_sweep", "mmc_sweep_sampled",
+    "mmc_set_m", "mmc_get_m", "mmc_set_m_all", "mmc_get_m_all", "mmc_observables_all", "mmc_init_random", "mmc_sweep", "mmc_sweep_sampled",
     "mmc_demag_update", "mmc_pass_debug", "mmc_observables", "mmc_energy", "mmc_demag_field",
     "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_fft_tuning", "mmc_tuning", "mmc_sweep_field", "mmc_sweep_serial", "mmc_minimize", "mmc_set_temperature", "mmc_angle_hist", "mmc_trial_terms", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell", "mmc_demag_kernel", "mmc_thermo",
     "mmc_checkpoint", "mmc_restore", "mmc_observables_noalloc", "mmc_status_str", "mmc_last_error",
@@ -98,6 +98,10 @@ def load():
     L.mmc_set_m.argtypes = [vp, C.c_int, vp, C.c_int]
     L.mmc_get_m.restype = st
     L.mmc_get_m.argtypes = [vp, C.c_int, vp, C.c_int]
+    L.mmc_set_m_all.restype = st
+    L.mmc_set_m_all.argtypes = [vp, vp, C.c_int]
+    L.mmc_get_m_all.restype = st
+    L.mmc_get_m_all.argtypes = [vp, vp, C.c_int]
     L.mmc_init_random.restype = st
     L.mmc_init_random.argtypes = [vp, C.c_uint64, C.c_double]
     L.mmc_sweep.restype = st
@@ -110,6 +114,8 @@ def load():
     L.mmc_pass_debug.argtypes = [vp, C.c_int, C.c_int, C.c_uint32, C.c_uint64, C.c_double, vp, vp]
     L.mmc_observables.restype = st
     L.mmc_observables.argtypes = [vp, C.c_int, C.POINTER(Obs), C.c_int]
+    L.mmc_observables_all.restype = st
+    L.mmc_observables_all.argtypes = [vp, C.POINTER(Obs), C.c_int]
     L.mmc_energy.restype = st
     L.mmc_energy.argtypes = [vp, C.c_int, dp]
     L.mmc_demag_field.restype = st

@@ -215,6 +215,7 @@ struct mmc_ctx {
   double *d_g8 = nullptr;
   double *d_Hd = nullptr, *d_eout = nullptr, *d_etab = nullptr;
   float4 *d_nat = nullptr;
+  float4 *d_nat_all = nullptr;          // every chain in natural order (mmc_set_m_all / get_m_all)
   float *d_dec = nullptr;
   signed char *d_acc = nullptr;
   long long max_ncell = 0, max_slots = 0;
@@ -1841,6 +1842,62 @@ mmc_status mmc_get_m(mmc_ctx *c, int chain, float *dst, int is_device) {
   return MMC_OK;
 }
 
+// the natural-order buffer of the whole batch, allocated on first use
+static mmc_status nat_all(mmc_ctx *c, long long *n) {
+  long long tot = 0;
+  for (int k = 0; k < c->nchains; ++k) tot += c->hc[k].ncell;
+  if (!c->d_nat_all) MMC_TRY(dalloc_t(c, &c->d_nat_all, (size_t)tot));
+  *n = tot;
+  return MMC_OK;
+}
+
+mmc_status mmc_set_m_all(mmc_ctx *c, const float *src, int is_device) {
+  Trace trace("mmc_set_m_all");
+  if (!c) return fail(MMC_ERR_ARG, "null context");
+  if (!src) return fail(MMC_ERR_ARG, "null source");
+  long long n = 0;
+  MMC_TRY(nat_all(c, &n));
+  if (!c->d_flag) MMC_TRY(dalloc_t(c, &c->d_flag, 1));
+  CUDA_TRY(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->stream));
+  CUDA_TRY(cudaMemcpyAsync(c->d_nat_all, src, (size_t)n * sizeof(float4),
+                           is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  Launch L = c->L();
+  launch_check_finite(L, c->d_nat_all, n, c->d_flag);
+  MMC_TRY(check_launch());
+  int bad = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bad, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (bad) return fail(MMC_ERR_NONFINITE, "non-finite value in m");
+  long long off = 0;
+  for (int k = 0; k < c->nchains; ++k) {
+    launch_pack(L, c->d_ch, k, c->hc[k].slots, c->d_m, c->d_nat_all + off, 1);
+    off += c->hc[k].ncell;
+  }
+  MMC_TRY(check_launch());
+  c->heff_stale = true;
+  c->obs_fresh = false;
+  return MMC_OK;
+}
+
+mmc_status mmc_get_m_all(mmc_ctx *c, float *dst, int is_device) {
+  Trace trace("mmc_get_m_all");
+  if (!c) return fail(MMC_ERR_ARG, "null context");
+  if (!dst) return fail(MMC_ERR_ARG, "null destination");
+  long long n = 0;
+  MMC_TRY(nat_all(c, &n));
+  Launch L = c->L();
+  long long off = 0;
+  for (int k = 0; k < c->nchains; ++k) {
+    launch_pack(L, c->d_ch, k, c->hc[k].slots, c->d_m, c->d_nat_all + off, 0);
+    off += c->hc[k].ncell;
+  }
+  MMC_TRY(check_launch());
+  CUDA_TRY(cudaMemcpyAsync(dst, c->d_nat_all, (size_t)n * sizeof(float4),
+                           is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MMC_OK;
+}
+
 mmc_status mmc_init_random(mmc_ctx *c, uint64_t seed, double len) {
   if (!c) return fail(MMC_ERR_ARG, "null context");
   Launch L = c->L();
@@ -2006,6 +2063,77 @@ mmc_status mmc_observables(mmc_ctx *c, int chain, mmc_obs *out, int reset) {
     z.nsamples = z.nsnap = z.nonfinite = 0;
     CUDA_TRY(cudaMemcpyAsync(c->d_st + chain, &z, sizeof(ChainState), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaMemsetAsync(c->d_hist_acc + (size_t)chain * nb, 0, nb * sizeof(unsigned long long), c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  return MMC_OK;
+}
+
+mmc_status mmc_observables_all(mmc_ctx *c, mmc_obs *out, int reset) {
+  Trace trace("mmc_observables_all");
+  if (!c) return fail(MMC_ERR_ARG, "null context");
+  if (!out) return fail(MMC_ERR_ARG, "null output");
+  const int nc = c->nchains, nb = c->opt.hist_bins + 1;
+  // the current-state reduction of every chain (cheap next to a sweep block),
+  // then everything back in one round trip
+  if (!c->obs_fresh) {
+    CUDA_TRY(cudaMemsetAsync(c->d_hist_cur, 0, (size_t)nc * nb * sizeof(unsigned long long), c->stream));
+    Launch L = c->L();
+    launch_obs(L, obs_launch(c, 0));
+    MMC_TRY(check_launch());
+    c->obs_fresh = true;
+  }
+  std::vector<ChainState> st((size_t)nc);
+  std::vector<double> o((size_t)8 * nc);
+  std::vector<unsigned long long> hc((size_t)nc * nb), ha((size_t)nc * nb);
+  int err = 0;
+  if (c->d_err) CUDA_TRY(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(st.data(), c->d_st, st.size() * sizeof(ChainState), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(o.data(), c->d_obs_out, o.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(hc.data(), c->d_hist_cur, hc.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           c->stream));
+  CUDA_TRY(cudaMemcpyAsync(ha.data(), c->d_hist_acc, ha.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (err) {
+    CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return fail(MMC_ERR_TIMEOUT, "a band of the sublattice pass gave up waiting for its copies; the bands that "
+                                 "gave up were not updated");
+  }
+  for (int k = 0; k < nc; ++k) {
+    const ChainState &s = st[(size_t)k];
+    mmc_obs &r = out[k];
+    const unsigned long long *h = (s.nsnap == 0 ? hc.data() : ha.data()) + (size_t)k * nb;
+    if (s.nsnap == 0) {
+      const double *ok = o.data() + 8 * k;
+      const double nv = ok[6] > 0 ? ok[6] : 1.0;
+      for (int a = 0; a < 3; ++a) r.mean_m[a] = ok[a] / nv;
+      r.mean_len = ok[3] / nv;
+      r.mean_len2 = ok[4] / nv;
+      r.nonfinite = (int64_t)ok[5];
+      r.nsnap = 0;
+    } else {
+      const double ns = s.nsamples > 0 ? (double)s.nsamples : 1.0;
+      for (int a = 0; a < 3; ++a) r.mean_m[a] = s.sum_m[a] / ns;
+      r.mean_len = s.sum_len / ns;
+      r.mean_len2 = s.sum_len2 / ns;
+      r.nonfinite = (int64_t)s.nonfinite;
+      r.nsnap = (int64_t)s.nsnap;
+    }
+    if (r.hist)
+      for (int b = 0; b < nb; ++b) r.hist[b] = (int64_t)h[b];
+    r.acc_rate = s.last_att > 0 ? (double)s.last_acc / (double)s.last_att : 0.0;
+    r.theta_deg = s.theta_deg;
+    r.sweeps = (int64_t)c->host_sweep;
+  }
+  if (reset) {
+    for (auto &z : st) {
+      z.sum_m[0] = z.sum_m[1] = z.sum_m[2] = 0;
+      z.sum_len = z.sum_len2 = 0;
+      z.nsamples = z.nsnap = z.nonfinite = 0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->d_st, st.data(), st.size() * sizeof(ChainState), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->d_hist_acc, 0, (size_t)nc * nb * sizeof(unsigned long long), c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
   }
   return MMC_OK;

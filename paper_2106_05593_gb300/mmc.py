@@ -182,6 +182,28 @@ class MMC:
         check(load().mmc_get_m(self._ctx, int(chain), a.ctypes.data_as(C.c_void_p), 0), "mmc_get_m")
         return a
 
+    def set_m_all(self, m):
+        """Every chain at once: m holds chain 0's cells in natural order, then chain
+        1's, ... (total cells x 4 float32), on the host or as a CUDA torch tensor."""
+        tot = int(sum(self.ncell))
+        if hasattr(m, "is_cuda") and m.is_cuda:
+            assert m.dtype.is_floating_point and m.numel() == 4 * tot and m.is_contiguous()
+            check(load().mmc_set_m_all(self._ctx, C.c_void_p(m.data_ptr()), 1), "mmc_set_m_all")
+            return
+        a = np.ascontiguousarray(m, dtype=np.float32).reshape(-1, 4)
+        assert a.shape[0] == tot
+        check(load().mmc_set_m_all(self._ctx, a.ctypes.data_as(C.c_void_p), 0), "mmc_set_m_all")
+
+    def get_m_all(self, out=None):
+        """Every chain's m, concatenated in chain order (total cells x 4 float32)."""
+        tot = int(sum(self.ncell))
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            check(load().mmc_get_m_all(self._ctx, C.c_void_p(out.data_ptr()), 1), "mmc_get_m_all")
+            return out
+        a = np.empty((tot, 4), dtype=np.float32) if out is None else out
+        check(load().mmc_get_m_all(self._ctx, a.ctypes.data_as(C.c_void_p), 0), "mmc_get_m_all")
+        return a
+
     def init_random(self, seed, length=0.0):
         """Random directions for every chain (Philox counter (cell, 0, chain, 1));
         |m| = length, or m_e (the Eq. 7 rms length where m_e = 0) when length <= 0."""
@@ -244,6 +266,19 @@ class MMC:
         return {"mean_m": np.array(o.mean_m[:]), "mean_len": o.mean_len, "mean_len2": o.mean_len2,
                 "nsnap": o.nsnap, "nonfinite": o.nonfinite, "acc_rate": o.acc_rate,
                 "theta_deg": o.theta_deg, "sweeps": o.sweeps, "hist": hist}
+
+    def observables_all(self, reset=False):
+        """observables() of every chain, read in one device round trip."""
+        bins = self.options.hist_bins
+        n = self.nchains
+        hist = np.zeros((n, bins + 1), dtype=np.int64)
+        obs = (Obs * n)()
+        for k in range(n):
+            obs[k].hist = hist[k].ctypes.data_as(C.POINTER(C.c_int64))
+        check(load().mmc_observables_all(self._ctx, obs, int(bool(reset))), "mmc_observables_all")
+        return [{"mean_m": np.array(o.mean_m[:]), "mean_len": o.mean_len, "mean_len2": o.mean_len2,
+                 "nsnap": o.nsnap, "nonfinite": o.nonfinite, "acc_rate": o.acc_rate,
+                 "theta_deg": o.theta_deg, "sweeps": o.sweeps, "hist": hist[k]} for k, o in enumerate(obs)]
 
     def energy(self, chain=0):
         """Energy terms of the current state (J): total, exchange, DMI, anisotropy,
