@@ -29,6 +29,11 @@ template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; retu
 // multiply by -i
 template <typename C> __device__ __forceinline__ C cmi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
 
+// FP32 complex sums as one packed two-lane instruction each (Blackwell's
+// FADD2: both components in one issue, rounded like two FADDs)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
 // in-register forward DFTs
 template <typename C> __device__ __forceinline__ void dft2(C &a, C &b) {
   C t = a; a = cadd(t, b); b = csub(t, b);
@@ -38,6 +43,16 @@ template <typename C> __device__ __forceinline__ void dft4(C *v) {
   C b0 = cadd(v[1], v[3]), b1 = cmi(csub(v[1], v[3]));
   v[0] = cadd(a0, b0); v[2] = csub(a0, b0);
   v[1] = cadd(a1, b1); v[3] = csub(a1, b1);
+}
+// FP32: the sums packed; the two outputs that take -i (v1 - v3) add its
+// swapped components, which stays two scalar adds each
+__device__ __forceinline__ void dft4(float2 *v) {
+  const float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+  const float2 b0 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+  v[0] = cadd(a0, b0);
+  v[2] = csub(a0, b0);
+  v[1] = make_float2(a1.x + d.y, a1.y - d.x);
+  v[3] = make_float2(a1.x - d.y, a1.y + d.x);
 }
 template <typename C> __device__ __forceinline__ void dft8(C *v) {
   using R = decltype(v[0].x);
@@ -53,6 +68,21 @@ template <typename C> __device__ __forceinline__ void dft8(C *v) {
   v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
   v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
   v[2] = cadd(e[2], o2);   v[6] = csub(e[2], o2);
+  v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
+}
+// FP32: as above with the packed sums; the -i rotation of o[2] stays scalar
+__device__ __forceinline__ void dft8(float2 *v) {
+  const float h = 0.70710678118654752440f;
+  float2 e[4] = {v[0], v[2], v[4], v[6]};
+  float2 o[4] = {v[1], v[3], v[5], v[7]};
+  dft4(e);
+  dft4(o);
+  const float2 o1 = make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+  const float2 o3 = make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+  v[0] = cadd(e[0], o[0]); v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);   v[5] = csub(e[1], o1);
+  v[2] = make_float2(e[2].x + o[2].y, e[2].y - o[2].x);
+  v[6] = make_float2(e[2].x - o[2].y, e[2].y + o[2].x);
   v[3] = cadd(e[3], o3);   v[7] = csub(e[3], o3);
 }
 

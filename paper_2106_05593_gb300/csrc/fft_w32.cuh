@@ -35,9 +35,9 @@ __device__ __forceinline__ void dft32_lo16(float2 *x) {
   for (int n2 = 0; n2 < 8; ++n2) {
     const float2 t0 = x[n2], t1 = x[8 + n2];
     float2 o[4];
-    o[0] = make_float2(t0.x + t1.x, t0.y + t1.y);
+    o[0] = cadd(t0, t1);
     o[1] = make_float2(t0.x + t1.y, t0.y - t1.x);      // t0 - i t1
-    o[2] = make_float2(t0.x - t1.x, t0.y - t1.y);
+    o[2] = csub(t0, t1);
     o[3] = make_float2(t0.x - t1.y, t0.y + t1.x);      // t0 + i t1
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) a[4 * n2 + k1] = (n2 * k1) ? cmul_w32(o[k1], n2 * k1) : o[k1];
