@@ -93,6 +93,50 @@ struct SeqMap {
   __device__ __forceinline__ int start(int f) const { return (f / inner) * so + (f % inner) * si; }
 };
 
+// One Stockham pass of radix R (8, 4 or 2) after p elements: every thread
+// loads its `per` butterflies (per <= 8 / R), all threads synchronize, then
+// twiddle, transform and store them.  R is a compile-time constant so that the
+// butterflies' values stay in registers.
+template <typename C, int R>
+__device__ __forceinline__ void fft_smem_pass(C *buf, int N, int p, int G, int g, int st, int se, bool active,
+                                              int twshift, const C *__restrict__ tw) {
+  const int nbf = N / R;                       // butterflies in this pass
+  const int per = nbf / G;                     // butterflies per thread (1, 2 or 4)
+  C v[8];
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < 8 / R; ++t) {
+      if (t >= per) break;
+      const int b = g + t * G;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[t * R + r] = buf[st + (b + r * nbf) * se];
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < 8 / R; ++t) {
+      if (t >= per) break;
+      const int b = g + t * G;
+      const int k = b & (p - 1);
+      C *u = v + t * R;
+      if (k != 0) {
+        // twiddle exp(-2 pi i r k / (p R)): table index r * k * N / (p R)
+        const int step = (k * (N / (p * R))) << twshift;
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw[(r * step) & 4095]);
+      }
+      if (R == 8) dft8(u);
+      else if (R == 4) dft4(u);
+      else dft2(u[0], u[1]);
+      const int j = (b - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[st + (j + r * p) * se] = u[r];
+    }
+  }
+  __syncthreads();
+}
+
 // Forward (inverse = false) or inverse (unnormalized) FFT of nseq sequences of
 // length N = 2^logN in place in shared memory.  Every thread of the block must
 // call it.  The inverse is computed as conj(FFT(conj(x))).
@@ -118,36 +162,16 @@ __device__ void fft_smem(C *buf, int logN, int nseq, SeqMap map, const C *__rest
     int p = 1;
     while (p < N) {
       const int rem = N / p;
-      const int R = rem >= 8 ? 8 : rem;
-      const int nbf = N / R;                   // butterflies in this pass
-      const int per = nbf / G;                 // butterflies per thread (1, 2 or 4)
-      C v[8];
-      if (active) {
-        for (int t = 0; t < per; ++t) {
-          const int b = g + t * G;
-          for (int r = 0; r < R; ++r) v[t * R + r] = buf[st + (b + r * nbf) * map.se];
-        }
+      if (rem >= 8) {
+        fft_smem_pass<C, 8>(buf, N, p, G, g, st, map.se, active, twshift, tw);
+        p *= 8;
+      } else if (rem == 4) {
+        fft_smem_pass<C, 4>(buf, N, p, G, g, st, map.se, active, twshift, tw);
+        p *= 4;
+      } else {
+        fft_smem_pass<C, 2>(buf, N, p, G, g, st, map.se, active, twshift, tw);
+        p *= 2;
       }
-      __syncthreads();
-      if (active) {
-        for (int t = 0; t < per; ++t) {
-          const int b = g + t * G;
-          const int k = b & (p - 1);
-          C *u = v + t * R;
-          if (k != 0) {
-            // twiddle exp(-2 pi i r k / (p R)): table index r * k * N / (p R)
-            const int step = (k * (N / (p * R))) << twshift;
-            for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw[(r * step) & 4095]);
-          }
-          if (R == 8) dft8(u);
-          else if (R == 4) dft4(u);
-          else if (R == 2) dft2(u[0], u[1]);
-          const int j = (b - k) * R + k;
-          for (int r = 0; r < R; ++r) buf[st + (j + r * p) * map.se] = u[r];
-        }
-      }
-      __syncthreads();
-      p *= R;
     }
     if (inverse && active)
       for (int e = g; e < N; e += G) {

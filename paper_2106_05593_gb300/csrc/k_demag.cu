@@ -32,8 +32,11 @@
 
 namespace mmc {
 
+// the plans launch the generic kernels with at most this many threads
+constexpr int kGenericThreads = 512;
+
 template <typename R>
-__global__ void k_rows_fwd(DemagArgs<R> A) {
+__global__ void __launch_bounds__(kGenericThreads) k_rows_fwd(DemagArgs<R> A) {
   using C = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
@@ -100,7 +103,7 @@ __global__ void k_rows_fwd(DemagArgs<R> A) {
 }
 
 template <typename R>
-__global__ void k_cols(DemagArgs<R> A, int CC) {
+__global__ void __launch_bounds__(kGenericThreads) k_cols(DemagArgs<R> A, int CC) {
   using C = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
@@ -173,7 +176,7 @@ __global__ void k_cols(DemagArgs<R> A, int CC) {
 }
 
 template <typename R>
-__global__ void k_rows_inv(DemagArgs<R> A) {
+__global__ void __launch_bounds__(kGenericThreads) k_rows_inv(DemagArgs<R> A) {
   using C = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
