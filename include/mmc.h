@@ -512,6 +512,31 @@ mmc_status mmc_restore(mmc_ctx *ctx, const void *buf, size_t len);
 mmc_status mmc_observables_noalloc(const float *m, int64_t n, int hist_bins, double hist_max,
                                    double *out, unsigned long long *hist, void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Bounds-checked builds (no counterpart in the paper: a debugging aid in place
+ * of a memory checker).  A library built with -DMMC_CHECKED (build.py,
+ * build(checked=True): libmmc_checked.so) compares every global-memory index
+ * of the sweep and demag kernels with the range of the buffer region it
+ * belongs to before the access; an index outside is counted, the first one is
+ * recorded, and the access goes to the first element of the region instead,
+ * so a wrong index is reported here and never faults.  Normal builds carry no
+ * checks and always report zero.
+ * ------------------------------------------------------------------------- */
+
+/* 1 in a checked build, 0 otherwise.  Host only. */
+int mmc_checked_build(void);
+
+/* The out-of-range indices met since the context was created or last cleared:
+ * *count of them; for the first, *site (see mmc_check_site_name), and
+ * range[0] = the index, range[1..2] = the range [lo, hi) it had to lie in
+ * (element units of the buffer, relative as the kernel indexes it).  Any output
+ * pointer may be NULL.  clear != 0 resets the record after reading it.
+ * Synchronizes the context's stream. */
+mmc_status mmc_check_report(mmc_ctx *ctx, int64_t *count, int *site, int64_t range[3], int clear);
+
+/* Name of an access site of mmc_check_report ("?" for an unknown one). */
+const char *mmc_check_site_name(int site);
+
 const char *mmc_status_str(mmc_status s);
 const char *mmc_last_error(void);
 

@@ -4,6 +4,6 @@ moves, FFT demag convolution, observables and energies, behind the C ABI of
 include/mmc.h.  This package is the thin Python binding of that library.
 """
 from ._lib import EXPORTS, MmcError, load  # noqa: F401
-from .mmc import MMC, default_options, demag_kernel, thermo  # noqa: F401
+from .mmc import MMC, checked_build, default_options, demag_kernel, thermo  # noqa: F401
 
-__all__ = ["MMC", "default_options", "demag_kernel", "thermo", "MmcError", "load", "EXPORTS"]
+__all__ = ["MMC", "checked_build", "default_options", "demag_kernel", "thermo", "MmcError", "load", "EXPORTS"]

@@ -1,7 +1,8 @@
 """ctypes declarations of the C ABI in include/mmc.h (argument marshalling only).
 
 The shared library is loaded from this package directory; a missing library is
-an error (there is no fallback implementation).
+an error (there is no fallback implementation).  MMC_LIB_VARIANT=checked loads
+the bounds-checked build (libmmc_checked.so) instead.
 """
 from __future__ import annotations
 
@@ -9,7 +10,8 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmmc.so")
+LIB_PATH = os.path.join(HERE, "libmmc_checked.so" if os.environ.get("MMC_LIB_VARIANT") == "checked"
+                        else "libmmc.so")
 
 MMC_OK = 0
 STATUS = {0: "MMC_OK", -1: "MMC_ERR_ARG", -2: "MMC_ERR_CUDA", -3: "MMC_ERR_TIMEOUT",
@@ -21,7 +23,8 @@ EXPORTS = [
     "mmc_set_m", "mmc_get_m", "mmc_set_m_all", "mmc_get_m_all", "mmc_observables_all", "mmc_init_random", "mmc_sweep", "mmc_sweep_sampled",
     "mmc_demag_update", "mmc_pass_debug", "mmc_observables", "mmc_energy", "mmc_demag_field",
     "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_fft_tuning", "mmc_tuning", "mmc_sweep_field", "mmc_sweep_serial", "mmc_minimize", "mmc_set_temperature", "mmc_angle_hist", "mmc_trial_terms", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell", "mmc_demag_kernel", "mmc_thermo",
-    "mmc_checkpoint", "mmc_restore", "mmc_observables_noalloc", "mmc_status_str", "mmc_last_error",
+    "mmc_checkpoint", "mmc_restore", "mmc_observables_noalloc", "mmc_checked_build", "mmc_check_report",
+    "mmc_check_site_name", "mmc_status_str", "mmc_last_error",
 ]
 
 
@@ -159,6 +162,12 @@ def load():
     L.mmc_restore.argtypes = [vp, vp, C.c_size_t]
     L.mmc_observables_noalloc.restype = st
     L.mmc_observables_noalloc.argtypes = [vp, C.c_int64, C.c_int, C.c_double, vp, vp, vp]
+    L.mmc_checked_build.restype = C.c_int
+    L.mmc_checked_build.argtypes = []
+    L.mmc_check_report.restype = st
+    L.mmc_check_report.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int64), C.c_int]
+    L.mmc_check_site_name.restype = C.c_char_p
+    L.mmc_check_site_name.argtypes = [C.c_int]
     L.mmc_status_str.restype = C.c_char_p
     L.mmc_status_str.argtypes = [st]
     L.mmc_last_error.restype = C.c_char_p

@@ -2,6 +2,8 @@
 
 Each translation unit is compiled in parallel to an object under _build/, then
 linked into paper_2106_05593_gb300/libmmc.so against the CUDA runtime and cuFFT.
+build(checked=True) makes the bounds-checked variant (-DMMC_CHECKED, objects
+under _build_checked/) as libmmc_checked.so.
 """
 from __future__ import annotations
 
@@ -15,6 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmmc.so")
+LIB_CHECKED = os.path.join(HERE, "libmmc_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cu", "k_sweep.cu", "k_demag.cu", "k_demag_il_f16.cu", "k_demag_il_f32.cu", "k_demag_il_f16h.cu",
            "k_demag_il_d16.cu", "k_demag_w32.cu", "k_reduce.cu", "k_grad.cu", "noalloc.cu", "k_serial.cu", "k_sdesc.cu", "k_angles.cu", "k_terms.cu",
@@ -35,9 +38,12 @@ def _stale(obj: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, checked: bool = False) -> str:
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = BUILD + "_checked" if checked else BUILD
+    lib = LIB_CHECKED if checked else LIB
+    extra = (extra or []) + (["-DMMC_CHECKED"] if checked else [])
+    os.makedirs(bdir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "mmc.h"))
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
@@ -46,7 +52,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     objs = []
     for src in SOURCES:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(bdir, src + ".o")
         objs.append(obj)
         if force or _stale(obj, [path] + headers):
             cmd = [nvcc, "-c", path, "-o", obj] + flags
@@ -65,12 +71,12 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             for out in ex.map(run, jobs):
                 if verbose and out.strip():
                     print(out)
-    if force or jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcufft", "-lcudart", "-Xcompiler", "-fPIC"]
         run(cmd)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -120,7 +120,8 @@ struct DemagPlan {
   IlTables small;                       // FP32 variant 3: E = 6144 (2 blocks per SM)
   IlTables w32;                         // FP32 variant 4: warp transforms, 1024 x 1024 grids only
   bool fp64 = false;
-  bool ff = false;                      // fp64 plan run by the float-float 2D kernels
+  bool ff = false;                      // fp64 plan run by the float-float generic kernels
+  int nchain_table = 0;                 // entries of the chain table the plan indexes
   ChainDev *d_ch = nullptr;             // chain table the plan indexes
   int *rows_chain = nullptr;
   long long *rows_first = nullptr;
@@ -226,6 +227,7 @@ struct mmc_ctx {
   std::vector<int> item_first;          // first item of every chain (nchains + 1 entries)
   int band_grid = 0, stage_own = 0, stage_other = 0;
   int *d_err = nullptr;                 // device error word of the kernels' bounded waits
+  MmcCheck *d_check = nullptr;          // checked builds: the first out-of-range index (checked.cuh)
   long long launches = 0;
   uint64_t host_sweep = 0;
   bool heff_stale = true;               // state or field changed since the last demag update
@@ -659,6 +661,7 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
   P.cols_smem = csmem;
   P.fp64 = fp64;
   P.ff = ffp;
+  P.nchain_table = nid;
   if (il && !fp64) MMC_TRY(build_il_tables(c, P.small, table, ids, nid, il_elements_small(), false));
   if (il && !fp64 && !single) {
     // warp-transform path: every chain on a 1024 x 1024 padded grid; one row block
@@ -735,6 +738,8 @@ DemagLaunch make_demag_launch(mmc_ctx *c, const DemagPlan &P, float4 *heff, doub
   D.inv_smem = P.inv_smem;
   D.w32 = false;
   D.err = c->d_err;
+  D.ck = c->d_check;
+  D.nchains = P.nchain_table;
   D.nhatT = (const void *const *)c->d_nhat32t;
   D.tw1024 = c->d_tw1024;
   if (P.il2d && P.fft_variant == 4 && P.w32.ok && !P.fp64) {
@@ -791,6 +796,10 @@ SweepLaunch sweep_launch(mmc_ctx *c, int color, unsigned off, unsigned key0, uns
   P.max_polls = c->opt.wait_polls > 0 ? (unsigned)c->opt.wait_polls : (1u << 22);
   P.err = c->d_err;
   P.wait_test = c->opt.wait_test;
+  P.ck = c->d_check;
+  P.blk_total = c->sw_blocks;
+  P.nchains = c->nchains;
+  P.nitems = c->band ? c->item_first.back() : 0;
   return P;
 }
 
@@ -1554,6 +1563,8 @@ mmc_status mmc_create(const mmc_chain_desc *chains, int nchains, const mmc_optio
     }
     MMC_TRY_OR(dalloc_t(c, &c->d_err, 1));
     CUDA_TRY_OR(cudaMemset(c->d_err, 0, sizeof(int)));
+    MMC_TRY_OR(dalloc_t(c, &c->d_check, 1));
+    CUDA_TRY_OR(cudaMemset(c->d_check, 0, sizeof(MmcCheck)));
     std::vector<int> oc;
     std::vector<long long> of;
     for (int ci = 0; ci < nchains; ++ci) {
@@ -2574,6 +2585,35 @@ mmc_status mmc_restore(mmc_ctx *c, const void *buf, size_t len) {
   c->heff_stale = true;
   c->obs_fresh = false;
   return MMC_OK;
+}
+
+int mmc_checked_build(void) { return kChecked ? 1 : 0; }
+
+mmc_status mmc_check_report(mmc_ctx *c, int64_t *count, int *site, int64_t range[3], int clear) {
+  if (!c) return fail(MMC_ERR_ARG, "null context");
+  MmcCheck r;
+  std::memset(&r, 0, sizeof(r));
+  if (c->d_check) {
+    CUDA_TRY(cudaMemcpyAsync(&r, c->d_check, sizeof(r), cudaMemcpyDeviceToHost, c->stream));
+    if (clear) CUDA_TRY(cudaMemsetAsync(c->d_check, 0, sizeof(MmcCheck), c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  if (count) *count = (int64_t)r.count;
+  if (site) *site = r.count ? r.site : 0;
+  if (range) {
+    range[0] = r.index;
+    range[1] = r.lo;
+    range[2] = r.hi;
+  }
+  return MMC_OK;
+}
+
+const char *mmc_check_site_name(int site) {
+  static const char *const names[kCkSiteCount] = {
+      "none", "sweep block table", "sweep cell", "sweep neighbour", "sweep field", "sweep per-cell table",
+      "sweep debug output", "band item", "band copy", "demag m", "demag spectrum", "demag tensor", "demag field",
+      "demag block table", "fused copy", "fused state"};
+  return site >= 0 && site < kCkSiteCount ? names[site] : "?";
 }
 
 const char *mmc_status_str(mmc_status s) {

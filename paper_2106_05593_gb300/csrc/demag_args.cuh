@@ -26,7 +26,21 @@ struct DemagArgs {
   int Hd_chain;
   const R *m_nat;     // optional natural-order input (3 per cell) instead of the split state
   R Ms_override;      // > 0: uniform Ms0 used with m_nat
+  MmcCheck *ck;       // checked builds: the record (checked.cuh)
+  int nchains;        // entries of the chain table
 };
+
+// the block's chain, checked against the chain table
+template <typename R>
+__device__ __forceinline__ int demag_chain_of_block(const DemagArgs<R> &A) {
+  return (int)MMC_CK(A.ck, A.blk_chain[blockIdx.x], 0, A.nchains, kCkDemagBlock);
+}
+
+// elements of a chain's spectrum region (rows rounded up to four in 2D)
+__device__ __forceinline__ long long spectrum_elems(const ChainDev &ch) {
+  const long long rows = ch.Pz == 1 ? ((ch.nrows + 3) & ~3) : ch.nrows;
+  return 3 * rows * ch.Sx;
+}
 
 __device__ __forceinline__ int pairs_per_block(int Px) {
   const int G = Px >= 8 ? Px >> 3 : 1;
@@ -37,11 +51,11 @@ __device__ __forceinline__ int pairs_per_block(int Px) {
 // M = Ms0 m of cell (x, row r) from the split layout, formed in the convolution's precision
 template <typename R>
 __device__ __forceinline__ void load_M(const ChainDev &ch, const float4 *m, const float *ms, const float *ms_lo,
-                                       int r, int x, R &Mx, R &My, R &Mz) {
+                                       int r, int x, R &Mx, R &My, R &Mz, MmcCheck *ck = nullptr) {
   const int k = (int)divq((unsigned)r, ch.ny_m, ch.ny_l), j = r - k * ch.ny;
   const int col = (x + j + k) & 1;
   const long long S = (long long)ch.nrows * ch.hx;
-  const long long idx = (long long)col * S + (long long)r * ch.hx + (x >> 1);
+  const long long idx = MMC_CK(ck, (long long)col * S + (long long)r * ch.hx + (x >> 1), 0, 2 * S, kCkDemagM);
   const float4 v = m[ch.m_off + idx];
   R Ms = ch.ms_off >= 0 ? (R)ms[ch.ms_off + idx] : (R)ch.Ms0d;
   // the wider formats take per-cell Ms0 as the pair (FP32 value, rest)

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kGenericThreads) k_rows_fwd(DemagArgs<R> A) {
   using C = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
-  const int c = A.blk_chain[blockIdx.x];
+  const int c = demag_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, lx = ch.lx, nx = ch.nx, nrows = ch.nrows, Sx = ch.Sx;
   const int np = pairs_per_block(Px);
@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(kGenericThreads) k_rows_fwd(DemagArgs<R> A) {
           M1x = Ms * v1[0]; M1y = Ms * v1[1]; M1z = Ms * v1[2];
         }
       } else {
-        load_M<R>(ch, A.m, A.ms, A.ms_lo, r0, x, M0x, M0y, M0z);
-        if (r1 < nrows) load_M<R>(ch, A.m, A.ms, A.ms_lo, r1, x, M1x, M1y, M1z);
+        load_M<R>(ch, A.m, A.ms, A.ms_lo, r0, x, M0x, M0y, M0z, A.ck);
+        if (r1 < nrows) load_M<R>(ch, A.m, A.ms, A.ms_lo, r1, x, M1x, M1y, M1z, A.ck);
       }
     }
     C z;
@@ -87,16 +87,16 @@ __global__ void __launch_bounds__(kGenericThreads) k_rows_fwd(DemagArgs<R> A) {
       a.x = (R)0.5 * (Z.x + Zm.x); a.y = (R)0.5 * (Z.y - Zm.y);
       b.x = (R)0.5 * (Z.y + Zm.y); b.y = (R)0.5 * (Zm.x - Z.x);
       if (sq == 0) {
-        S[0 * plane + (long long)r0 * Sx + kx] = a;
-        S[1 * plane + (long long)r0 * Sx + kx] = b;
+        S[MMC_CK(A.ck, 0 * plane + (long long)r0 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)] = a;
+        S[MMC_CK(A.ck, 1 * plane + (long long)r0 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)] = b;
       } else if (sq == 1) {
         if (r1 < nrows) {
-          S[0 * plane + (long long)r1 * Sx + kx] = a;
-          S[1 * plane + (long long)r1 * Sx + kx] = b;
+          S[MMC_CK(A.ck, 0 * plane + (long long)r1 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)] = a;
+          S[MMC_CK(A.ck, 1 * plane + (long long)r1 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)] = b;
         }
       } else {
-        S[2 * plane + (long long)r0 * Sx + kx] = a;
-        if (r1 < nrows) S[2 * plane + (long long)r1 * Sx + kx] = b;
+        S[MMC_CK(A.ck, 2 * plane + (long long)r0 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)] = a;
+        if (r1 < nrows) S[MMC_CK(A.ck, 2 * plane + (long long)r1 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)] = b;
       }
     }
   }
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kGenericThreads) k_cols(DemagArgs<R> A, int CC
   using C = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
-  const int c = A.blk_chain[blockIdx.x];
+  const int c = demag_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, Py = ch.Py, Pz = ch.Pz, ly = ch.ly, lz = ch.lz;
   const int ny = ch.ny, nz = ch.nz, nrows = ch.nrows, Sx = ch.Sx;
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kGenericThreads) k_cols(DemagArgs<R> A, int CC
     const int kx = kx0 + col;
     if (kx < ncolq) {
       const int j = r % ny, k = r / ny;
-      buf[((comp * CC + col) * Pz + k) * Py + j] = S[comp * plane + (long long)r * Sx + kx];
+      buf[((comp * CC + col) * Pz + k) * Py + j] = S[MMC_CK(A.ck, comp * plane + (long long)r * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)];
     }
   }
   __syncthreads();
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kGenericThreads) k_cols(DemagArgs<R> A, int CC
     const int kzq = kz <= Pz / 2 ? kz : Pz - kz;
     const R sy = ky <= Py / 2 ? (R)1 : (R)-1;
     const R sz = kz <= Pz / 2 ? (R)1 : (R)-1;
-    const long long qi = ((long long)kzq * qy + kyq) * qx + kx;
+    const long long qi = MMC_CK(A.ck, ((long long)kzq * qy + kyq) * qx + kx, 0, Q, kCkDemagTensor);
     const R Nxx = nh[qi], Nyy = nh[Q + qi], Nzz = nh[2 * Q + qi], Nxy = sy * nh[3 * Q + qi];
     R Nxz = 0, Nyz = 0;
     if (Pz > 1) { Nxz = sz * nh[4 * Q + qi]; Nyz = sy * sz * nh[5 * Q + qi]; }
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kGenericThreads) k_cols(DemagArgs<R> A, int CC
     const int kx = kx0 + col;
     if (kx < ncolq) {
       const int j = r % ny, k = r / ny;
-      S[comp * plane + (long long)r * Sx + kx] = buf[((comp * CC + col) * Pz + k) * Py + j];
+      S[MMC_CK(A.ck, comp * plane + (long long)r * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)] = buf[((comp * CC + col) * Pz + k) * Py + j];
     }
   }
 }
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kGenericThreads) k_rows_inv(DemagArgs<R> A) {
   using C = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
-  const int c = A.blk_chain[blockIdx.x];
+  const int c = demag_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, lx = ch.lx, nx = ch.nx, nrows = ch.nrows, Sx = ch.Sx;
   const int np = pairs_per_block(Px);
@@ -195,13 +195,13 @@ __global__ void __launch_bounds__(kGenericThreads) k_rows_inv(DemagArgs<R> A) {
     C a[3], b[3];
     for (int t = 0; t < 3; ++t) { a[t].x = 0; a[t].y = 0; b[t] = a[t]; }
     if (pr < totpairs) {
-      a[0] = S[0 * plane + (long long)r0 * Sx + kx];
-      b[0] = S[1 * plane + (long long)r0 * Sx + kx];
-      a[2] = S[2 * plane + (long long)r0 * Sx + kx];
+      a[0] = S[MMC_CK(A.ck, 0 * plane + (long long)r0 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)];
+      b[0] = S[MMC_CK(A.ck, 1 * plane + (long long)r0 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)];
+      a[2] = S[MMC_CK(A.ck, 2 * plane + (long long)r0 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)];
       if (r1 < nrows) {
-        a[1] = S[0 * plane + (long long)r1 * Sx + kx];
-        b[1] = S[1 * plane + (long long)r1 * Sx + kx];
-        b[2] = S[2 * plane + (long long)r1 * Sx + kx];
+        a[1] = S[MMC_CK(A.ck, 0 * plane + (long long)r1 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)];
+        b[1] = S[MMC_CK(A.ck, 1 * plane + (long long)r1 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)];
+        b[2] = S[MMC_CK(A.ck, 2 * plane + (long long)r1 * Sx + kx, 0, spectrum_elems(ch), kCkDemagSpectrum)];
       }
     }
     const bool edge = (kx == 0) || (2 * kx == Px);
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kGenericThreads) k_rows_inv(DemagArgs<R> A) {
       const R Hz = (h == 0 ? z2.x : z2.y) * scale;
       const int j = r % ch.ny, k = r / ch.ny;
       const int colr = (x + j + k) & 1;
-      const long long li = (long long)colr * Sl + (long long)r * ch.hx + (x >> 1);
+      const long long li = MMC_CK(A.ck, (long long)colr * Sl + (long long)r * ch.hx + (x >> 1), 0, 2 * Sl, kCkDemagField);
       if (A.heff) {
         const float zee = percell ? A.tab[ch.t_off + 2 * Sl + li].x : ch.zee;
         const float mu0f = (float)mu0d;
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kGenericThreads) k_rows_inv(DemagArgs<R> A) {
                                             zee * (ch.Bz + mu0f * (float)Hz), 0.f);
       }
       if (A.Hd && c == A.Hd_chain) {
-        const long long nat = x + (long long)nx * r;
+        const long long nat = MMC_CK(A.ck, x + (long long)nx * r, 0, (long long)nx * nrows, kCkDemagField);
         A.Hd[3 * nat + 0] = (double)Hx;
         A.Hd[3 * nat + 1] = (double)Hy;
         A.Hd[3 * nat + 2] = (double)Hz;
@@ -267,6 +267,8 @@ void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
   A.heff = P.heff; A.Hd = P.Hd; A.Hd_chain = P.Hd_chain;
   A.m_nat = reinterpret_cast<const R *>(P.m_nat);
   A.Ms_override = (R)P.Ms_override;
+  A.ck = P.ck;
+  A.nchains = P.nchains;
   if constexpr (!std::is_same<R, ff>::value) {
     if (P.il2d) {
       if constexpr (sizeof(R) == 8) launch_il<CfgD16>(L, P, A);

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagA
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *raw = reinterpret_cast<C *>(smem_raw);
   C *buf = raw;
-  const int c = A.blk_chain[blockIdx.x];
+  const int c = demag_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
   // 3 groups (x+iy of the even row, x+iy of the odd row, z_even + i z_odd) of np
@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagA
           M1x = Ms * v1[0]; M1y = Ms * v1[1]; M1z = Ms * v1[2];
         }
       } else {
-        load_M<R>(ch, A.m, A.ms, A.ms_lo, r0, x, M0x, M0y, M0z);
-        if (r1 < ny) load_M<R>(ch, A.m, A.ms, A.ms_lo, r1, x, M1x, M1y, M1z);
+        load_M<R>(ch, A.m, A.ms, A.ms_lo, r0, x, M0x, M0y, M0z, A.ck);
+        if (r1 < ny) load_M<R>(ch, A.m, A.ms, A.ms_lo, r1, x, M1x, M1y, M1z, A.ck);
       }
     }
     C z;
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagA
     C o2;
     if (!take_b) { o2.x = (R)0.5 * (Z.x + Zm.x); o2.y = (R)0.5 * (Z.y - Zm.y); }
     else { o2.x = (R)0.5 * (Z.y + Zm.y); o2.y = (R)0.5 * (Zm.x - Z.x); }
-    S[tiled(comp, r, kx, ny, NG, lcc)] = o2;
+    S[MMC_CK(A.ck, tiled(comp, r, kx, ny, NG, lcc), 0, spectrum_elems(ch), kCkDemagSpectrum)] = o2;
   }
 }
 
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *raw = reinterpret_cast<C *>(smem_raw);
   C *buf = raw;
-  const int c = A.blk_chain[blockIdx.x];
+  const int c = demag_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, Py = ch.Py, ly = ch.ly, ny = ch.ny, Sx = ch.Sx;
   constexpr int LE3 = ilog2c(E / 3);         // E / 3 is a power of two
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
 #pragma unroll 8
     for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
       const int cc = idx & (CC - 1), y = (idx >> lcc) & (Py - 1), comp = idx >> LE3;
-      buf[idx] = S[((long long)(comp * NG + g) * ny + y) * CC + cc];
+      buf[idx] = S[MMC_CK(A.ck, ((long long)(comp * NG + g) * ny + y) * CC + cc, 0, spectrum_elems(ch), kCkDemagSpectrum)];
     }
   } else {
 #pragma unroll 8
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
       const int cc = idx & (CC - 1), y = (idx >> lcc) & ((Py >> 1) - 1), comp = idx >> (LE3 - 1);
       C v;
       v.x = 0; v.y = 0;
-      if (y < ny) v = S[((long long)(comp * NG + g) * ny + y) * CC + cc];
+      if (y < ny) v = S[MMC_CK(A.ck, ((long long)(comp * NG + g) * ny + y) * CC + cc, 0, spectrum_elems(ch), kCkDemagSpectrum)];
       buf[(comp * Py + y) * CC + cc] = v;
     }
   }
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
     if (kx >= qx) continue;
     const int kyq = ky <= Py / 2 ? ky : Py - ky;
     const R sy = ky <= Py / 2 ? (R)1 : (R)-1;
-    const long long qi = (long long)kyq * qx + kx;
+    const long long qi = MMC_CK(A.ck, (long long)kyq * qx + kx, 0, Q, kCkDemagTensor);
     const R Nxx = nh[qi], Nyy = nh[Q + qi], Nzz = nh[2 * Q + qi], Nxy = sy * nh[3 * Q + qi];
     const int b0 = ky * CC + cc, b1 = (Py + ky) * CC + cc, b2 = (2 * Py + ky) * CC + cc;
     const C Mx = buf[b0], My = buf[b1], Mz = buf[b2];
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
   C *So = A.S + ch.s_off;
   for (int idx = threadIdx.x; idx < E; idx += blockDim.x) {
     const int cc = idx & (CC - 1), y = (idx >> lcc) & (Py - 1), comp = idx >> LE3;
-    if (y < ny) So[((long long)(comp * NG + g) * ny + y) * CC + cc] = buf[idx];
+    if (y < ny) So[MMC_CK(A.ck, ((long long)(comp * NG + g) * ny + y) * CC + cc, 0, spectrum_elems(ch), kCkDemagSpectrum)] = buf[idx];
   }
 }
 
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_inv2(DemagA
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *raw = reinterpret_cast<C *>(smem_raw);
   C *buf = raw;
-  const int c = A.blk_chain[blockIdx.x];
+  const int c = demag_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int Px = ch.Px, lx = ch.lx, nx = ch.nx, ny = ch.ny, Sx = ch.Sx;
   constexpr int LE3 = ilog2c(E / 3);         // E / 3 is a power of two
@@ -222,11 +222,12 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_inv2(DemagA
     C ax, ay, z0, z1;
     ax.x = ax.y = ay.x = ay.y = z0.x = z0.y = z1.x = z1.y = 0;
     if (r < ny) {
-      ax = S[tiled(0, r, kx, ny, NG, lcc)];
-      ay = S[tiled(1, r, kx, ny, NG, lcc)];
+      const long long se = spectrum_elems(ch);
+      ax = S[MMC_CK(A.ck, tiled(0, r, kx, ny, NG, lcc), 0, se, kCkDemagSpectrum)];
+      ay = S[MMC_CK(A.ck, tiled(1, r, kx, ny, NG, lcc), 0, se, kCkDemagSpectrum)];
       if (h == 0) {
-        z0 = S[tiled(2, r, kx, ny, NG, lcc)];
-        if (r + 1 < ny) z1 = S[tiled(2, r + 1, kx, ny, NG, lcc)];
+        z0 = S[MMC_CK(A.ck, tiled(2, r, kx, ny, NG, lcc), 0, se, kCkDemagSpectrum)];
+        if (r + 1 < ny) z1 = S[MMC_CK(A.ck, tiled(2, r + 1, kx, ny, NG, lcc), 0, se, kCkDemagSpectrum)];
       }
     }
     put(h * gs + qq, kx, ax, ay);
@@ -253,14 +254,14 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_inv2(DemagA
       const R Hy = (h == 0 ? z0.y : z1.y) * scale;
       const R Hz = (h == 0 ? z2.x : z2.y) * scale;
       const int colr = (x + r) & 1;
-      const long long li = (long long)colr * Sl + (long long)r * ch.hx + (x >> 1);
+      const long long li = MMC_CK(A.ck, (long long)colr * Sl + (long long)r * ch.hx + (x >> 1), 0, 2 * Sl, kCkDemagField);
       if (A.heff) {
         const float zee = percell ? A.tab[ch.t_off + 2 * Sl + li].x : ch.zee;
         A.heff[ch.h_off + li] = make_float4(zee * (ch.Bx + mu0f * (float)Hx), zee * (ch.By + mu0f * (float)Hy),
                                             zee * (ch.Bz + mu0f * (float)Hz), 0.f);
       }
       if (A.Hd && c == A.Hd_chain) {
-        const long long nat = x + (long long)nx * r;
+        const long long nat = MMC_CK(A.ck, x + (long long)nx * r, 0, (long long)nx * ny, kCkDemagField);
         A.Hd[3 * nat + 0] = (double)Hx;
         A.Hd[3 * nat + 1] = (double)Hy;
         A.Hd[3 * nat + 2] = (double)Hz;

@@ -43,6 +43,8 @@ struct W32Args {
   double *Hd;
   int Hd_chain;
   int *err;                       // device error word (a wait for the tensor copy that gave up)
+  MmcCheck *ck;                   // checked builds: the record (checked.cuh)
+  int nchains;                    // entries of the chain table
 };
 
 constexpr int kW32Half = 513;           // kx = 0..512
@@ -58,10 +60,23 @@ __device__ __forceinline__ long long w32_at(const ChainDev &ch, int comp, int y,
   return ch.s_off + (long long)comp * R4 * kW32Sx + (long long)(y >> 2) * kW32Tile + 4LL * kx + (y & 3);
 }
 
+// index of float2 pair o (two rows of one kx) of component comp's tile `tile`,
+// checked against the chain's spectrum
+__device__ __forceinline__ long long w32_tile_pair(const W32Args &A, const ChainDev &ch, int comp, int tile, int o) {
+  const long long R4 = (long long)((ch.nrows + 3) & ~3);
+  return MMC_CKR(A.ck, w32_at(ch, comp, 4 * tile, 0) + 2LL * o, 2, ch.s_off, ch.s_off + 3 * R4 * kW32Sx,
+                 kCkDemagSpectrum);
+}
+
+// the block's chain, checked against the chain table
+__device__ __forceinline__ int w32_chain_of_block(const W32Args &A) {
+  return (int)MMC_CK(A.ck, A.blk_chain[blockIdx.x], 0, A.nchains, kCkDemagBlock);
+}
+
 __global__ void __launch_bounds__(192, 3) k_w32_rows_fwd(W32Args A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
-  const int c = A.blk_chain[blockIdx.x];
+  const int c = w32_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int tile = (int)(blockIdx.x - A.blk_first[c]);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -87,13 +102,13 @@ __global__ void __launch_bounds__(192, 3) k_w32_rows_fwd(W32Args A) {
     const bool in = 32 * n1 + lane < nx;
     float2 z = make_float2(0.f, 0.f);
     if (in && ha) {
-      const float4 t = ma[16 * n1];
-      const float Ms = pc ? A.ms[ch.ms_off + oa + 16 * n1] : Msu;
+      const float4 t = ma[MMC_CK(A.ck, 16 * n1, -oa, 2 * S - oa, kCkDemagM)];
+      const float Ms = pc ? A.ms[ch.ms_off + MMC_CK(A.ck, oa + 16 * n1, 0, 2 * S, kCkDemagM)] : Msu;
       z = q == 2 ? make_float2(Ms * t.z, 0.f) : make_float2(Ms * t.x, Ms * t.y);
     }
     if (in && hb) {
-      const float4 t = mb[16 * n1];
-      const float Ms = pc ? A.ms[ch.ms_off + ob + 16 * n1] : Msu;
+      const float4 t = mb[MMC_CK(A.ck, 16 * n1, -ob, 2 * S - ob, kCkDemagM)];
+      const float Ms = pc ? A.ms[ch.ms_off + MMC_CK(A.ck, ob + 16 * n1, 0, 2 * S, kCkDemagM)] : Msu;
       z.y = Ms * t.z;
     }
     v[n1] = z;
@@ -136,8 +151,7 @@ __global__ void __launch_bounds__(192, 3) k_w32_rows_fwd(W32Args A) {
     const int kx = o >> 1, h = o & 1;
     const float2 a = sm[(comp * 4 + 2 * h) * kW32TilePitch + kx];
     const float2 b = sm[(comp * 4 + 2 * h + 1) * kW32TilePitch + kx];
-    float4 *dst = reinterpret_cast<float4 *>(A.S + w32_at(ch, comp, 4 * tile, 0));
-    dst[o] = make_float4(a.x, a.y, b.x, b.y);
+    *reinterpret_cast<float4 *>(A.S + w32_tile_pair(A, ch, comp, tile, o)) = make_float4(a.x, a.y, b.x, b.y);
   }
 }
 
@@ -146,7 +160,7 @@ __global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A) {
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
   float *tn = reinterpret_cast<float *>(sm + 3 * kW32Buf);   // this column's tensor, [4][kW32TPitch]
   __shared__ uint64_t tbar;
-  const int c = A.blk_chain[blockIdx.x];
+  const int c = w32_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int kx = (int)(blockIdx.x - A.blk_first[c]);
   const int lane = threadIdx.x & 31, comp = threadIdx.x >> 5;
@@ -157,20 +171,26 @@ __global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A) {
   if (threadIdx.x == 0) {
     mbar_init(&tbar, 1);
     mbar_init_fence();
-    const float *src = A.nhatT[ch.spec] + (long long)kx * kW32TPitch;
+    const float *src = A.nhatT[ch.spec];
     mbar_arrive_expect_tx(&tbar, 4u * kW32TPitch * 4u);
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      bulk_g2s(tn + t * kW32TPitch, src + (long long)t * kW32TQ, kW32TPitch * 4u, &tbar);
+      bulk_g2s(tn + t * kW32TPitch,
+               src + MMC_CKR(A.ck, (long long)kx * kW32TPitch + (long long)t * kW32TQ, kW32TPitch, 0, 4 * kW32TQ,
+                             kCkDemagTensor),
+               kW32TPitch * 4u, &tbar);
   }
   // column kx of component comp: row y = 32 n1 + lane is in tile 8 n1 + lane / 4
   const long long R4 = (long long)((ch.nrows + 3) & ~3);
-  float2 *col = A.S + ch.s_off + (long long)comp * R4 * kW32Sx + (long long)(lane >> 2) * kW32Tile + 4 * kx + (lane & 3);
+  const long long cb = (long long)comp * R4 * kW32Sx + (long long)(lane >> 2) * kW32Tile + 4 * kx + (lane & 3);
+  float2 *col = A.S + ch.s_off + cb;
+  const long long clo = -cb, chi = 3 * R4 * kW32Sx - cb;   // the chain's spectrum, relative to col
 
   float2 v[32];
 #pragma unroll
   for (int n1 = 0; n1 < 16; ++n1)
-    v[n1] = 32 * n1 + lane < ny ? col[(long long)n1 * 8 * kW32Tile] : make_float2(0.f, 0.f);
+    v[n1] = 32 * n1 + lane < ny ? col[MMC_CK(A.ck, (long long)n1 * 8 * kW32Tile, clo, chi, kCkDemagSpectrum)]
+                                : make_float2(0.f, 0.f);
   dft32_lo16(v);
   w32_fwd_tail(v, buf, A.tw, lane);                    // v[k2] = M^_comp(kx, lane + 32 k2)
 
@@ -214,13 +234,13 @@ __global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A) {
   w32_inv(v, buf, A.tw, lane);                         // v[n''] = H_comp(kx, row lane + 32 n'')
 #pragma unroll
   for (int n2 = 0; n2 < 16; ++n2)
-    if (lane + 32 * n2 < ny) col[(long long)n2 * 8 * kW32Tile] = v[n2];
+    if (lane + 32 * n2 < ny) col[MMC_CK(A.ck, (long long)n2 * 8 * kW32Tile, clo, chi, kCkDemagSpectrum)] = v[n2];
 }
 
 __global__ void __launch_bounds__(192, 3) k_w32_rows_inv(W32Args A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
-  const int c = A.blk_chain[blockIdx.x];
+  const int c = w32_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int tile = (int)(blockIdx.x - A.blk_first[c]);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -232,7 +252,7 @@ __global__ void __launch_bounds__(192, 3) k_w32_rows_inv(W32Args A) {
     constexpr int per = kW32Half * 2;                  // float4 (two rows of one kx) per component
     for (int i = threadIdx.x; i < 3 * per; i += blockDim.x) {
       const int comp = i / per, o = i - comp * per;
-      const float4 t = reinterpret_cast<const float4 *>(A.S + w32_at(ch, comp, 4 * tile, 0))[o];
+      const float4 t = *reinterpret_cast<const float4 *>(A.S + w32_tile_pair(A, ch, comp, tile, o));
       const int kx = o >> 1, r = 2 * (o & 1);
       sm[(comp * 4 + r) * kW32TilePitch + kx] = make_float2(t.x, t.y);
       sm[(comp * 4 + r + 1) * kW32TilePitch + kx] = make_float2(t.z, t.w);
@@ -280,14 +300,14 @@ __global__ void __launch_bounds__(192, 3) k_w32_rows_inv(W32Args A) {
     if (r >= ny) break;
     const float Hx = ft[(0 * 4 + rr) * 512 + x], Hy = ft[(1 * 4 + rr) * 512 + x], Hz = ft[(2 * 4 + rr) * 512 + x];
     const int colr = (x + r) & 1;
-    const long long li = (long long)colr * Sl + (long long)r * ch.hx + (x >> 1);
+    const long long li = MMC_CK(A.ck, (long long)colr * Sl + (long long)r * ch.hx + (x >> 1), 0, 2 * Sl, kCkDemagField);
     if (A.heff) {
       const float zee = percell ? A.tab[ch.t_off + 2 * Sl + li].x : ch.zee;
       A.heff[ch.h_off + li] = make_float4(zee * (ch.Bx + mu0f * Hx), zee * (ch.By + mu0f * Hy),
                                           zee * (ch.Bz + mu0f * Hz), 0.f);
     }
     if (A.Hd && c == A.Hd_chain) {
-      const long long nat = x + (long long)nx * r;
+      const long long nat = MMC_CK(A.ck, x + (long long)nx * r, 0, (long long)nx * ny, kCkDemagField);
       A.Hd[3 * nat + 0] = (double)Hx;
       A.Hd[3 * nat + 1] = (double)Hy;
       A.Hd[3 * nat + 2] = (double)Hz;
@@ -332,7 +352,7 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_black_rows_fwd(FusedAr
   __shared__ float4 skv[kChainKVec];
   __shared__ unsigned wacc[kFusedThreads / 32], watt[kFusedThreads / 32];
   const W32Args &A = F.W;
-  const int c = A.blk_chain[blockIdx.x];
+  const int c = w32_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int tile = (int)(blockIdx.x - A.blk_first[c]);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -350,11 +370,15 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_black_rows_fwd(FusedAr
     const int ra = r0 + nr < ny ? r0 + nr : (pby ? 0 : -1);
     const unsigned row_b = (unsigned)hx * 16u;
     mbar_arrive_expect_tx(&bar, 3u * (unsigned)nr * row_b + (rb >= 0 ? row_b : 0u) + (ra >= 0 ? row_b : 0u));
-    bulk_g2s(tb, mblk + (long long)r0 * hx, (unsigned)nr * row_b, &bar);
-    bulk_g2s(tr + hx, mred + (long long)r0 * hx, (unsigned)nr * row_b, &bar);
-    if (rb >= 0) bulk_g2s(tr, mred + (long long)rb * hx, row_b, &bar);
-    if (ra >= 0) bulk_g2s(tr + (long long)(nr + 1) * hx, mred + (long long)ra * hx, row_b, &bar);
-    bulk_g2s(th, F.heff + ch.h_off + S + (long long)r0 * hx, (unsigned)nr * row_b, &bar);
+    // row offsets within one colour of the chain (S slots)
+    const long long o0 = MMC_CKR(A.ck, (long long)r0 * hx, (long long)nr * hx, 0, S, kCkFusedCopy);
+    bulk_g2s(tb, mblk + o0, (unsigned)nr * row_b, &bar);
+    bulk_g2s(tr + hx, mred + o0, (unsigned)nr * row_b, &bar);
+    if (rb >= 0) bulk_g2s(tr, mred + MMC_CKR(A.ck, (long long)rb * hx, hx, 0, S, kCkFusedCopy), row_b, &bar);
+    if (ra >= 0)
+      bulk_g2s(tr + (long long)(nr + 1) * hx, mred + MMC_CKR(A.ck, (long long)ra * hx, hx, 0, S, kCkFusedCopy), row_b,
+               &bar);
+    bulk_g2s(th, F.heff + ch.h_off + S + o0, (unsigned)nr * row_b, &bar);
   }
   __syncthreads();
   const ChainK K = load_chain_vec(skv);
@@ -432,7 +456,7 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_black_rows_fwd(FusedAr
         if (acc) {
           const float4 mp = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
           tb[ql[e]] = mp;
-          mblk[(long long)r0 * hx + ql[e]] = mp;
+          mblk[MMC_CK(A.ck, (long long)r0 * hx + ql[e], 0, S, kCkFusedState)] = mp;
         }
       }
       na += __popc(__ballot_sync(0xffffffffu, acc));
@@ -509,8 +533,7 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_black_rows_fwd(FusedAr
     const int kx = o >> 1, hh = o & 1;
     const float2 aa = sm[(comp * 4 + 2 * hh) * kW32TilePitch + kx];
     const float2 bb = sm[(comp * 4 + 2 * hh + 1) * kW32TilePitch + kx];
-    float4 *dst = reinterpret_cast<float4 *>(A.S + w32_at(ch, comp, 4 * tile, 0));
-    dst[o] = make_float4(aa.x, aa.y, bb.x, bb.y);
+    *reinterpret_cast<float4 *>(A.S + w32_tile_pair(A, ch, comp, tile, o)) = make_float4(aa.x, aa.y, bb.x, bb.y);
   }
 }
 
@@ -536,7 +559,7 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_rows_inv_red(FusedArgs
   __shared__ float4 skv[kChainKVec];
   __shared__ unsigned wacc[kFusedThreads / 32], watt[kFusedThreads / 32];
   const W32Args &A = F.W;
-  const int c = A.blk_chain[blockIdx.x];
+  const int c = w32_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int tile = (int)(blockIdx.x - A.blk_first[c]);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -553,7 +576,7 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_rows_inv_red(FusedArgs
     constexpr int per = kW32Half * 2;
     for (int i = threadIdx.x; i < 3 * per; i += blockDim.x) {
       const int comp = i / per, o = i - comp * per;
-      const float4 t = reinterpret_cast<const float4 *>(A.S + w32_at(ch, comp, 4 * tile, 0))[o];
+      const float4 t = *reinterpret_cast<const float4 *>(A.S + w32_tile_pair(A, ch, comp, tile, o));
       const int kx = o >> 1, r = 2 * (o & 1);
       sm[(comp * 4 + r) * kW32TilePitch + kx] = make_float2(t.x, t.y);
       sm[(comp * 4 + r + 1) * kW32TilePitch + kx] = make_float2(t.z, t.w);
@@ -588,10 +611,13 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_rows_inv_red(FusedArgs
     const unsigned row_b = (unsigned)hx * 16u;
     const float4 *mred = A.m + ch.m_off, *mblk = A.m + ch.m_off + S;
     mbar_arrive_expect_tx(&bar, 2u * (unsigned)nr * row_b + (rb >= 0 ? row_b : 0u) + (ra >= 0 ? row_b : 0u));
-    bulk_g2s(tred, mred + (long long)r0 * hx, (unsigned)nr * row_b, &bar);
-    bulk_g2s(tblk + hx, mblk + (long long)r0 * hx, (unsigned)nr * row_b, &bar);
-    if (rb >= 0) bulk_g2s(tblk, mblk + (long long)rb * hx, row_b, &bar);
-    if (ra >= 0) bulk_g2s(tblk + (long long)(nr + 1) * hx, mblk + (long long)ra * hx, row_b, &bar);
+    const long long o0 = MMC_CKR(A.ck, (long long)r0 * hx, (long long)nr * hx, 0, S, kCkFusedCopy);
+    bulk_g2s(tred, mred + o0, (unsigned)nr * row_b, &bar);
+    bulk_g2s(tblk + hx, mblk + o0, (unsigned)nr * row_b, &bar);
+    if (rb >= 0) bulk_g2s(tblk, mblk + MMC_CKR(A.ck, (long long)rb * hx, hx, 0, S, kCkFusedCopy), row_b, &bar);
+    if (ra >= 0)
+      bulk_g2s(tblk + (long long)(nr + 1) * hx, mblk + MMC_CKR(A.ck, (long long)ra * hx, hx, 0, S, kCkFusedCopy),
+               row_b, &bar);
   }
   const float scale = 1.f / ((float)kW32N * (float)kW32N);
 #pragma unroll
@@ -610,7 +636,7 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_rows_inv_red(FusedArgs
     const int x = 2 * sl + ((r0 + rl + 1) & 1);
     if (x >= nx) continue;
     const float Hx = ft[(0 * 4 + rl) * 512 + x], Hy = ft[(1 * 4 + rl) * 512 + x], Hz = ft[(2 * 4 + rl) * 512 + x];
-    A.heff[ch.h_off + S + (long long)r0 * hx + qb] = make_float4(
+    A.heff[ch.h_off + S + MMC_CK(A.ck, (long long)r0 * hx + qb, 0, S, kCkDemagField)] = make_float4(
         ch.zee * (ch.Bx + mu0f * Hx), ch.zee * (ch.By + mu0f * Hy), ch.zee * (ch.Bz + mu0f * Hz), 0.f);
   }
   if (!mbar_wait(&bar, 0u, F.max_polls)) {
@@ -684,7 +710,7 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_rows_inv_red(FusedArgs
         const float fan = anisotropy_change(mv, flags, K.k1, K.k2, K.ex, K.ey, K.ez);
         const float dl = floc + flong + fan - 4.f * log1p_move_s(mv.tt, K.sigma);
         acc = dl + __logf(u3) < 0.f;
-        if (acc) mredw[(long long)r0 * hx + ql[e]] = make_float4(mv.mpx, mv.mpy, mv.mpz, a[e].w);
+        if (acc) mredw[MMC_CK(A.ck, (long long)r0 * hx + ql[e], 0, S, kCkFusedState)] = make_float4(mv.mpx, mv.mpy, mv.mpz, a[e].w);
       }
       na += __popc(__ballot_sync(0xffffffffu, acc));
       nv += __popc(__ballot_sync(0xffffffffu, valid[e]));
@@ -721,6 +747,7 @@ static W32Args w32_args(const DemagLaunch &P) {
   A.tw = reinterpret_cast<const float2 *>(P.tw1024);
   A.heff = P.heff; A.Hd = P.Hd; A.Hd_chain = P.Hd_chain;
   A.err = P.err;
+  A.ck = P.ck; A.nchains = P.nchains;
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
   return A;
 }

@@ -50,6 +50,9 @@ struct SweepArgs {
   unsigned max_polls;       // bound of a wait for a band's copies
   int *err;                 // device error word (MMC_ERR_TIMEOUT on a wait that gave up)
   int wait_test;            // test hook: every band's barrier waits for 16 bytes no copy delivers
+  // checked builds (checked.cuh): the record and the table sizes indices are checked against
+  MmcCheck *ck;
+  int blk_total, nchains, nitems;
 };
 
 // A thread handles kSweepCells cells of its block's 256 slots (slot t + j 128):
@@ -66,8 +69,8 @@ constexpr int kSweepThreads = kSweepBlock / kSweepCells;
 // blocks (80 registers) or eight (64 registers, more spills) did on GB300.
 template <bool PERCELL, bool DEBUG, bool FLAT>
 __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 7) k_sweep_pass(SweepArgs A) {
-  const int2 bd = A.blk_desc[A.blk_base + (int)blockIdx.x];
-  const int c = bd.x;
+  const int2 bd = A.blk_desc[MMC_CK(A.ck, A.blk_base + (int)blockIdx.x, 0, A.blk_total, kCkSweepBlock)];
+  const int c = (int)MMC_CK(A.ck, bd.x, 0, A.nchains, kCkSweepBlock);
   const ChainK K = load_chain(A.chains + c);
   const int nx = K.nx, ny = K.ny, nz = FLAT ? 1 : K.nz, hx = K.hx;
   const int pbc = FLAT ? (K.pbc & 3) : K.pbc;
@@ -114,10 +117,11 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 7) k_sweep_pass(S
     qq[e] = q32;
     cellid[e] = (unsigned)i + (unsigned)nx * (unsigned)row;
     if (ok) {
-      a[e] = mc[q32];
-      load_neighbours(pbc, (flags & F_GRAIN) != 0, K.gscale, nx, ny, nz, hx, mo, a[e], i, j, k, row, s, p, nb[e], w[e]);
-      M[e] = cell_material<PERCELL>(K, A.tab, S, (long long)color * S + q32);
-      if (flags & F_DEMAG) h[e] = A.heff[K.h_off + (long long)color * S + q32];
+      a[e] = mc[MMC_CK(A.ck, q32, 0, S, kCkSweepCell)];
+      load_neighbours(pbc, (flags & F_GRAIN) != 0, K.gscale, nx, ny, nz, hx, mo, a[e], i, j, k, row, s, p, nb[e], w[e],
+                      A.ck, S);
+      M[e] = cell_material<PERCELL>(K, A.tab, S, (long long)color * S + q32, A.ck);
+      if (flags & F_DEMAG) h[e] = A.heff[K.h_off + (long long)color * S + MMC_CK(A.ck, q32, 0, S, kCkSweepField)];
       else h[e] = make_float4(M[e].zee * K.Bx, M[e].zee * K.By, M[e].zee * K.Bz, 0.f);
     }
   }
@@ -146,10 +150,11 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 7) k_sweep_pass(S
     if (DEBUG || dl > 0.f) dec = dl + __logf(u3);
     else dec = dl;
     accepted[e] = dec < 0.f;
-    if (accepted[e]) mc[qq[e]] = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
+    if (accepted[e]) mc[MMC_CK(A.ck, qq[e], 0, S, kCkSweepCell)] = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
     if (DEBUG) {
-      A.dec_dbg[cellid[e]] = dec;
-      A.acc_dbg[cellid[e]] = (signed char)accepted[e];
+      const long long cd = MMC_CK(A.ck, cellid[e], 0, (long long)K.nrows * nx, kCkSweepDebug);
+      A.dec_dbg[cd] = dec;
+      A.acc_dbg[cd] = (signed char)accepted[e];
     }
   }
 
@@ -189,8 +194,8 @@ template <bool PERCELL, bool DEBUG, int MINB>
 __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_flat(SweepArgs A) {
   __shared__ float4 skv[kChainKVec];
   __shared__ unsigned wacc[kSweepThreads / 32], watt[kSweepThreads / 32];
-  const int2 bd = A.blk_desc[A.blk_base + (int)blockIdx.x];
-  const int c = bd.x;
+  const int2 bd = A.blk_desc[MMC_CK(A.ck, A.blk_base + (int)blockIdx.x, 0, A.blk_total, kCkSweepBlock)];
+  const int c = (int)MMC_CK(A.ck, bd.x, 0, A.nchains, kCkSweepBlock);
   if (threadIdx.x < kChainKVec) skv[threadIdx.x] = __ldg(reinterpret_cast<const float4 *>(A.chains + c) + threadIdx.x);
   __syncthreads();
   const ChainK K = load_chain_vec(skv);
@@ -235,10 +240,11 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_flat(SweepArgs A)
     qq[e] = q32;
     cellid[e] = (unsigned)i + (unsigned)nx * (unsigned)j;
     if (ok) {
-      a[e] = mc[q32];
+      a[e] = mc[MMC_CK(A.ck, q32, 0, S, kCkSweepCell)];
       // the other colour's slots of the -x, +x, -y, +y neighbours, relative to
       // slot s of row j (periodic axes have even extents)
-      const float4 *P = mo + (long long)j * hx + s;
+      const long long pb = (long long)j * hx + s;
+      const float4 *P = mo + pb;
       const bool hl = i > 0 || (pbc & 1), hr = i < nx - 1 || (pbc & 1);
       const bool hu = j > 0 || (pbc & 2), hd = j < ny - 1 || (pbc & 2);
       const int ol = i > 0 ? p - 1 : hx - 1;
@@ -246,10 +252,10 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_flat(SweepArgs A)
       const int ou = j > 0 ? -hx : (ny - 1) * hx;
       const int od = j < ny - 1 ? hx : -(ny - 1) * hx;
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      nb[e][0] = hl ? P[ol] : z4;
-      nb[e][1] = hr ? P[orr] : z4;
-      nb[e][2] = hu ? P[ou] : z4;
-      nb[e][3] = hd ? P[od] : z4;
+      nb[e][0] = hl ? P[MMC_CK(A.ck, ol, -pb, S - pb, kCkSweepNeighbour)] : z4;
+      nb[e][1] = hr ? P[MMC_CK(A.ck, orr, -pb, S - pb, kCkSweepNeighbour)] : z4;
+      nb[e][2] = hu ? P[MMC_CK(A.ck, ou, -pb, S - pb, kCkSweepNeighbour)] : z4;
+      nb[e][3] = hd ? P[MMC_CK(A.ck, od, -pb, S - pb, kCkSweepNeighbour)] : z4;
       pres[e][0] = hl ? 1.f : 0.f;
       pres[e][1] = hr ? 1.f : 0.f;
       pres[e][2] = hu ? 1.f : 0.f;
@@ -259,8 +265,8 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_flat(SweepArgs A)
         for (int b = 0; b < 4; ++b)
           if (nb[e][b].w != a[e].w) pres[e][b] *= K.gscale;
       }
-      M[e] = cell_material<PERCELL>(K, A.tab, S, (long long)color * S + q32);
-      if (flags & F_DEMAG) h[e] = A.heff[K.h_off + (long long)color * S + q32];
+      M[e] = cell_material<PERCELL>(K, A.tab, S, (long long)color * S + q32, A.ck);
+      if (flags & F_DEMAG) h[e] = A.heff[K.h_off + (long long)color * S + MMC_CK(A.ck, q32, 0, S, kCkSweepField)];
       else h[e] = make_float4(M[e].zee * K.Bx, M[e].zee * K.By, M[e].zee * K.Bz, 0.f);
     }
   }
@@ -298,10 +304,11 @@ __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_flat(SweepArgs A)
     // ln u3 < 0: accept iff dl + ln u3 < 0 (taken for every cell: no divergent branch)
     const float dec = dl + __logf(u3);
     accepted[e] = dec < 0.f;
-    if (accepted[e]) mc[qq[e]] = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
+    if (accepted[e]) mc[MMC_CK(A.ck, qq[e], 0, S, kCkSweepCell)] = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
     if (DEBUG) {
-      A.dec_dbg[cellid[e]] = dec;
-      A.acc_dbg[cellid[e]] = (signed char)accepted[e];
+      const long long cd = MMC_CK(A.ck, cellid[e], 0, (long long)nx * K.nrows, kCkSweepDebug);
+      A.dec_dbg[cd] = dec;
+      A.acc_dbg[cd] = (signed char)accepted[e];
     }
   }
 
@@ -368,11 +375,14 @@ __device__ __forceinline__ void band_issue(const SweepArgs &A, int4 it, const Ba
   unsigned bytes = 2u * (unsigned)nr * row_b + (rb >= 0 ? row_b : 0u) + (ra >= 0 ? row_b : 0u);
   if (demag) bytes += (unsigned)nr * row_b;
   mbar_arrive_expect_tx(bar, bytes + extra);
-  bulk_g2s(g.own, own + (long long)r0 * hx, (unsigned)nr * row_b, bar);
-  bulk_g2s(g.other + hx, oth + (long long)r0 * hx, (unsigned)nr * row_b, bar);
-  if (rb >= 0) bulk_g2s(g.other, oth + (long long)rb * hx, row_b, bar);
-  if (ra >= 0) bulk_g2s(g.other + (long long)(nr + 1) * hx, oth + (long long)ra * hx, row_b, bar);
-  if (demag) bulk_g2s(g.heff, A.heff + ch.h_off + (long long)A.color * S + (long long)r0 * hx, (unsigned)nr * row_b, bar);
+  const long long band = MMC_CKR(A.ck, (long long)r0 * hx, (long long)nr * hx, 0, S, kCkBandCopy);
+  bulk_g2s(g.own, own + band, (unsigned)nr * row_b, bar);
+  bulk_g2s(g.other + hx, oth + band, (unsigned)nr * row_b, bar);
+  if (rb >= 0) bulk_g2s(g.other, oth + MMC_CKR(A.ck, (long long)rb * hx, hx, 0, S, kCkBandCopy), row_b, bar);
+  if (ra >= 0)
+    bulk_g2s(g.other + (long long)(nr + 1) * hx, oth + MMC_CKR(A.ck, (long long)ra * hx, hx, 0, S, kCkBandCopy), row_b,
+             bar);
+  if (demag) bulk_g2s(g.heff, A.heff + ch.h_off + (long long)A.color * S + band, (unsigned)nr * row_b, bar);
 }
 
 template <bool DEBUG>
@@ -394,16 +404,18 @@ __global__ void __launch_bounds__(kBandThreads, 3) k_sweep_band(SweepArgs A) {
   }
   __syncthreads();
   int item = A.i0 + (int)blockIdx.x;
-  if (threadIdx.x == 0 && item < A.i1) band_issue(A, A.items[item], band_stage(band_smem, 0, A), &bar[0], extra);
+  if (threadIdx.x == 0 && item < A.i1)
+    band_issue(A, A.items[MMC_CK(A.ck, item, 0, A.nitems, kCkBandItem)], band_stage(band_smem, 0, A), &bar[0], extra);
   int prev_c = -1, k = 0;
   for (; item < A.i1; ++k, item += G) {
     const int st = k & 1;
-    const int4 it = A.items[item];
+    const int4 it = A.items[MMC_CK(A.ck, item, 0, A.nitems, kCkBandItem)];
     if (threadIdx.x == 0) {
       const int nxt = item + G;
       if (nxt < A.i1) {
         fence_proxy_async_smem();
-        band_issue(A, A.items[nxt], band_stage(band_smem, st ^ 1, A), &bar[st ^ 1], extra);
+        band_issue(A, A.items[MMC_CK(A.ck, nxt, 0, A.nitems, kCkBandItem)], band_stage(band_smem, st ^ 1, A),
+                   &bar[st ^ 1], extra);
       }
       if (prev_c >= 0) {                      // counts of the previous band
         unsigned sa = 0, sv = 0;
@@ -491,10 +503,11 @@ __global__ void __launch_bounds__(kBandThreads, 3) k_sweep_band(SweepArgs A) {
       const float dec = dl + __logf(u3);
       accepted[e] = dec < 0.f;
       const unsigned qg = (unsigned)r0 * (unsigned)hx + ql[e];
-      if (accepted[e]) mc[qg] = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
+      if (accepted[e]) mc[MMC_CK(A.ck, qg, 0, S, kCkSweepCell)] = make_float4(v.mpx, v.mpy, v.mpz, a[e].w);
       if (DEBUG) {
-        A.dec_dbg[cellid[e]] = dec;
-        A.acc_dbg[cellid[e]] = (signed char)accepted[e];
+        const long long cd = MMC_CK(A.ck, cellid[e], 0, (long long)nx * K.nrows, kCkSweepDebug);
+        A.dec_dbg[cd] = dec;
+        A.acc_dbg[cd] = (signed char)accepted[e];
       }
     }
     unsigned na = 0, nv = 0;
@@ -568,6 +581,7 @@ void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
   A.items = P.items; A.i0 = P.i0; A.i1 = P.i1;
   A.stage_own = P.stage_own; A.stage_other = P.stage_other;
   A.max_polls = P.max_polls; A.err = P.err; A.wait_test = P.wait_test;
+  A.ck = P.ck; A.blk_total = P.blk_total; A.nchains = P.nchains; A.nitems = P.nitems;
   if (P.band && P.nstripes <= 1 && P.i1 > P.i0) {
     const int grid = std::min(P.i1 - P.i0, P.band_grid);
     const size_t sm = band_smem_bytes(P.stage_own, P.stage_other);

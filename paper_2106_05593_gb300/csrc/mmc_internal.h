@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "checked.cuh"
+
 namespace mmc {
 
 // CODATA 2018 SI values
@@ -202,6 +204,8 @@ struct SweepLaunch {
   unsigned max_polls;           // bound of a wait for a band's copies
   int *err;                     // device error word
   int wait_test;                // test hook (mmc_options.wait_test)
+  MmcCheck *ck;                 // checked builds: the record (checked.cuh)
+  int blk_total, nchains, nitems;   // sizes of the block table, chain table and item table
 };
 constexpr int MMC_ERR_TIMEOUT_CODE = -3;   // mmc_status MMC_ERR_TIMEOUT
 void launch_sweep_pass(const Launch &L, const SweepLaunch &P);
@@ -274,6 +278,8 @@ struct DemagLaunch {
   const void *const *nhatT;     // their tensor spectra, per set [comp][kx][kyq] (or null), kyq pitch kW32TensorPitch
   const void *tw1024;           // their 32 x 32 twiddle table
   int *err;                     // device error word of bounded waits
+  MmcCheck *ck;                 // checked builds: the record (checked.cuh)
+  int nchains;                  // entries of the chain table
   bool ff;                      // with fp64: float-float arithmetic in the generic kernels (nhat and
                                 // twiddle tables in float-float, the spectrum as pairs of float pairs)
 };

@@ -64,10 +64,12 @@ struct CellMat {
 // off = colour * S + slot; per-cell tables are 3 float4 arrays of 2 S entries:
 // {p2, p4, m_e^2 (high part), sigma}, {zee, k1, k2, bond scale}, {e_A, m_e^2 low part}
 template <bool PERCELL, typename CH>
-__device__ __forceinline__ CellMat cell_material(const CH &ch, const float4 *tab, long long S, long long off) {
+__device__ __forceinline__ CellMat cell_material(const CH &ch, const float4 *tab, long long S, long long off,
+                                                 MmcCheck *ck = nullptr) {
   CellMat M;
   if (PERCELL) {
     const float4 *tb = tab + ch.t_off;
+    off = MMC_CK(ck, off, 0, 2 * S, kCkSweepTable);
     const float4 t0 = tb[off], t1 = tb[2 * S + off], t2 = tb[4 * S + off];
     M.p2 = t0.x; M.p4 = t0.y; M.me2h = t0.z; M.me2l = t2.w; M.sigma = t0.w;
     M.zee = t1.x; M.k1 = t1.y; M.k2 = t1.z; M.bs = t1.w;
@@ -84,7 +86,8 @@ __device__ __forceinline__ CellMat cell_material(const CH &ch, const float4 *tab
 // colour's array mo; absent bonds get weight 0, bonds across grains gscale
 __device__ __forceinline__ void load_neighbours(int pbc, bool grain, float gscale, int nx, int ny, int nz, int hx,
                                                 const float4 *mo, float4 a, int i, int j, int k, int row, int s,
-                                                int p, float4 nb[6], float w[6]) {
+                                                int p, float4 nb[6], float w[6], MmcCheck *ck = nullptr,
+                                                long long S = 0) {
   const int im = i > 0 ? i - 1 : ((pbc & 1) ? nx - 1 : -1);
   const int ip = i < nx - 1 ? i + 1 : ((pbc & 1) ? 0 : -1);
   const int jm = j > 0 ? j - 1 : ((pbc & 2) ? ny - 1 : -1);
@@ -93,12 +96,12 @@ __device__ __forceinline__ void load_neighbours(int pbc, bool grain, float gscal
   const int kp = k < nz - 1 ? k + 1 : ((pbc & 4) ? 0 : -1);
   const long long rb = (long long)row * hx;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  nb[0] = im >= 0 ? mo[rb + ((im - 1 + p) >> 1)] : z4;
-  nb[1] = ip >= 0 ? mo[rb + ((ip - 1 + p) >> 1)] : z4;
-  nb[2] = jm >= 0 ? mo[(long long)(jm + ny * k) * hx + s] : z4;
-  nb[3] = jp >= 0 ? mo[(long long)(jp + ny * k) * hx + s] : z4;
-  nb[4] = km >= 0 ? mo[(long long)(j + ny * km) * hx + s] : z4;
-  nb[5] = kp >= 0 ? mo[(long long)(j + ny * kp) * hx + s] : z4;
+  nb[0] = im >= 0 ? mo[MMC_CK(ck, rb + ((im - 1 + p) >> 1), 0, S, kCkSweepNeighbour)] : z4;
+  nb[1] = ip >= 0 ? mo[MMC_CK(ck, rb + ((ip - 1 + p) >> 1), 0, S, kCkSweepNeighbour)] : z4;
+  nb[2] = jm >= 0 ? mo[MMC_CK(ck, (long long)(jm + ny * k) * hx + s, 0, S, kCkSweepNeighbour)] : z4;
+  nb[3] = jp >= 0 ? mo[MMC_CK(ck, (long long)(jp + ny * k) * hx + s, 0, S, kCkSweepNeighbour)] : z4;
+  nb[4] = km >= 0 ? mo[MMC_CK(ck, (long long)(j + ny * km) * hx + s, 0, S, kCkSweepNeighbour)] : z4;
+  nb[5] = kp >= 0 ? mo[MMC_CK(ck, (long long)(j + ny * kp) * hx + s, 0, S, kCkSweepNeighbour)] : z4;
   w[0] = im >= 0 ? 1.f : 0.f;
   w[1] = ip >= 0 ? 1.f : 0.f;
   w[2] = jm >= 0 ? 1.f : 0.f;

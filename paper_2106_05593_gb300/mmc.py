@@ -35,6 +35,11 @@ def default_options(**kw) -> Options:
     return o
 
 
+def checked_build() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return bool(load().mmc_checked_build())
+
+
 def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -279,6 +284,17 @@ class MMC:
         return [{"mean_m": np.array(o.mean_m[:]), "mean_len": o.mean_len, "mean_len2": o.mean_len2,
                  "nsnap": o.nsnap, "nonfinite": o.nonfinite, "acc_rate": o.acc_rate,
                  "theta_deg": o.theta_deg, "sweeps": o.sweeps, "hist": hist[k]} for k, o in enumerate(obs)]
+
+    def check_report(self, clear=False):
+        """Bounds-checked builds: out-of-range indices met so far, and the first
+        (site name, index, [lo, hi)); always zero in normal builds."""
+        n = C.c_int64(0)
+        site = C.c_int(0)
+        rng = (C.c_int64 * 3)()
+        check(load().mmc_check_report(self._ctx, C.byref(n), C.byref(site), rng, int(bool(clear))),
+              "mmc_check_report")
+        return {"count": int(n.value), "site": load().mmc_check_site_name(site.value).decode(),
+                "index": int(rng[0]), "lo": int(rng[1]), "hi": int(rng[2])}
 
     def energy(self, chain=0):
         """Energy terms of the current state (J): total, exchange, DMI, anisotropy,
