@@ -14,6 +14,7 @@
 #include <thread>
 #include <vector>
 
+#include <cuda.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/mmc.h"
@@ -119,6 +120,7 @@ struct IlTables {
 struct DemagPlan {
   IlTables small;                       // FP32 variant 3: E = 6144 (2 blocks per SM)
   IlTables w32;                         // FP32 variant 4: warp transforms, 1024 x 1024 grids only
+  CUtensorMap tmap_spec;                // variant 4: the spectrum as a 2D tensor of tiles (column boxes)
   bool fp64 = false;
   bool ff = false;                      // fp64 plan run by the float-float generic kernels
   int nchain_table = 0;                 // entries of the chain table the plan indexes
@@ -556,6 +558,33 @@ mmc_status build_il_tables(mmc_ctx *c, IlTables &T, const std::vector<ChainDev> 
   return MMC_OK;
 }
 
+// The spectrum buffer of the warp-transform path as a 2D FP32 tensor: one row per
+// tile of four rows (kW32Tile complex values, 4160 floats, 16,640 bytes), `tiles`
+// rows; boxes of 8 floats (one kx of a tile) x 128 tiles (a 512-row column).
+// The encoder is the driver's, looked up through the runtime (no link to the
+// driver library).
+static bool encode_spec_map(CUtensorMap *map, void *spec, long long tiles) {
+  using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode enc = nullptr;
+  if (!enc) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    enc = reinterpret_cast<Encode>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * kW32Tile), (cuuint64_t)tiles};
+  const cuuint64_t strides[1] = {(cuuint64_t)(2 * kW32Tile) * sizeof(float)};
+  const cuuint32_t box[2] = {8, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, spec, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 // Plan of the demag kernels over `chains`.  single: the plan carries its own
 // chain table and spectrum buffer (chain ids are positions in `chains`);
 // otherwise it indexes the context's chain table by global chain id and uses the
@@ -700,6 +729,18 @@ mmc_status build_demag_plan(mmc_ctx *c, DemagPlan &P, const std::vector<int> &ch
     MMC_TRY(dalloc(c, &P.spec, (size_t)spec_elems * csz));
     CUDA_TRY(cudaMemset(P.spec, 0, (size_t)spec_elems * csz));   // padding columns stay defined
   }
+  if (P.w32.ok) {
+    // the tensor spans the whole buffer (a shared one holds every chain of the batch)
+    long long tot = spec_elems;
+    if (shared_spec) {
+      tot = 0;
+      for (const ChainDev &D : c->ch) tot += 3LL * spectrum_rows(D) * D.Sx;
+    }
+    if (tot % kW32Tile != 0 || !encode_spec_map(&P.tmap_spec, P.spec, tot / kW32Tile)) {
+      P.w32.ok = false;
+      if (P.fft_variant == 4) P.fft_variant = 1;
+    }
+  }
   P.ready = true;
   return MMC_OK;
 }
@@ -742,6 +783,7 @@ DemagLaunch make_demag_launch(mmc_ctx *c, const DemagPlan &P, float4 *heff, doub
   D.nchains = P.nchain_table;
   D.nhatT = (const void *const *)c->d_nhat32t;
   D.tw1024 = c->d_tw1024;
+  D.tmap_spec = &P.tmap_spec;
   if (P.il2d && P.fft_variant == 4 && P.w32.ok && !P.fp64) {
     D.w32 = true;
     D.rows_chain = P.w32.rows_chain; D.rows_first = P.w32.rows_first; D.rows_blocks = P.w32.rows_blocks;

@@ -21,6 +21,8 @@
 //   k_w32_rows_inv  one block per tile: the packed sequences z = a + i b built
 //                   from the half spectra, inverse transforms, the crop x < nx,
 //                   and the sweep's field zee (B + mu0 H) in the split layout.
+#include <cuda.h>
+
 #include "demag_args.cuh"
 #include "fft_w32.cuh"
 #include "philox.cuh"
@@ -50,8 +52,6 @@ struct W32Args {
 constexpr int kW32Half = 513;           // kx = 0..512
 constexpr int kW32TPitch = kW32TensorPitch;                    // tensor row (kyq) pitch, 16-byte multiple
 constexpr long long kW32TQ = (long long)kW32Half * kW32TPitch; // one tensor component
-constexpr int kW32Sx = 520;             // spectrum row stride of a 1024-point grid (complex values)
-constexpr int kW32Tile = 4 * kW32Sx;    // one tile of four rows
 constexpr int kW32TilePitch = 524;      // smem row pitch of the row kernels' tiles
 constexpr unsigned kW32Polls = 1u << 22;
 
@@ -155,17 +155,40 @@ __global__ void __launch_bounds__(192, 3) k_w32_rows_fwd(W32Args A) {
   }
 }
 
-__global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A) {
+// The spectrum seen as a 2D tensor for the column loads (tensor map tmS): a
+// row of the tensor is one tile of four rows (kW32Tile complex values = 4160
+// floats), so one kx of a tile is 8 consecutive floats; a box of 8 floats x
+// kW32ColTiles tiles is one 512-row column of one component.  Boxes of chains
+// with fewer rows reach into the next component's tiles (read, not used), and
+// past the end of the buffer they read zeros.
+constexpr int kW32ColTiles = 128;
+constexpr unsigned kW32ColBytes = kW32ColTiles * 32u;
+static_assert(kW32ColBytes + 128 <= kW32Buf * sizeof(float2), "a column box fits a warp buffer");
+
+__global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A, const __grid_constant__ CUtensorMap tmS) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
   float *tn = reinterpret_cast<float *>(sm + 3 * kW32Buf);   // this column's tensor, [4][kW32TPitch]
-  __shared__ uint64_t tbar;
+  __shared__ uint64_t tbar, cbar[3];
   const int c = w32_chain_of_block(A);
   const ChainDev &ch = A.chains[c];
   const int kx = (int)(blockIdx.x - A.blk_first[c]);
   const int lane = threadIdx.x & 31, comp = threadIdx.x >> 5;
   const int ny = ch.ny;
   float2 *buf = sm + comp * kW32Buf;
+  // this warp's column of the spectrum comes in as one box of the tensor map,
+  // into the start of the warp's buffer rounded up to 128 bytes
+  const long long R4 = (long long)((ch.nrows + 3) & ~3);
+  float2 *colbuf = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(buf) + 127) & ~(uintptr_t)127);
+  if (lane == 0) {
+    mbar_init(&cbar[comp], 1);
+    mbar_init_fence();
+    mbar_arrive_expect_tx(&cbar[comp], kW32ColBytes);
+    const long long t0 = ch.s_off / kW32Tile;
+    const long long tile0 = MMC_CK(A.ck, t0 + (long long)comp * (R4 / 4), t0, t0 + 3 * (R4 / 4), kCkDemagSpectrum);
+    tma_load_2d(colbuf, &tmS, 8 * (int)MMC_CK(A.ck, kx, 0, kW32Half, kCkDemagSpectrum), (int)tile0, &cbar[comp]);
+  }
+  __syncwarp();
   // the column's four tensor components come in by bulk copy while the
   // forward transforms run
   if (threadIdx.x == 0) {
@@ -181,16 +204,18 @@ __global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A) {
                kW32TPitch * 4u, &tbar);
   }
   // column kx of component comp: row y = 32 n1 + lane is in tile 8 n1 + lane / 4
-  const long long R4 = (long long)((ch.nrows + 3) & ~3);
   const long long cb = (long long)comp * R4 * kW32Sx + (long long)(lane >> 2) * kW32Tile + 4 * kx + (lane & 3);
   float2 *col = A.S + ch.s_off + cb;
   const long long clo = -cb, chi = 3 * R4 * kW32Sx - cb;   // the chain's spectrum, relative to col
 
+  // in the box, row y is at tile y / 4, element y % 4: float2 index y
   float2 v[32];
+  const bool col_ok = mbar_wait(&cbar[comp], 0u, kW32Polls);
+  if (!col_ok && lane == 0) atomicExch(A.err, -3);      // MMC_ERR_TIMEOUT; this column's field is wrong
 #pragma unroll
   for (int n1 = 0; n1 < 16; ++n1)
-    v[n1] = 32 * n1 + lane < ny ? col[MMC_CK(A.ck, (long long)n1 * 8 * kW32Tile, clo, chi, kCkDemagSpectrum)]
-                                : make_float2(0.f, 0.f);
+    v[n1] = col_ok && 32 * n1 + lane < ny ? colbuf[32 * n1 + lane] : make_float2(0.f, 0.f);
+  __syncwarp();                                        // the box is read: the buffer takes the transpose
   dft32_lo16(v);
   w32_fwd_tail(v, buf, A.tw, lane);                    // v[k2] = M^_comp(kx, lane + 32 k2)
 
@@ -235,6 +260,13 @@ __global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A) {
 #pragma unroll
   for (int n2 = 0; n2 < 16; ++n2)
     if (lane + 32 * n2 < ny) col[MMC_CK(A.ck, (long long)n2 * 8 * kW32Tile, clo, chi, kCkDemagSpectrum)] = v[n2];
+  if (!col_ok) {
+    // the box may still land in the block's shared memory: give it a fixed
+    // time (about a millisecond) before the block exits
+    const long long t0 = clock64();
+    while (clock64() - t0 < (1LL << 21)) {
+    }
+  }
 }
 
 __global__ void __launch_bounds__(192, 3) k_w32_rows_inv(W32Args A) {
@@ -758,7 +790,7 @@ void launch_w32(const Launch &L, const DemagLaunch &P) {
   k_w32_rows_fwd<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);
   if (P.ev) cudaEventRecord(P.ev[1], L.stream);
   A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
-  k_w32_cols<<<P.cols_blocks, 96, kW32ColsSmem, L.stream>>>(A);
+  k_w32_cols<<<P.cols_blocks, 96, kW32ColsSmem, L.stream>>>(A, *static_cast<const CUtensorMap *>(P.tmap_spec));
   if (P.ev) cudaEventRecord(P.ev[2], L.stream);
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
   k_w32_rows_inv<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);
@@ -772,7 +804,7 @@ void launch_w32_stage(const Launch &L, const DemagLaunch &P, int stage) {
     k_w32_rows_fwd<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);
   } else if (stage == 1) {
     A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
-    k_w32_cols<<<P.cols_blocks, 96, kW32ColsSmem, L.stream>>>(A);
+    k_w32_cols<<<P.cols_blocks, 96, kW32ColsSmem, L.stream>>>(A, *static_cast<const CUtensorMap *>(P.tmap_spec));
   } else {
     k_w32_rows_inv<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);
   }

@@ -277,13 +277,16 @@ struct DemagLaunch {
   bool w32;                     // FP32 1024 x 1024 warp-transform kernels (k_demag_w32.cu)
   const void *const *nhatT;     // their tensor spectra, per set [comp][kx][kyq] (or null), kyq pitch kW32TensorPitch
   const void *tw1024;           // their 32 x 32 twiddle table
+  const void *tmap_spec;        // their spectrum as a 2D tensor (CUtensorMap, host copy) for the column boxes
   int *err;                     // device error word of bounded waits
   MmcCheck *ck;                 // checked builds: the record (checked.cuh)
   int nchains;                  // entries of the chain table
   bool ff;                      // with fp64: float-float arithmetic in the generic kernels (nhat and
                                 // twiddle tables in float-float, the spectrum as pairs of float pairs)
 };
-constexpr int kW32TensorPitch = 516;   // kyq = 0..512 padded to a 16-byte multiple of floats
+constexpr int kW32TensorPitch = 516;      // kyq = 0..512 padded to a 16-byte multiple of floats
+constexpr int kW32Sx = 520;                // spectrum row stride of a 1024-point grid (513 kx, 32-byte multiple)
+constexpr int kW32Tile = 4 * kW32Sx;       // complex values of one tile of four rows
 void launch_w32(const Launch &L, const DemagLaunch &P);
 void launch_w32_stage(const Launch &L, const DemagLaunch &P, int stage);   // 0 rows fwd, 1 cols, 2 rows inv
 // the black pass fused with the forward row transforms (k_demag_w32.cu)

@@ -1,5 +1,6 @@
-// Bulk asynchronous copies global -> shared memory (the TMA engine's 1D form,
-// cp.async.bulk) completing on an mbarrier, with bounded waits.
+// Bulk asynchronous copies global -> shared memory by the TMA engine (the 1D
+// form cp.async.bulk, and 2D boxes of a tensor map, cp.async.bulk.tensor)
+// completing on an mbarrier, with bounded waits.
 //
 // Rules these helpers rely on: source and destination 16-byte aligned, sizes a
 // multiple of 16 bytes; one thread arms the barrier with the byte count of the
@@ -47,6 +48,19 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                    smem_u32(dst)),
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
+}
+
+// a 2D box of a tensor described by the tensor map at tmap (a kernel parameter
+// declared __grid_constant__) from global to shared memory at coordinates
+// (x, y) of the map (x in elements of the innermost dimension, x times the
+// element size a multiple of 16 bytes); dst 128-byte aligned; counted on bar's
+// transaction count
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
