@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A, const __grid_cons
   // this warp's column of the spectrum comes in as one box of the tensor map,
   // into the start of the warp's buffer rounded up to 128 bytes
   const long long R4 = (long long)((ch.nrows + 3) & ~3);
-  float2 *colbuf = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(buf) + 127) & ~(uintptr_t)127);
+  // (an offset from buf, so that the compiler keeps the shared-memory accesses)
+  float2 *colbuf = buf + ((128u - (smem_u32(buf) & 127u)) & 127u) / sizeof(float2);
   if (lane == 0) {
     mbar_init(&cbar[comp], 1);
     mbar_init_fence();
