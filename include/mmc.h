@@ -534,6 +534,11 @@ int mmc_checked_build(void);
  * Synchronizes the context's stream. */
 mmc_status mmc_check_report(mmc_ctx *ctx, int64_t *count, int *site, int64_t range[3], int clear);
 
+/* The out-of-range indices met by all contexts destroyed so far in this
+ * process (checked builds; 0 otherwise), and the site of the first of them.
+ * Host only. */
+mmc_status mmc_check_total(int64_t *count, int *site);
+
 /* Name of an access site of mmc_check_report ("?" for an unknown one). */
 const char *mmc_check_site_name(int site);
 

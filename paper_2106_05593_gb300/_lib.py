@@ -23,7 +23,7 @@ EXPORTS = [
     "mmc_set_m", "mmc_get_m", "mmc_set_m_all", "mmc_get_m_all", "mmc_observables_all", "mmc_init_random", "mmc_sweep", "mmc_sweep_sampled",
     "mmc_demag_update", "mmc_pass_debug", "mmc_observables", "mmc_energy", "mmc_demag_field",
     "mmc_tables", "mmc_energy_grad", "mmc_phase_times", "mmc_fft_tuning", "mmc_tuning", "mmc_sweep_field", "mmc_sweep_serial", "mmc_minimize", "mmc_set_temperature", "mmc_angle_hist", "mmc_trial_terms", "mmc_kernel_launches", "mmc_nchains", "mmc_ncell", "mmc_demag_kernel", "mmc_thermo",
-    "mmc_checkpoint", "mmc_restore", "mmc_observables_noalloc", "mmc_checked_build", "mmc_check_report",
+    "mmc_checkpoint", "mmc_restore", "mmc_observables_noalloc", "mmc_checked_build", "mmc_check_report", "mmc_check_total",
     "mmc_check_site_name", "mmc_status_str", "mmc_last_error",
 ]
 
@@ -166,6 +166,8 @@ def load():
     L.mmc_checked_build.argtypes = []
     L.mmc_check_report.restype = st
     L.mmc_check_report.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int64), C.c_int]
+    L.mmc_check_total.restype = st
+    L.mmc_check_total.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int)]
     L.mmc_check_site_name.restype = C.c_char_p
     L.mmc_check_site_name.argtypes = [C.c_int]
     L.mmc_status_str.restype = C.c_char_p

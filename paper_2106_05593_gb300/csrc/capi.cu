@@ -2,6 +2,7 @@
 // launch plans, the sweep loop (eager or CUDA-graph blocks of 100 iterations),
 // measurements and checkpoints.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1300,9 +1301,22 @@ mmc_status mmc_default_options(mmc_options *o) {
   return MMC_OK;
 }
 
+// checked builds: bad indices met by the contexts destroyed so far, and the
+// site of the first of them
+static std::atomic<long long> g_check_total{0};
+static std::atomic<int> g_check_site{0};
+
 void mmc_destroy(mmc_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (kChecked && c->d_check) {
+    MmcCheck r;
+    if (cudaMemcpy(&r, c->d_check, sizeof(r), cudaMemcpyDeviceToHost) == cudaSuccess && r.count) {
+      int none = 0;
+      g_check_site.compare_exchange_strong(none, r.site);
+      g_check_total += (long long)r.count;
+    }
+  }
   for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
   for (auto &g : c->cf) destroy_cufft_plans(g);
   for (auto &g : c->groups) {
@@ -2647,6 +2661,12 @@ mmc_status mmc_check_report(mmc_ctx *c, int64_t *count, int *site, int64_t range
     range[1] = r.lo;
     range[2] = r.hi;
   }
+  return MMC_OK;
+}
+
+mmc_status mmc_check_total(int64_t *count, int *site) {
+  if (count) *count = (int64_t)g_check_total.load();
+  if (site) *site = g_check_site.load();
   return MMC_OK;
 }
 
