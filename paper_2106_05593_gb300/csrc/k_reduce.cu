@@ -35,6 +35,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 __global__ void __launch_bounds__(kReduceBlock)
 k_obs_partial(const ChainDev *chains, const int *blk_chain, const long long *blk_first,
               const float4 *m, double *part, unsigned long long *hist, int bins, float scale) {
+  pdl_enter();
   __shared__ unsigned hcount[kHistMax + 1];
   __shared__ double red[kReduceBlock / 32][6];
   const int c = blk_chain[blockIdx.x];
@@ -84,6 +85,7 @@ k_obs_partial(const ChainDev *chains, const int *blk_chain, const long long *blk
 // one block per chain: fixed-order sum of the chain's partials
 __global__ void k_obs_final(const ChainDev *chains, ChainState *st, const long long *blk_first,
                             const double *part, double *out, int accumulate) {
+  pdl_enter();
   __shared__ double red[6][32];
   const int c = blockIdx.x;
   const long long b0 = blk_first[c], b1 = blk_first[c + 1];
@@ -118,9 +120,9 @@ __global__ void k_obs_final(const ChainDev *chains, ChainState *st, const long l
 }
 
 void launch_obs(const Launch &L, const ObsLaunch &P) {
-  k_obs_partial<<<P.nblocks, kReduceBlock, 0, L.stream>>>(P.chains, P.blk_chain, P.blk_first, P.m,
+  launch_pdl(k_obs_partial, P.nblocks, kReduceBlock, 0, L.stream, P.chains, P.blk_chain, P.blk_first, P.m,
                                                            P.part, P.hist, P.bins, P.scale);
-  k_obs_final<<<P.nchains, 128, 0, L.stream>>>(P.chains, P.st, P.blk_first, P.part, P.out,
+  launch_pdl(k_obs_final, P.nchains, 128, 0, L.stream, P.chains, P.st, P.blk_first, P.part, P.out,
                                                 P.accumulate);
   *L.counter += 2;
 }

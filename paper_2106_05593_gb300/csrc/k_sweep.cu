@@ -69,6 +69,7 @@ constexpr int kSweepThreads = kSweepBlock / kSweepCells;
 // blocks (80 registers) or eight (64 registers, more spills) did on GB300.
 template <bool PERCELL, bool DEBUG, bool FLAT>
 __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 7) k_sweep_pass(SweepArgs A) {
+  pdl_enter();
   const int2 bd = A.blk_desc[MMC_CK(A.ck, A.blk_base + (int)blockIdx.x, 0, A.blk_total, kCkSweepBlock)];
   const int c = (int)MMC_CK(A.ck, bd.x, 0, A.nchains, kCkSweepBlock);
   const ChainK K = load_chain(A.chains + c);
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(kSweepThreads, PERCELL ? 5 : 7) k_sweep_pass(S
 // one local vector (local_change_flat).
 template <bool PERCELL, bool DEBUG, int MINB>
 __global__ void __launch_bounds__(kSweepThreads, MINB) k_sweep_flat(SweepArgs A) {
+  pdl_enter();
   __shared__ float4 skv[kChainKVec];
   __shared__ unsigned wacc[kSweepThreads / 32], watt[kSweepThreads / 32];
   const int2 bd = A.blk_desc[MMC_CK(A.ck, A.blk_base + (int)blockIdx.x, 0, A.blk_total, kCkSweepBlock)];
@@ -593,14 +595,14 @@ void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
   const int v = (P.percell ? 4 : 0) | (P.dec_dbg != nullptr ? 2 : 0) | (P.flat ? 1 : 0);
   const dim3 g(P.nblocks), b(kSweepThreads);
   switch (v) {
-    case 0: k_sweep_pass<false, false, false><<<g, b, 0, L.stream>>>(A); break;
-    case 1: k_sweep_flat<false, false, 7><<<g, b, 0, L.stream>>>(A); break;
-    case 2: k_sweep_pass<false, true, false><<<g, b, 0, L.stream>>>(A); break;
-    case 3: k_sweep_flat<false, true, 7><<<g, b, 0, L.stream>>>(A); break;
-    case 4: k_sweep_pass<true, false, false><<<g, b, 0, L.stream>>>(A); break;
-    case 5: k_sweep_flat<true, false, 5><<<g, b, 0, L.stream>>>(A); break;
-    case 6: k_sweep_pass<true, true, false><<<g, b, 0, L.stream>>>(A); break;
-    default: k_sweep_flat<true, true, 5><<<g, b, 0, L.stream>>>(A); break;
+    case 0: launch_pdl(k_sweep_pass<false, false, false>, g, b, 0, L.stream, A); break;
+    case 1: launch_pdl(k_sweep_flat<false, false, 7>, g, b, 0, L.stream, A); break;
+    case 2: launch_pdl(k_sweep_pass<false, true, false>, g, b, 0, L.stream, A); break;
+    case 3: launch_pdl(k_sweep_flat<false, true, 7>, g, b, 0, L.stream, A); break;
+    case 4: launch_pdl(k_sweep_pass<true, false, false>, g, b, 0, L.stream, A); break;
+    case 5: launch_pdl(k_sweep_flat<true, false, 5>, g, b, 0, L.stream, A); break;
+    case 6: launch_pdl(k_sweep_pass<true, true, false>, g, b, 0, L.stream, A); break;
+    default: launch_pdl(k_sweep_flat<true, true, 5>, g, b, 0, L.stream, A); break;
   }
   ++*L.counter;
 }
@@ -609,6 +611,7 @@ void launch_sweep_pass(const Launch &L, const SweepLaunch &P) {
 // half-angle by +-1 deg when outside 0.5 +- 0.05; the window restarts.
 __global__ void k_advance(ChainState *st, int nchains, unsigned by, unsigned *sweep_base,
                           int adapt_now, int adapt, float tmin, float tmax) {
+  pdl_enter();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c == 0) *sweep_base += by;
   if (c >= nchains || !adapt_now) return;
@@ -631,7 +634,7 @@ __global__ void k_advance(ChainState *st, int nchains, unsigned by, unsigned *sw
 void launch_advance(const Launch &L, ChainState *st, int nchains, unsigned by, unsigned *sweep_base,
                     int adapt_now, int adapt, float tmin, float tmax) {
   const int nb = (nchains + 127) / 128;
-  k_advance<<<nb, 128, 0, L.stream>>>(st, nchains, by, sweep_base, adapt_now, adapt, tmin, tmax);
+  launch_pdl(k_advance, nb, 128, 0, L.stream, st, nchains, by, sweep_base, adapt_now, adapt, tmin, tmax);
   ++*L.counter;
 }
 

@@ -11,6 +11,37 @@
 
 namespace mmc {
 
+// Programmatic dependent launch.  The kernels of an MMC iteration are launched
+// with launch_pdl, so a kernel may be scheduled while the previous kernel of its
+// stream drains; each of them first waits for the previous grid to complete and
+// its memory to be visible (griddepcontrol.wait), then lets its own successor be
+// scheduled (the successor waits the same way before it touches memory).
+__device__ __forceinline__ void pdl_enter() {
+#if defined(__CUDA_ARCH__)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+}  // namespace mmc
+
+namespace mmc {
+
 // CODATA 2018 SI values
 constexpr double kB = 1.380649e-23;
 constexpr double muB = 9.2740100783e-24;
