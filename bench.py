@@ -573,7 +573,9 @@ def run_ours(args):
                                                          "radix16x2": tms[2], "warp32x32": tms[3]}}
             del cf
         if len(specs) > 1:
-            plain = [MMC([sp], demag=int(demag), demag_fp64=demag_prec(args), fft_variant=args.fft_variant,
+            # the plain form runs the kernels the batch runs (its FFT variant), so that
+            # the two forms differ only in how the chains are launched
+            plain = [MMC([sp], demag=int(demag), demag_fp64=demag_prec(args), fft_variant=g.fft_tuning()[0],
                          stream=stream) for sp in specs]
             for k, p1 in enumerate(plain):
                 p1.set_m(g.get_m(k))

@@ -37,7 +37,6 @@ constexpr int kGenericThreads = 512;
 
 template <typename R>
 __global__ void __launch_bounds__(kGenericThreads) k_rows_fwd(DemagArgs<R> A) {
-  pdl_enter();
   using C = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
@@ -105,7 +104,6 @@ __global__ void __launch_bounds__(kGenericThreads) k_rows_fwd(DemagArgs<R> A) {
 
 template <typename R>
 __global__ void __launch_bounds__(kGenericThreads) k_cols(DemagArgs<R> A, int CC) {
-  pdl_enter();
   using C = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
@@ -179,7 +177,6 @@ __global__ void __launch_bounds__(kGenericThreads) k_cols(DemagArgs<R> A, int CC
 
 template <typename R>
 __global__ void __launch_bounds__(kGenericThreads) k_rows_inv(DemagArgs<R> A) {
-  pdl_enter();
   using C = typename Cx<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *buf = reinterpret_cast<C *>(smem_raw);
@@ -283,13 +280,13 @@ void launch_demag_impl(const Launch &L, const DemagLaunch &P) {
   }
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
   if (P.ev) cudaEventRecord(P.ev[0], L.stream);
-  launch_pdl(k_rows_fwd<R>, P.rows_blocks, P.rows_threads, P.rows_smem, L.stream, A);
+  k_rows_fwd<R><<<P.rows_blocks, P.rows_threads, P.rows_smem, L.stream>>>(A);
   if (P.ev) cudaEventRecord(P.ev[1], L.stream);
   A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
-  launch_pdl(k_cols<R>, P.cols_blocks, P.cols_threads, P.cols_smem, L.stream, A, P.cols_per_block);
+  k_cols<R><<<P.cols_blocks, P.cols_threads, P.cols_smem, L.stream>>>(A, P.cols_per_block);
   if (P.ev) cudaEventRecord(P.ev[2], L.stream);
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
-  launch_pdl(k_rows_inv<R>, P.rows_blocks, P.rows_threads, P.rows_smem, L.stream, A);
+  k_rows_inv<R><<<P.rows_blocks, P.rows_threads, P.rows_smem, L.stream>>>(A);
   if (P.ev) cudaEventRecord(P.ev[3], L.stream);
   *L.counter += 3;
 }

@@ -24,7 +24,6 @@ __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c
 
 template <typename CFG>
 __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagArgs<typename CFG::R> A) {
-  pdl_enter();
   using R = typename CFG::R;
   using C = typename Cx<R>::T;
   constexpr int E = CFG::E, V = CFG::V;
@@ -102,7 +101,6 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_fwd2(DemagA
 
 template <typename CFG>
 __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs<typename CFG::R> A) {
-  pdl_enter();
   using R = typename CFG::R;
   using C = typename Cx<R>::T;
   constexpr int E = CFG::E, V = CFG::V;
@@ -176,7 +174,6 @@ __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_cols2d(DemagArgs
 
 template <typename CFG>
 __global__ void __launch_bounds__(CFG::E / CFG::V, CFG::MINB) k_rows_inv2(DemagArgs<typename CFG::R> A) {
-  pdl_enter();
   using R = typename CFG::R;
   using C = typename Cx<R>::T;
   constexpr int E = CFG::E, V = CFG::V;
@@ -279,13 +276,13 @@ void launch_il(const Launch &L, const DemagLaunch &P, DemagArgs<typename CFG::R>
   constexpr int T = CFG::E / CFG::V;
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
   if (P.ev) cudaEventRecord(P.ev[0], L.stream);
-  launch_pdl(k_rows_fwd2<CFG>, P.rows_blocks, T, P.rows_smem, L.stream, A);
+  k_rows_fwd2<CFG><<<P.rows_blocks, T, P.rows_smem, L.stream>>>(A);
   if (P.ev) cudaEventRecord(P.ev[1], L.stream);
   A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
-  launch_pdl(k_cols2d<CFG>, P.cols_blocks, T, P.cols_smem, L.stream, A);
+  k_cols2d<CFG><<<P.cols_blocks, T, P.cols_smem, L.stream>>>(A);
   if (P.ev) cudaEventRecord(P.ev[2], L.stream);
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
-  launch_pdl(k_rows_inv2<CFG>, P.rows_blocks, T, P.inv_smem, L.stream, A);
+  k_rows_inv2<CFG><<<P.rows_blocks, T, P.inv_smem, L.stream>>>(A);
   if (P.ev) cudaEventRecord(P.ev[3], L.stream);
   *L.counter += 3;
 }

@@ -74,7 +74,6 @@ __device__ __forceinline__ int w32_chain_of_block(const W32Args &A) {
 }
 
 __global__ void __launch_bounds__(192, 3) k_w32_rows_fwd(W32Args A) {
-  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
   const int c = w32_chain_of_block(A);
@@ -167,7 +166,6 @@ constexpr unsigned kW32ColBytes = kW32ColTiles * 32u;
 static_assert(kW32ColBytes + 128 <= kW32Buf * sizeof(float2), "a column box fits a warp buffer");
 
 __global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A, const __grid_constant__ CUtensorMap tmS) {
-  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
   float *tn = reinterpret_cast<float *>(sm + 3 * kW32Buf);   // this column's tensor, [4][kW32TPitch]
@@ -273,7 +271,6 @@ __global__ void __launch_bounds__(96, 5) k_w32_cols(W32Args A, const __grid_cons
 }
 
 __global__ void __launch_bounds__(192, 3) k_w32_rows_inv(W32Args A) {
-  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
   const int c = w32_chain_of_block(A);
@@ -379,7 +376,6 @@ struct FusedArgs {
 };
 
 __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_black_rows_fwd(FusedArgs F) {
-  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
   float4 *tb = reinterpret_cast<float4 *>(smem_raw);  // black rows r0 .. r0 + nr - 1, pitch hx
@@ -587,7 +583,6 @@ static_assert(kFusedInvSmem >= 6 * kW32Buf * sizeof(float2), "the buffers cover 
 static_assert(kFieldTileBytes % 16 == 0, "bulk copy alignment");
 
 __global__ void __launch_bounds__(kFusedThreads, 3) k_w32_rows_inv_red(FusedArgs F) {
-  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
   float *ft = reinterpret_cast<float *>(smem_raw);                      // field tile [comp][row][x]
@@ -793,13 +788,13 @@ static W32Args w32_args(const DemagLaunch &P) {
 void launch_w32(const Launch &L, const DemagLaunch &P) {
   W32Args A = w32_args(P);
   if (P.ev) cudaEventRecord(P.ev[0], L.stream);
-  launch_pdl(k_w32_rows_fwd, P.rows_blocks, 192, kW32RowsSmem, L.stream, A);
+  k_w32_rows_fwd<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);
   if (P.ev) cudaEventRecord(P.ev[1], L.stream);
   A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
-  launch_pdl(k_w32_cols, P.cols_blocks, 96, kW32ColsSmem, L.stream, A, *static_cast<const CUtensorMap *>(P.tmap_spec));
+  k_w32_cols<<<P.cols_blocks, 96, kW32ColsSmem, L.stream>>>(A, *static_cast<const CUtensorMap *>(P.tmap_spec));
   if (P.ev) cudaEventRecord(P.ev[2], L.stream);
   A.blk_chain = P.rows_chain; A.blk_first = P.rows_first;
-  launch_pdl(k_w32_rows_inv, P.rows_blocks, 192, kW32RowsSmem, L.stream, A);
+  k_w32_rows_inv<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);
   if (P.ev) cudaEventRecord(P.ev[3], L.stream);
   *L.counter += 3;
 }
@@ -807,12 +802,12 @@ void launch_w32(const Launch &L, const DemagLaunch &P) {
 void launch_w32_stage(const Launch &L, const DemagLaunch &P, int stage) {
   W32Args A = w32_args(P);
   if (stage == 0) {
-    launch_pdl(k_w32_rows_fwd, P.rows_blocks, 192, kW32RowsSmem, L.stream, A);
+    k_w32_rows_fwd<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);
   } else if (stage == 1) {
     A.blk_chain = P.cols_chain; A.blk_first = P.cols_first;
-    launch_pdl(k_w32_cols, P.cols_blocks, 96, kW32ColsSmem, L.stream, A, *static_cast<const CUtensorMap *>(P.tmap_spec));
+    k_w32_cols<<<P.cols_blocks, 96, kW32ColsSmem, L.stream>>>(A, *static_cast<const CUtensorMap *>(P.tmap_spec));
   } else {
-    launch_pdl(k_w32_rows_inv, P.rows_blocks, 192, kW32RowsSmem, L.stream, A);
+    k_w32_rows_inv<<<P.rows_blocks, 192, kW32RowsSmem, L.stream>>>(A);
   }
   ++*L.counter;
 }
@@ -838,7 +833,7 @@ static FusedArgs fused_args(const DemagLaunch &P, const SweepLaunch &Q) {
 
 void launch_w32_rows_inv_red(const Launch &L, const DemagLaunch &P, const SweepLaunch &Q) {
   FusedArgs F = fused_args(P, Q);
-  launch_pdl(k_w32_rows_inv_red, P.rows_blocks, kFusedThreads, kFusedInvSmem, L.stream, F);
+  k_w32_rows_inv_red<<<P.rows_blocks, kFusedThreads, kFusedInvSmem, L.stream>>>(F);
   ++*L.counter;
 }
 
@@ -858,7 +853,7 @@ void launch_w32_black_rows_fwd(const Launch &L, const DemagLaunch &P, const Swee
     k1 += 0xBB67AE85u;
   }
   F.max_polls = Q.max_polls;
-  launch_pdl(k_w32_black_rows_fwd, P.rows_blocks, kFusedThreads, kFusedSmem, L.stream, F);
+  k_w32_black_rows_fwd<<<P.rows_blocks, kFusedThreads, kFusedSmem, L.stream>>>(F);
   ++*L.counter;
 }
 

@@ -11,11 +11,14 @@
 
 namespace mmc {
 
-// Programmatic dependent launch.  The kernels of an MMC iteration are launched
-// with launch_pdl, so a kernel may be scheduled while the previous kernel of its
-// stream drains; each of them first waits for the previous grid to complete and
-// its memory to be visible (griddepcontrol.wait), then lets its own successor be
-// scheduled (the successor waits the same way before it touches memory).
+// Programmatic dependent launch.  The sublattice-pass, window-step and
+// observables kernels are launched with launch_pdl, so such a kernel may be
+// scheduled while the previous kernel of its stream drains; each of them first
+// waits for the previous grid to complete and its memory to be visible
+// (griddepcontrol.wait), then lets its own successor be scheduled (the
+// successor waits the same way before it touches memory).  Small, launch-bound
+// batches gain from it; the demag kernels, whose blocks hold large shared-memory
+// tiles, are launched plainly (scheduled early, they slowed single-chain runs).
 __device__ __forceinline__ void pdl_enter() {
 #if defined(__CUDA_ARCH__)
   asm volatile("griddepcontrol.wait;" ::: "memory");
