@@ -568,15 +568,16 @@ static bool encode_spec_map(CUtensorMap *map, void *spec, long long tiles) {
   using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static Encode enc = nullptr;
-  if (!enc) {
+  // looked up once (thread-safe initialization of a function-local static)
+  static const Encode enc = []() -> Encode {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return false;
-    enc = reinterpret_cast<Encode>(fn);
-  }
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<Encode>(fn);
+  }();
+  if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)(2 * kW32Tile), (cuuint64_t)tiles};
   const cuuint64_t strides[1] = {(cuuint64_t)(2 * kW32Tile) * sizeof(float)};
   const cuuint32_t box[2] = {8, 128};
