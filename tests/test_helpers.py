@@ -35,3 +35,14 @@ def test_compare_hist_accepts_edge_cells_and_rejects_moves():
     bad[k + 2] += 1
     with pytest.raises(AssertionError):
         compare_hist(bad, m4, bins, 1.0)
+
+
+def test_granular_sizes_cover_even_sides():
+    """The granular batch's square sides are even values of 64..1024 drawn
+    uniformly: not only multiples of 32 (the kernels take any even side)."""
+    import workloads as W
+    s = np.array(W.granular_sizes(2000, seed=3))
+    assert s.min() >= 64 and s.max() <= 1024 and (s % 2 == 0).all()
+    assert (s % 32 != 0).mean() > 0.9
+    assert abs(s.mean() - 544.0) < 15.0
+    assert W.granular_sizes() == W.granular_sizes()          # seeded
