@@ -12,6 +12,9 @@ C-3  Non-interacting cells in a field B along x: <m_x> equals the quadrature of
      Zeeman term), which tests the cone move's symmetry.
 C-7  Fitting Eq. 7 to the sampled lengths recovers m_e and chi (Fig. 2 idea).
      Plus sublattice independence of the red-black pass.
+Interacting equilibrium: an open chain coupled by exchange only samples bond
+     angles whose mean cosine given the lengths is the classical Heisenberg
+     chain's exact L(K) (Fisher, Am. J. Phys. 32, 1964).
 """
 import math
 
@@ -278,3 +281,37 @@ def test_row_bands_of_a_pass():
     for s in (2, 3, 7, 40):
         got, _, _ = on.run(m1, 3, O.new_state(seed=9, adapt=False, demag_mode=2, stripes=s))
         assert np.array_equal(ref, got), s
+
+
+def test_exchange_chain_bond_correlation_is_exact():
+    """An interacting equilibrium with an exact answer: an open chain of cells
+    coupled by exchange only (pair energy c |m_i - m_j|^2, c = V A0 / h^2).
+    Given the lengths, the directions of an open chain are distributed as
+    exp(sum_b K_b m^_i . m^_j) with K_b = 2 c |m_i| |m_j| / kT, whose bond
+    angles are independent with E[cos] = L(K_b) = coth K_b - 1/K_b (the
+    classical Heisenberg chain).  So the sampled mean of cos - L(K_b) over bonds
+    and snapshots vanishes whatever the length distribution; a coupling off by
+    a factor of two would shift it by ~0.2, a wrong sign by ~1."""
+    T, Tc, A0, h = 300.0, 870.0, 1.3e-11, 0.4e-9
+    n = 64
+    spec = W._base((n, 1, 1), (h, h, h), A0=A0, Tc=Tc, T=T)
+    o = O.Oracle(spec)
+    me = O.me(T, Tc)
+    c_kt = h * A0 / (KB * T)               # c / kT with V / h^2 = h for cubic cells
+    assert 1.5 < 2 * c_kt * me * me < 2.5  # K of the typical bond ~ 1.9
+    m = W.random_state(n, 11, me, me)[:, :3].astype(np.float64)
+    st = O.new_state(seed=13, theta_deg=60.0, adapt=False, demag_mode=0)
+    m, _, _ = o.run(m, 500, st)
+    vals = []
+    for _ in range(3000):
+        m, _, _ = o.run(m, 5, st)
+        ln = np.linalg.norm(m, axis=1)
+        u = m / ln[:, None]
+        cos = np.sum(u[:-1] * u[1:], axis=1)
+        K = 2.0 * c_kt * ln[:-1] * ln[1:]
+        vals.append(np.mean(cos - (1.0 / np.tanh(K) - 1.0 / K)))
+    vals = np.array(vals)
+    blocks = vals.reshape(30, 100).mean(axis=1)          # batch means against autocorrelation
+    mean, se = blocks.mean(), blocks.std(ddof=1) / math.sqrt(blocks.size)
+    assert se < 0.006
+    assert abs(mean) < 4.0 * se + 1e-3, (mean, se)
