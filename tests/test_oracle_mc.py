@@ -12,6 +12,8 @@ C-3  Non-interacting cells in a field B along x: <m_x> equals the quadrature of
      Zeeman term), which tests the cone move's symmetry.
 C-7  Fitting Eq. 7 to the sampled lengths recovers m_e and chi (Fig. 2 idea).
      Plus sublattice independence of the red-black pass.
+Anisotropy: free cells with uniaxial K1(T) sample c = m^.e from exp(kappa c^2)
+     (exact, the energy depends on the direction only).
 Interacting equilibrium: an open chain coupled by exchange only samples bond
      angles whose mean cosine given the lengths is the classical Heisenberg
      chain's exact L(K) (Fisher, Am. J. Phys. 32, 1964).
@@ -315,3 +317,38 @@ def test_exchange_chain_bond_correlation_is_exact():
     mean, se = blocks.mean(), blocks.std(ddof=1) / math.sqrt(blocks.size)
     assert se < 0.006
     assert abs(mean) < 4.0 * se + 1e-3, (mean, se)
+
+
+def test_uniaxial_anisotropy_direction_law():
+    """Free cells (no exchange) with uniaxial anisotropy V K1(T) (1 - (m^.e)^2),
+    K1(T) = K1 m_e^3 (Eq. 11 with the l = 2 scaling): the energy depends on the
+    direction only, so c = m^.e is distributed as exp(kappa c^2) on [-1, 1],
+    kappa = V K1(T) / kT, independently of the lengths; <c^2> from that law by
+    quadrature.  A sign error gives the opposite tilt, a missing m_e^3 a kappa
+    1.5x too large."""
+    T, Tc, h = 300.0, 870.0, 5e-9
+    V = h ** 3
+    me = O.me(T, Tc)
+    kappa = 2.0
+    K1 = kappa * KB * T / (V * me ** 3)
+    spec = W._base((64, 64, 1), (h, h, h), A0=0.0, K1=K1, eA=(0.0, 0.0, 1.0), Tc=Tc, T=T)
+    o = O.Oracle(spec)
+    n = o.n
+    m = W.random_state(n, 21, me, me)[:, :3].astype(np.float64)
+    st = O.new_state(seed=23, theta_deg=60.0, adapt=False, demag_mode=0)
+    m, _, _ = o.run(m, 200, st)
+    vals = []
+    for _ in range(200):
+        m, _, _ = o.run(m, 3, st)
+        c = m[:, 2] / np.linalg.norm(m, axis=1)
+        vals.append(np.mean(c * c))
+    vals = np.array(vals)
+    blocks = vals.reshape(20, 10).mean(axis=1)
+    mean, se = blocks.mean(), blocks.std(ddof=1) / math.sqrt(blocks.size)
+    x = np.linspace(-1.0, 1.0, 200001)
+    w = np.exp(kappa * x * x)
+    ref = np.trapezoid(w * x * x, x) / np.trapezoid(w, x)
+    assert se < 0.003
+    assert abs(mean - ref) < 4.0 * se + 5e-4, (mean, ref, se)
+    wrong = np.trapezoid(np.exp(1.5 * kappa * x * x) * x * x, x) / np.trapezoid(np.exp(1.5 * kappa * x * x), x)
+    assert abs(wrong - ref) > 10 * se
