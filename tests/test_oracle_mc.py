@@ -14,6 +14,8 @@ C-7  Fitting Eq. 7 to the sampled lengths recovers m_e and chi (Fig. 2 idea).
      Plus sublattice independence of the red-black pass.
 Anisotropy: free cells with uniaxial K1(T) sample c = m^.e from exp(kappa c^2)
      (exact, the energy depends on the direction only).
+Demag self energy: one flat cell samples the shape-anisotropy law of its own
+     demag factors exactly with the self term, biased with the frozen field.
 Interacting equilibrium: an open chain coupled by exchange only samples bond
      angles whose mean cosine given the lengths is the classical Heisenberg
      chain's exact L(K) (Fisher, Am. J. Phys. 32, 1964).
@@ -352,3 +354,47 @@ def test_uniaxial_anisotropy_direction_law():
     assert abs(mean - ref) < 4.0 * se + 5e-4, (mean, ref, se)
     wrong = np.trapezoid(np.exp(1.5 * kappa * x * x) * x * x, x) / np.trapezoid(np.exp(1.5 * kappa * x * x), x)
     assert abs(wrong - ref) > 10 * se
+
+
+def _self_demag_statistic(demag_self):
+    """mean and standard error of c^2 - g(-kappa(l)) for one flat cell with
+    demag (see test_single_cell_demag_shape_anisotropy_law)."""
+    T, Tc, Ms0 = 300.0, 870.0, 8.6e5
+    h = (5e-9, 5e-9, 1e-9)
+    V = h[0] * h[1] * h[2]
+    spec = W._base((1, 1, 1), h, A0=0.0, Tc=Tc, T=T, demag=True, Ms0=Ms0)
+    o = O.Oracle(spec, demag_self=demag_self)
+    # the cell's own demag factors from the oracle's (separately pinned) tensor
+    Nx = -o.demag_field(np.array([[1.0, 0.0, 0.0]]))[0, 0] / Ms0
+    Nz = -o.demag_field(np.array([[0.0, 0.0, 1.0]]))[0, 2] / Ms0
+    me = O.me(T, Tc)
+    m = np.array([[0.0, 0.6 * me, 0.8 * me]])
+    st = O.new_state(seed=31, theta_deg=60.0, adapt=False, demag_mode=1)
+    m, _, _ = o.run(m, 200, st)
+    x = np.linspace(-1.0, 1.0, 4001)
+    x2 = x * x
+    vals = []
+    for _ in range(20000):
+        m, _, _ = o.run(m, 2, st)
+        ln = float(np.linalg.norm(m[0]))
+        c = m[0, 2] / ln
+        kap = O.MU0 * V * Ms0 ** 2 * ln * ln * (Nz - Nx) / (2.0 * KB * T)
+        w = np.exp(-kap * x2)
+        vals.append(c * c - np.trapezoid(w * x2, x) / np.trapezoid(w, x))
+    blocks = np.array(vals).reshape(100, 200).mean(axis=1)
+    return blocks.mean(), blocks.std(ddof=1) / math.sqrt(blocks.size)
+
+
+def test_single_cell_demag_shape_anisotropy_law():
+    """One flat cell (5 x 5 x 1 nm) with demag: its energy (mu0 V Ms0^2 / 2) m.N.m
+    is a shape anisotropy, so given the length l the direction's c = m^.z follows
+    exp(-kappa(l) c^2), kappa(l) = mu0 V Ms0^2 l^2 (Nzz - Nxx) / 2kT (~1.1 here).
+    With the self term (the exact energy change, App. B's exact form) the sampled
+    mean of c^2 - <c^2>_exact(l) vanishes; with the field frozen at the state
+    before the move (Eq. 14 alone) one cell samples a biased law, which the
+    statistic resolves."""
+    mean, se = _self_demag_statistic(True)
+    assert se < 0.004
+    assert abs(mean) < 4.0 * se + 1e-3, (mean, se)
+    mean_f, se_f = _self_demag_statistic(False)
+    assert mean_f > 5.0 * se_f, (mean_f, se_f)
