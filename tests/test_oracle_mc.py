@@ -16,6 +16,8 @@ Anisotropy: free cells with uniaxial K1(T) sample c = m^.e from exp(kappa c^2)
      (exact, the energy depends on the direction only).
 Demag self energy: one flat cell samples the shape-anisotropy law of its own
      demag factors exactly with the self term, biased with the frozen field.
+Two cells with exchange and DMI: each cell's direction given the other follows
+     the exact von Mises-Fisher law of the pair energy.
 Interacting equilibrium: an open chain coupled by exchange only samples bond
      angles whose mean cosine given the lengths is the classical Heisenberg
      chain's exact L(K) (Fisher, Am. J. Phys. 32, 1964).
@@ -398,3 +400,46 @@ def test_single_cell_demag_shape_anisotropy_law():
     assert abs(mean) < 4.0 * se + 1e-3, (mean, se)
     mean_f, se_f = _self_demag_statistic(False)
     assert mean_f > 5.0 * se_f, (mean_f, se_f)
+
+
+def test_two_cell_exchange_dmi_conditional_law():
+    """Two cells along x coupled by exchange and interfacial DMI (pair energy
+    c |m0 - m1|^2 - d y.(m0 x m1), c = V A0 / h^2, d = V D0 / h, DMI vector
+    z x x = y).  Given cell 1 and both lengths, cell 0's direction follows a
+    von Mises-Fisher law with parameter k0 = l0 l1 (2c u1 + d u1 x y) / kT, so
+    E[u0.k0^ - L(|k0|)] = 0 exactly (L the Langevin function), and the same for
+    cell 1 with k1 = l0 l1 (2c u0 + d y x u0) / kT.  The DMI's sign or its
+    absence shifts the statistic by ~0.5 or ~0.05."""
+    T, Tc, A0, h = 300.0, 870.0, 1.3e-11, 0.4e-9
+    D0 = 2.0 * A0 / h                      # DMI and exchange couplings of the same size
+    spec = W._base((2, 1, 1), (h, h, h), A0=A0, D0=D0, Tc=Tc, T=T)
+    o = O.Oracle(spec)
+    me = O.me(T, Tc)
+    c, d = h * A0, h * h * D0
+    y = np.array([0.0, 1.0, 0.0])
+    m = np.array([[me, 0.0, 0.0], [0.0, me, 0.0]])
+    st = O.new_state(seed=41, theta_deg=60.0, adapt=False, demag_mode=0)
+    m, _, _ = o.run(m, 200, st)
+
+    def lang(k):
+        return 1.0 / np.tanh(k) - 1.0 / k
+
+    vals = {1.0: [], -1.0: []}
+    for _ in range(20000):
+        m, _, _ = o.run(m, 2, st)
+        ln = np.linalg.norm(m, axis=1)
+        u = m / ln[:, None]
+        f = ln[0] * ln[1] / (KB * T)
+        for sgn in vals:
+            k0 = f * (2.0 * c * u[1] + sgn * d * np.cross(u[1], y))
+            k1 = f * (2.0 * c * u[0] + sgn * d * np.cross(y, u[0]))
+            n0, n1 = np.linalg.norm(k0), np.linalg.norm(k1)
+            vals[sgn].append(0.5 * (u[0] @ k0 / n0 - lang(n0) + u[1] @ k1 / n1 - lang(n1)))
+    stats_ = {}
+    for sgn, v in vals.items():
+        b = np.array(v).reshape(100, 200).mean(axis=1)
+        stats_[sgn] = (b.mean(), b.std(ddof=1) / math.sqrt(b.size))
+    mean, se = stats_[1.0]
+    assert se < 0.006
+    assert abs(mean) < 4.0 * se + 1e-3, stats_
+    assert stats_[-1.0][0] < -20.0 * stats_[-1.0][1]
