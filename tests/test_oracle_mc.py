@@ -12,7 +12,8 @@ C-3  Non-interacting cells in a field B along x: <m_x> equals the quadrature of
      Zeeman term), which tests the cone move's symmetry.
 C-7  Fitting Eq. 7 to the sampled lengths recovers m_e and chi (Fig. 2 idea).
      Plus sublattice independence of the red-black pass.
-Anisotropy: free cells with uniaxial K1(T) sample c = m^.e from exp(kappa c^2)
+Anisotropy: free cells with uniaxial K1(T) (and K2(T)) or cubic anisotropy
+     sample their directions from the exact laws exp(-V K(T) f(direction)/kT)
      (exact, the energy depends on the direction only).
 Demag self energy: one flat cell samples the shape-anisotropy law of its own
      demag factors exactly with the self term, biased with the frozen field.
@@ -443,3 +444,62 @@ def test_two_cell_exchange_dmi_conditional_law():
     assert se < 0.006
     assert abs(mean) < 4.0 * se + 1e-3, stats_
     assert stats_[-1.0][0] < -20.0 * stats_[-1.0][1]
+
+
+def _free_cell_directions(spec, seed, stat, nsnap=200, every=3):
+    """batch mean and error of stat(unit directions) over snapshots of free cells"""
+    o = O.Oracle(spec)
+    me = O.me(spec["T"], spec["Tc"])
+    m = W.random_state(o.n, seed, me, me)[:, :3].astype(np.float64)
+    st = O.new_state(seed=seed + 1, theta_deg=60.0, adapt=False, demag_mode=0)
+    m, _, _ = o.run(m, 200, st)
+    vals = []
+    for _ in range(nsnap):
+        m, _, _ = o.run(m, every, st)
+        vals.append(stat(m / np.linalg.norm(m, axis=1)[:, None]))
+    b = np.array(vals).reshape(20, -1).mean(axis=1)
+    return b.mean(), b.std(ddof=1) / math.sqrt(b.size)
+
+
+def test_uniaxial_k2_direction_law():
+    """Uniaxial anisotropy with both terms of Eq. 11, V [K1(T) s + K2(T) s^2],
+    s = 1 - (m^.e)^2, K1(T) = K1 m_e^3, K2(T) = K2 m_e^10: c = m^.e follows
+    exp(-(k1 s + k2 s^2)) on [-1, 1] (k = V K(T) / kT).  With k1 = 1, k2 = 2,
+    <c^2> = 0.6160; K2 scaled like K1 (m_e^3) gives 0.763, no K2 0.429."""
+    T, Tc, h = 300.0, 870.0, 5e-9
+    V, me = h ** 3, O.me(T, Tc)
+    k1, k2 = 1.0, 2.0
+    spec = W._base((64, 64, 1), (h, h, h), A0=0.0, K1=k1 * KB * T / (V * me ** 3),
+                   K2=k2 * KB * T / (V * me ** 10), eA=(0.0, 0.0, 1.0), Tc=Tc, T=T)
+    mean, se = _free_cell_directions(spec, 31, lambda u: np.mean(u[:, 2] ** 2))
+    x = np.linspace(-1.0, 1.0, 200001)
+    s = 1.0 - x * x
+    w = np.exp(-(k1 * s + k2 * s * s))
+    ref = np.trapezoid(w * x * x, x) / np.trapezoid(w, x)
+    assert se < 0.002
+    assert abs(mean - ref) < 4.0 * se + 5e-4, (mean, ref, se)
+
+
+def test_cubic_anisotropy_direction_law():
+    """Cubic anisotropy (Eq. 12), V K1(T) (a^2 b^2 + b^2 c^2 + c^2 a^2) with
+    K1(T) = K1 m_e^10 and the cube axes along x, y, z: the directions follow
+    exp(-k f) on the sphere, f the bracket, k = V K1(T) / kT = 6; <f> by
+    quadrature over the sphere = 0.1495 (0.238 with the sign flipped, 0.076 with
+    the m_e^3 scaling)."""
+    T, Tc, h = 300.0, 870.0, 5e-9
+    V, me = h ** 3, O.me(T, Tc)
+    k = 6.0
+    spec = W._base((64, 64, 1), (h, h, h), A0=0.0, K1=k * KB * T / (V * me ** 10), Tc=Tc, T=T, aniso="cubic")
+
+    def bracket(a, b, c):
+        return a * a * b * b + b * b * c * c + c * c * a * a
+
+    mean, se = _free_cell_directions(spec, 41, lambda u: np.mean(bracket(u[:, 0], u[:, 1], u[:, 2])))
+    th = np.linspace(0.0, np.pi, 1201)
+    ph = np.linspace(0.0, 2.0 * np.pi, 2401)
+    TH, PH = np.meshgrid(th, ph, indexing="ij")
+    f = bracket(np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH))
+    w = np.exp(-k * f) * np.sin(TH)
+    ref = (w * f).sum() / w.sum()
+    assert se < 0.001
+    assert abs(mean - ref) < 4.0 * se + 3e-4, (mean, ref, se)
