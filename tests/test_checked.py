@@ -61,3 +61,10 @@ def test_checks_compile_away(tmp_path):
 def test_normal_library_is_not_checked():
     assert not P.checked_build()
     assert P.load().mmc_check_site_name(99).decode() == "?"
+
+
+def test_total_is_zero_without_contexts():
+    import ctypes
+    n, site = ctypes.c_int64(-1), ctypes.c_int(-1)
+    assert P.load().mmc_check_total(ctypes.byref(n), ctypes.byref(site)) == 0
+    assert n.value == 0 and site.value == 0
